@@ -1,0 +1,186 @@
+/*
+ * nolsm.h -- C ABI of the GB300 (sm_103a) hot path of the non-orthogonalised local submatrix method
+ * (NOLSM), arXiv:2104.08245.
+ *
+ * The method approximates the density matrix of Eq. purification,
+ *     D = 1/2 (I - sign(S^-1 H0 - mu I)) S^-1,
+ * molecule by molecule: for each molecule J it builds dense submatrices T_J(S), T_J(H0) over the rows
+ * where S or H0 is non-zero in J's columns (merged pattern, Sec. "The Non-Orthogonal Local Submatrix
+ * Method"), evaluates Eq. purification_submatrix on them with the Newton-Schulz sign iteration
+ * (Eq. NS1, NS2) after spectral rescaling, and writes the centre molecule's columns back into the
+ * sparse D (Sec. "The Submatrix Method", step (iii)). mu is set by bisection so that Tr(DS) equals
+ * the number of occupied orbitals (Sec. "Simulation Details").
+ *
+ * Conventions shared by every call:
+ *  - Pointers marked (device) are CUDA device pointers owned by the caller; the library never frees
+ *    them. Pointers marked (host) are ordinary host memory.
+ *  - Work is enqueued on the caller's stream (NULL = legacy default stream). Calls that return host
+ *    scalars synchronise that stream before returning.
+ *  - Errors come back as nolsm_status codes; no call aborts, throws across the ABI or prints. After an
+ *    error, nolsm_last_error() gives a one-line message (per thread). A CUDA error that corrupted the
+ *    context is reported as NOLSM_ERR_CUDA and the plan must then be destroyed.
+ *  - Per-submatrix outcomes (not SPD, not converged, non-finite) are reported in the optional device
+ *    array `status` and summarised in the return code (the first such error by submatrix index wins).
+ *  - Every device-side loop is bounded (iteration caps); no kernel waits without a limit.
+ *  - One submatrix per molecule, indexed by the molecule index J = 0 .. n_mol-1.
+ */
+#ifndef NOLSM_H
+#define NOLSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* nolsm_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  NOLSM_OK = 0,
+  NOLSM_ERR_ARG = 1,           /* invalid argument or malformed block-CSR input */
+  NOLSM_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  NOLSM_ERR_OOM = 3,           /* device allocation failed */
+  NOLSM_ERR_NOT_SPD = 4,       /* a Cholesky pivot of some T_J(S) was <= 0 */
+  NOLSM_ERR_NOT_CONVERGED = 5, /* some sign iteration hit max_iter or missed tol_accept */
+  NOLSM_ERR_NONFINITE = 6,     /* NaN/Inf met in some submatrix */
+  NOLSM_ERR_NO_PLATEAU = 7,    /* find_mu: bracket narrowed below tol_mu with |Tr(DS)-N| > tol_n */
+  NOLSM_ERR_UNSUPPORTED = 8,   /* option combination or size this build does not handle */
+  NOLSM_ERR_NO_SOLUTION = 9    /* scatter_density called before any solve_batch */
+} nolsm_status;
+
+/* Arithmetic of the sign-iteration products (a5/a6). The overlap factorisation, the centre columns of
+ * T_J(S)^-1 and all trace sums are FP64 in every mode.
+ *   NOLSM_FP64       every step in FP64 on the CUDA cores (the plain reference path).
+ *   NOLSM_FP32       every Newton-Schulz product as a three-term split of FP16 tensor-core products
+ *                    (hi*hi + hi*lo + lo*hi, FP32 accumulation): about 22 significant bits.
+ *   NOLSM_BF16       Newton-Schulz products as single BF16 tensor-core products (FP32 accumulation)
+ *                    until tol_ns, then refine_steps steps in the NOLSM_FP32 arithmetic.
+ *   NOLSM_BF16X3     three-term split BF16 products throughout (about 16 significant bits), then
+ *                    refine_steps steps in the NOLSM_FP32 arithmetic.
+ *   NOLSM_FP8E4M3    single E4M3 products with a per-submatrix power-of-two scale (FP32
+ *                    accumulation) until tol_ns, then refine_steps steps in NOLSM_FP32 arithmetic. */
+typedef enum {
+  NOLSM_FP64 = 0,
+  NOLSM_FP32 = 1,
+  NOLSM_BF16 = 2,
+  NOLSM_BF16X3 = 3,
+  NOLSM_FP8E4M3 = 4
+} nolsm_precision;
+
+/* Source of the spectral scale alpha_J(mu) >= rho(A_J - mu I) applied before the sign iteration. */
+typedef enum {
+  NOLSM_BOUND_GERSHGORIN = 0, /* Gershgorin interval of A_J = T_J(S)^-1 T_J(H0) */
+  NOLSM_BOUND_POWER = 1,      /* power-iteration estimates of the extreme eigenvalues, widened */
+  NOLSM_BOUND_MLP = 2         /* the learned predictor (nolsm_mlp_*); fallback: power iteration */
+} nolsm_bound_source;
+
+/* Sparse input. S and H0 are symmetric; each is stored block-CSR over molecules: block row I lists,
+ * in strictly ascending order, the molecules J with a stored block (I, J); block (I, J) holds
+ * nbf[I] x nbf[J] float64 values row-major; blocks are concatenated in CSR order. The two patterns
+ * may differ (their union is the merged pattern); each must be structurally symmetric. All arrays
+ * are device memory owned by the caller and must stay valid and unchanged until the plan built from
+ * them is destroyed. */
+typedef struct {
+  int32_t n_mol;
+  const int32_t* nbf;       /* (device) [n_mol], basis functions per molecule, 1..32 */
+  int64_t s_nnzb;
+  const int32_t* s_row_ptr; /* (device) [n_mol+1] */
+  const int32_t* s_col_idx; /* (device) [s_nnzb] */
+  const double* s_vals;     /* (device) [sum over blocks of nbf[I]*nbf[J]] */
+  int64_t h_nnzb;
+  const int32_t* h_row_ptr; /* (device) [n_mol+1] */
+  const int32_t* h_col_idx; /* (device) [h_nnzb] */
+  const double* h_vals;     /* (device) */
+} nolsm_system;
+
+typedef struct {
+  int32_t precision;     /* nolsm_precision */
+  int32_t refine_steps;  /* steps after the low-precision phase (ignored by FP64) */
+  int32_t max_iter;      /* cap on Newton-Schulz steps per submatrix (all phases) */
+  double tol_ns;         /* the low-precision (or FP64) phase ends after the step whose defect
+                            ||I - X_k^2||_F / sqrt(n) is <= tol_ns */
+  double tol_accept;     /* the final X must have defect <= tol_accept, else NOT_CONVERGED */
+  double tol_n;          /* find_mu: accept |Tr(DS) - N_occ| <= tol_n * N_occ */
+  double tol_mu;         /* find_mu: stop when the bracket is narrower than this (Ha) */
+  int32_t max_bisect;    /* find_mu: cap on evaluations */
+  int32_t bound_source;  /* nolsm_bound_source */
+  int64_t sub_begin;     /* solve only submatrices [sub_begin, sub_end) (streaming); */
+  int64_t sub_end;       /* sub_end <= 0 means n_mol */
+} nolsm_options;
+
+/* Defaults for a precision: FP64 tol_ns 1e-9, tol_accept 1e-7, max_iter 100; low-precision modes
+ * tol_ns 1e-2, refine_steps 2 (FP8: 3), tol_accept 1e-4; tol_n 1e-5 (relative), tol_mu 1e-10,
+ * max_bisect 100, Gershgorin bounds, all submatrices. */
+void nolsm_options_default(nolsm_options* opts, int32_t precision);
+
+typedef struct nolsm_plan nolsm_plan; /* opaque; owns all device workspaces */
+
+typedef struct {
+  int32_t n_mol;       /* = number of submatrices */
+  int64_t d_nnzb;      /* blocks of D in the merged pattern */
+  int64_t d_nvals;     /* float64 values of D */
+  int32_t max_n;       /* largest submatrix dimension n_J */
+  int32_t min_n;       /* smallest n_J */
+  double sum_n3;       /* sum over J of n_J^3 (work metric) */
+  int64_t device_bytes;/* device memory currently held by the plan */
+} nolsm_plan_info;
+
+/* a0: submatrix construction plan (Sec. "The Non-Orthogonal Local Submatrix Method", merged pattern;
+ * Sec. "The Submatrix Method", step (i); molecule-coalesced columns, Sec. "Simulation Details").
+ * Builds, on the device, N(J) = {I : block (I,J) stored in S or in H0} in ascending order, the local
+ * offsets of each molecule inside T_J, n_J, the offset of J's own columns, the slot of every block
+ * (I, J) in the merged pattern (used by the write-back) and the grouping of submatrices by size.
+ * Checks the input (sorted, in range, structurally symmetric); returns NOLSM_ERR_ARG if malformed.
+ * On success *out owns device memory until nolsm_plan_destroy. Synchronises the stream. */
+nolsm_status nolsm_build_submatrices(const nolsm_system* sys, nolsm_stream_t stream, nolsm_plan** out);
+
+nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info);
+
+/* Copies the plan's integer maps into caller device buffers (any pointer may be NULL):
+ * nb_ptr [n_mol+1], nb_idx [d_nnzb], nb_off [d_nnzb], sub_n [n_mol], sub_c0 [n_mol],
+ * d_blk_off [d_nnzb+1] (int64 element offsets of the D blocks). The merged pattern of D is
+ * block row I = nb_idx[nb_ptr[I] .. nb_ptr[I+1]). */
+nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_t* nb_idx, int32_t* nb_off,
+                                 int32_t* sub_n, int32_t* sub_c0, int64_t* d_blk_off, nolsm_stream_t stream);
+
+/* a1-a7: every submatrix J in [sub_begin, sub_end) at chemical potential mu:
+ *   T_J(S), T_J(H0) gathered (a1); T_J(S) = L L^T in FP64 (a2); A_J = T_J(S)^-1 T_J(H0) (a3);
+ *   X_0 = (A_J - mu I)/alpha_J (a4, Sec. rescaling before Eq. NS1); X <- 1/2 X (3I - X^2) (a5/a6,
+ *   Eq. NS1) until the defect test passes; centre columns of
+ *   T_J(D) = 1/2 (I - X) T_J(S)^-1 (a7, Eq. purification_submatrix) and the partial traces
+ *   t_S(J) = sum_{j centre, i} T_J(D)_ij T_J(S)_ij and t_H(J) likewise with H0 (Eq. e_elec).
+ * Steps a1-a3 depend only on the geometry and run once per plan and precision class; later calls
+ * at other mu reuse them. Outputs (any may be NULL):
+ *   trace_DS, trace_DH (host): FP64 sums of t_S, t_H over the range;
+ *   sub_t_S, sub_t_H (device, [n_mol] float64): per-submatrix partial traces (range entries written);
+ *   iters (device, [n_mol] int32): Newton-Schulz steps taken; status (device, [n_mol] int32):
+ *   per-submatrix nolsm_status. The centre columns are kept in the plan for nolsm_scatter_density.
+ * Synchronises the stream. */
+nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                               double* trace_DS, double* trace_DH, double* sub_t_S, double* sub_t_H,
+                               int32_t* iters, int32_t* status);
+
+/* a8: write-back (Sec. "The Submatrix Method", step (iii)): block (I, J) of D, for I in N(J), is set
+ * to the rows of I in the centre columns of T_J(D) from the most recent nolsm_solve_batch. D_vals
+ * (device, float64 [d_nvals]) is laid out in the merged pattern with offsets d_blk_off (see
+ * nolsm_plan_get_maps); blocks of submatrices outside the last solved range are left untouched. */
+nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream);
+
+/* a9: chemical potential by bisection (Sec. "Simulation Details"): f(mu) = Tr(DS) - n_occ with
+ * Tr(DS) from nolsm_solve_batch over the options' range; mu = (lo+hi)/2; f < 0 raises lo, otherwise
+ * hi is lowered; stops at the first |f| <= tol_n * n_occ (NOLSM_OK), when hi - lo <= tol_mu
+ * (NOLSM_ERR_NO_PLATEAU) or after max_bisect evaluations (NOLSM_ERR_NO_PLATEAU). The plan keeps the
+ * solution at the returned mu for nolsm_scatter_density. mu_history (host, may be NULL) receives up
+ * to max_bisect evaluated mu values. */
+nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
+                           nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
+                           double* mu_history);
+
+void nolsm_plan_destroy(nolsm_plan* plan);
+const char* nolsm_status_str(nolsm_status s);
+const char* nolsm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NOLSM_H */

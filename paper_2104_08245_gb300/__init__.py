@@ -1,0 +1,223 @@
+"""Python binding of the GB300 NOLSM library (include/nolsm.h).
+
+The binding only marshals arguments: PyTorch supplies device memory and the stream, and every step of
+the method runs in the library's CUDA kernels. Names follow the C ABI: ``nolsm_build_submatrices``,
+``nolsm_solve_batch``, ``nolsm_scatter_density``, ``nolsm_find_mu``. There is no CPU fallback; the
+library must be built (``__graft_entry__.build()``) and a CUDA device must be present.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional
+
+from . import _abi
+from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP32, FP64,  # noqa: F401
+                   PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmSystem)
+
+__all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
+           "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "options", "NolsmError", "Plan",
+           "SolveResult", "MuResult"]
+
+
+class NolsmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _abi.load()
+        msg = lib.nolsm_last_error().decode()
+        super().__init__(f"{where}: {lib.nolsm_status_str(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def options(precision="fp64", **kw) -> NolsmOptions:
+    """Default options of a precision (name or nolsm_precision value), then keyword overrides."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o = NolsmOptions()
+    _abi.load().nolsm_options_default(ctypes.byref(o), p)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class DeviceSystem:
+    """Block-CSR S and H0 copied to device tensors (caller-owned memory for the ABI)."""
+
+    def __init__(self, system, device="cuda"):
+        torch = _torch()
+        dev = torch.device(device)
+        as_t = lambda a, dt: torch.as_tensor(a, dtype=dt).to(dev)
+        self.n_mol = int(system.nbf.shape[0])
+        self.nbf = as_t(system.nbf, torch.int32)
+        self.s_row_ptr = as_t(system.S.row_ptr, torch.int32)
+        self.s_col_idx = as_t(system.S.col_idx, torch.int32)
+        self.s_vals = as_t(system.S.vals, torch.float64)
+        self.h_row_ptr = as_t(system.H.row_ptr, torch.int32)
+        self.h_col_idx = as_t(system.H.col_idx, torch.int32)
+        self.h_vals = as_t(system.H.vals, torch.float64)
+        self.n_occ = float(system.n_occ)
+
+    def struct(self) -> NolsmSystem:
+        s = NolsmSystem()
+        s.n_mol = self.n_mol
+        s.nbf = self.nbf.data_ptr()
+        s.s_nnzb = self.s_col_idx.numel()
+        s.s_row_ptr, s.s_col_idx, s.s_vals = (self.s_row_ptr.data_ptr(), self.s_col_idx.data_ptr(),
+                                              self.s_vals.data_ptr())
+        s.h_nnzb = self.h_col_idx.numel()
+        s.h_row_ptr, s.h_col_idx, s.h_vals = (self.h_row_ptr.data_ptr(), self.h_col_idx.data_ptr(),
+                                              self.h_vals.data_ptr())
+        return s
+
+
+def nolsm_build_submatrices(dsys: DeviceSystem, stream=None) -> "Plan":
+    lib = _abi.load()
+    st = dsys.struct()
+    out = ctypes.c_void_p()
+    rc = lib.nolsm_build_submatrices(ctypes.byref(st), _stream(stream), ctypes.byref(out))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_build_submatrices")
+    return Plan(out, dsys)
+
+
+def nolsm_plan_query(plan: "Plan") -> NolsmPlanInfo:
+    info = NolsmPlanInfo()
+    rc = _abi.load().nolsm_plan_query(plan.handle, ctypes.byref(info))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_query")
+    return info
+
+
+def nolsm_plan_get_maps(plan: "Plan", stream=None) -> dict:
+    torch = _torch()
+    info = nolsm_plan_query(plan)
+    n, m = info.n_mol, info.d_nnzb
+    dev = plan.dsys.nbf.device
+    out = {"nb_ptr": torch.empty(n + 1, dtype=torch.int32, device=dev),
+           "nb_idx": torch.empty(m, dtype=torch.int32, device=dev),
+           "nb_off": torch.empty(m, dtype=torch.int32, device=dev),
+           "sub_n": torch.empty(n, dtype=torch.int32, device=dev),
+           "sub_c0": torch.empty(n, dtype=torch.int32, device=dev),
+           "d_blk_off": torch.empty(m + 1, dtype=torch.int64, device=dev)}
+    rc = _abi.load().nolsm_plan_get_maps(plan.handle, *(out[k].data_ptr() for k in
+                                                        ("nb_ptr", "nb_idx", "nb_off", "sub_n", "sub_c0",
+                                                         "d_blk_off")), _stream(stream))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_get_maps")
+    return out
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    trace_DS: float
+    trace_DH: float
+    sub_t_S: object = None
+    sub_t_H: object = None
+    iters: object = None
+    sub_status: object = None
+
+
+def nolsm_solve_batch(plan: "Plan", mu: float, opts: NolsmOptions, stream=None, per_sub: bool = True,
+                      check: bool = True) -> SolveResult:
+    """Solves every submatrix of the options' range at chemical potential mu. Raises on argument,
+    CUDA or memory errors; per-submatrix outcomes are in ``status``/``sub_status`` (and raise only
+    when ``check``)."""
+    torch = _torch()
+    lib = _abi.load()
+    n = plan.dsys.n_mol
+    dev = plan.dsys.nbf.device
+    tS, tH = ctypes.c_double(), ctypes.c_double()
+    sts = sth = it = sst = None
+    if per_sub:
+        sts = torch.zeros(n, dtype=torch.float64, device=dev)
+        sth = torch.zeros(n, dtype=torch.float64, device=dev)
+        it = torch.zeros(n, dtype=torch.int32, device=dev)
+        sst = torch.zeros(n, dtype=torch.int32, device=dev)
+    rc = lib.nolsm_solve_batch(plan.handle, float(mu), ctypes.byref(opts), _stream(stream), ctypes.byref(tS),
+                               ctypes.byref(tH), _ptr(sts), _ptr(sth), _ptr(it), _ptr(sst))
+    if rc in (_abi.ERR_ARG, _abi.ERR_CUDA, _abi.ERR_OOM, _abi.ERR_UNSUPPORTED) or (check and rc != 0):
+        raise NolsmError(rc, "nolsm_solve_batch")
+    return SolveResult(rc, tS.value, tH.value, sts, sth, it, sst)
+
+
+def nolsm_scatter_density(plan: "Plan", D_vals=None, stream=None):
+    torch = _torch()
+    if D_vals is None:
+        D_vals = torch.zeros(nolsm_plan_query(plan).d_nvals, dtype=torch.float64, device=plan.dsys.nbf.device)
+    rc = _abi.load().nolsm_scatter_density(plan.handle, D_vals.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_scatter_density")
+    return D_vals
+
+
+@dataclasses.dataclass
+class MuResult:
+    status: int
+    mu: float
+    trace_DS: float
+    steps: int
+    history: list
+
+
+def nolsm_find_mu(plan: "Plan", n_occ: float, lo: float, hi: float, opts: NolsmOptions, stream=None,
+                  check: bool = False) -> MuResult:
+    lib = _abi.load()
+    mu, t, steps = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    cap = opts.max_bisect if opts.max_bisect > 0 else 100
+    hist = (ctypes.c_double * cap)()
+    rc = lib.nolsm_find_mu(plan.handle, float(n_occ), float(lo), float(hi), ctypes.byref(opts), _stream(stream),
+                           ctypes.byref(mu), ctypes.byref(t), ctypes.byref(steps), hist)
+    if rc in (_abi.ERR_ARG, _abi.ERR_CUDA, _abi.ERR_OOM, _abi.ERR_UNSUPPORTED) or (check and rc != 0):
+        raise NolsmError(rc, "nolsm_find_mu")
+    return MuResult(rc, mu.value, t.value, steps.value, list(hist[:steps.value]))
+
+
+class Plan:
+    """Owner of a nolsm_plan handle (destroyed with the object or by ``close``)."""
+
+    def __init__(self, handle: ctypes.c_void_p, dsys: DeviceSystem):
+        self.handle = handle
+        self.dsys = dsys      # keeps the caller-owned input tensors alive
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _abi.load().nolsm_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # conveniences with the same semantics as the module functions
+    def info(self):
+        return nolsm_plan_query(self)
+
+    def maps(self, stream=None):
+        return nolsm_plan_get_maps(self, stream)
+
+    def solve(self, mu, opts, **kw):
+        return nolsm_solve_batch(self, mu, opts, **kw)
+
+    def scatter(self, D_vals=None, stream=None):
+        return nolsm_scatter_density(self, D_vals, stream)
+
+    def find_mu(self, n_occ, lo, hi, opts, **kw):
+        return nolsm_find_mu(self, n_occ, lo, hi, opts, **kw)

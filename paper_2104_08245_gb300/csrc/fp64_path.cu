@@ -1,0 +1,578 @@
+// Geometry preparation (a1 gather, a2 FP64 Cholesky, a3 A = T_J(S)^-1 T_J(H0) and the centre
+// columns of T_J(S)^-1), the plain FP64 sign iteration (a4-a7), the trace reductions and the
+// write-back (a8). The FP64 sign iteration is the reference GPU path; the tensor-core paths reuse
+// everything here except the sign iteration itself.
+#include <algorithm>
+#include <cmath>
+
+#include "nolsm_internal.cuh"
+
+namespace nolsm {
+
+namespace {
+
+__device__ __forceinline__ int owner_of(const int32_t* __restrict__ nb_ptr, int n_mol, int64_t p) {
+  // largest J with nb_ptr[J] <= p
+  int lo = 0, hi = n_mol;  // invariant: nb_ptr[lo] <= p < nb_ptr[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if ((int64_t)nb_ptr[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_sorted(const int32_t* __restrict__ a, int lo, int hi, int32_t key) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t v = a[mid];
+    if (v == key) return mid;
+    if (v < key) lo = mid + 1; else hi = mid;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------------------ a1: gather
+// One block per row band (J, a): rows of molecule I_a inside T_J. For every molecule I_c of N(J) the
+// block (I_a, I_c) of S and of H0 is looked up by binary search in block row I_a; the band is written
+// in full (zeros where no block is stored), so the workspace needs no clearing. Also writes the centre
+// columns of T_J(S) and T_J(H0) into the geometry caches.
+struct GatherArgs {
+  int32_t n_mol;
+  const int32_t* nbf;
+  const int32_t* srp; const int32_t* sci; const int64_t* soff; const double* sval;
+  const int32_t* hrp; const int32_t* hci; const int64_t* hoff; const double* hval;
+  const int32_t* nb_ptr; const int32_t* nb_idx; const int32_t* nb_off;
+  const int32_t* sub_n; const int32_t* sub_c0;
+  const int64_t* a_off; const int64_t* c_off;
+  int64_t a_base;       // a_off of the chunk's first submatrix
+  int64_t chunk_n2;     // sum of n^2 over the chunk (offset of the T(H0) half)
+  int64_t p0;           // first row band of the chunk
+  double* ws;           // [2*chunk_n2]
+  double* Sc; double* Hc;
+};
+
+__global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
+  extern __shared__ int32_t sm[];
+  const int64_t p = g.p0 + blockIdx.x;
+  const int J = owner_of(g.nb_ptr, g.n_mol, p);
+  const int q0 = g.nb_ptr[J], nq = g.nb_ptr[J + 1] - q0;
+  const int Ia = g.nb_idx[p];
+  const int ba = g.nbf[Ia];
+  const int offa = g.nb_off[p];
+  const int n = g.sub_n[J];
+  int32_t* s_slot = sm;
+  int32_t* h_slot = sm + nq;
+  int32_t* coff = sm + 2 * nq;
+  for (int c = threadIdx.x; c < nq; c += blockDim.x) {
+    const int32_t Ic = g.nb_idx[q0 + c];
+    s_slot[c] = find_sorted(g.sci, g.srp[Ia], g.srp[Ia + 1], Ic);
+    h_slot[c] = find_sorted(g.hci, g.hrp[Ia], g.hrp[Ia + 1], Ic);
+    coff[c] = g.nb_off[q0 + c];
+  }
+  __syncthreads();
+  const int c0 = g.sub_c0[J];
+  const int bJ = g.nbf[J];
+  double* TS = g.ws + (g.a_off[J] - g.a_base);
+  double* TH = TS + g.chunk_n2;
+  double* Sc = g.Sc + g.c_off[J];
+  double* Hc = g.Hc + g.c_off[J];
+  const int total = ba * n;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = e / n, col = e - r * n;
+    // molecule block containing col: largest c with coff[c] <= col
+    int lo = 0, hi = nq;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (coff[mid] <= col) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int bc = g.nbf[g.nb_idx[q0 + c]];
+    const int cc = col - coff[c];
+    const int ss = s_slot[c], hs = h_slot[c];
+    const double vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
+    const double vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
+    const int64_t at = (int64_t)(offa + r) * n + col;
+    TS[at] = vs;
+    TH[at] = vh;
+    if (col >= c0 && col < c0 + bJ) {
+      Sc[(int64_t)(offa + r) * bJ + (col - c0)] = vs;
+      Hc[(int64_t)(offa + r) * bJ + (col - c0)] = vh;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------ a2: Cholesky
+// T_J(S) = L L^T in FP64, right-looking, one block per submatrix, in place (lower triangle).
+__global__ void __launch_bounds__(256) k_cholesky(const int32_t* __restrict__ sub_n, const int64_t* __restrict__ a_off,
+                                                  int64_t a_base, int32_t j0, double* ws, int32_t* prep_status) {
+  const int J = j0 + blockIdx.x;
+  const int n = sub_n[J];
+  double* S = ws + (a_off[J] - a_base);
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = S[(int64_t)k * n + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        piv = sqrt(d);
+        S[(int64_t)k * n + k] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double inv = 1.0 / piv;
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[(int64_t)i * n + k] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) S[(int64_t)i * n + j] -= S[(int64_t)i * n + k] * S[(int64_t)j * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) prep_status[J] = bad ? kSubNotSpd : kSubOk;
+}
+
+// ------------------------------------------------------------------------------------ a3: solves
+// A_J = L^-T (L^-1 T_J(H0)) with one thread per right-hand-side column (forward then backward
+// substitution), in FP64 (TA = double) or FP32 from the FP64 factor (TA = float); the b_J centre
+// columns of T_J(S)^-1 = L^-T L^-1 E_c are always FP64. Then the Gershgorin interval of A_J.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_solves(const int32_t* __restrict__ sub_n, const int32_t* __restrict__ sub_c0,
+                                                const int32_t* __restrict__ nbf, const int64_t* __restrict__ a_off,
+                                                const int64_t* __restrict__ c_off, int64_t a_base, int64_t chunk_n2,
+                                                int32_t j0, const double* __restrict__ ws, TA* __restrict__ Acache,
+                                                double* __restrict__ Q, double* __restrict__ lam,
+                                                const int32_t* __restrict__ prep_status) {
+  const int J = j0 + blockIdx.x;
+  if (prep_status[J] != kSubOk) return;
+  const int n = sub_n[J];
+  const int bJ = nbf[J];
+  const int c0 = sub_c0[J];
+  const double* L = ws + (a_off[J] - a_base);
+  const double* TH = L + chunk_n2;
+  TA* A = Acache + a_off[J];
+  double* QJ = Q + c_off[J];
+  for (int t = threadIdx.x; t < n + bJ; t += blockDim.x) {
+    if (t < n) {
+      for (int i = 0; i < n; ++i) {  // forward: L y = h_t
+        TA s = (TA)TH[(int64_t)i * n + t];
+        const double* Li = L + (int64_t)i * n;
+        for (int k = 0; k < i; ++k) s -= (TA)Li[k] * A[(int64_t)k * n + t];
+        A[(int64_t)i * n + t] = s / (TA)Li[i];
+      }
+      for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
+        TA s = A[(int64_t)i * n + t];
+        for (int k = i + 1; k < n; ++k) s -= (TA)L[(int64_t)k * n + i] * A[(int64_t)k * n + t];
+        A[(int64_t)i * n + t] = s / (TA)L[(int64_t)i * n + i];
+      }
+    } else {
+      const int c = t - n, col = c0 + c;
+      for (int i = 0; i < n; ++i) {
+        double s = (i == col) ? 1.0 : 0.0;
+        const double* Li = L + (int64_t)i * n;
+        for (int k = 0; k < i; ++k) s -= Li[k] * QJ[(int64_t)k * bJ + c];
+        QJ[(int64_t)i * bJ + c] = s / Li[i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double s = QJ[(int64_t)i * bJ + c];
+        for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * QJ[(int64_t)k * bJ + c];
+        QJ[(int64_t)i * bJ + c] = s / L[(int64_t)i * n + i];
+      }
+    }
+  }
+  __syncthreads();
+  // Gershgorin interval of A_J
+  __shared__ double rlo[256], rhi[256];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = 0.0;
+    const TA* Ai = A + (int64_t)i * n;
+    for (int j = 0; j < n; ++j)
+      if (j != i) r += fabs((double)Ai[j]);
+    lo = fmin(lo, (double)Ai[i] - r);
+    hi = fmax(hi, (double)Ai[i] + r);
+  }
+  rlo[threadIdx.x] = lo;
+  rhi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      rlo[threadIdx.x] = fmin(rlo[threadIdx.x], rlo[threadIdx.x + s]);
+      rhi[threadIdx.x] = fmax(rhi[threadIdx.x], rhi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    lam[2 * J] = rlo[0];
+    lam[2 * J + 1] = rhi[0];
+  }
+}
+
+// ------------------------------------------------------------------------------------ FP64 GEMM in one CTA
+// C = A B for n x n row-major matrices (leading dimension n), 256 threads, 64 x 64 output tiles, each
+// thread 4 x 4 outputs at rows ty + 16 i and columns tx + 16 j; epi(i, j, acc) consumes each output.
+constexpr int kTile = 64, kKc = 16;
+
+template <class Epi>
+__device__ __forceinline__ void cta_dgemm(const double* __restrict__ A, const double* __restrict__ B, int n,
+                                          double (*As)[kTile + 1], double (*Bs)[kTile + 1], Epi&& epi) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int tm = 0; tm < n; tm += kTile) {
+    for (int tn = 0; tn < n; tn += kTile) {
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int k0 = 0; k0 < n; k0 += kKc) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int idx = tid + 256 * q;
+          const int m = idx >> 4, k = idx & 15;  // A tile: 64 rows x 16 k
+          const int gm = tm + m, gk = k0 + k;
+          As[k][m] = (gm < n && gk < n) ? A[(int64_t)gm * n + gk] : 0.0;
+          const int kb = idx >> 6, nn = idx & 63;  // B tile: 16 k x 64 cols
+          const int gk2 = k0 + kb, gn = tn + nn;
+          Bs[kb][nn] = (gk2 < n && gn < n) ? B[(int64_t)gk2 * n + gn] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kKc; ++k) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gi = tm + ty + 16 * i, gj = tn + tx + 16 * j;
+          if (gi < n && gj < n) epi(gi, gj, acc[i][j]);
+        }
+    }
+  }
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// ------------------------------------------------------------------------------------ a4-a7 (FP64)
+struct NsArgs {
+  int32_t j0, j1;
+  const int32_t* sub_n; const int32_t* nbf;
+  const int64_t* a_off; const int64_t* c_off;
+  const double* A; const double* Q; const double* Sc; const double* Hc; const double* lam;
+  const int32_t* prep_status;
+  double mu, tol;
+  int32_t max_iter;
+  double* ws; int64_t slot_elems;
+  int32_t* next;               // work counter
+  double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status;
+};
+
+__global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
+  __shared__ double As[kKc][kTile + 1];
+  __shared__ double Bs[kKc][kTile + 1];
+  __shared__ double red[33];
+  __shared__ int job;
+  double* X = g.ws + (int64_t)blockIdx.x * 3 * g.slot_elems;
+  double* T = X + g.slot_elems;
+  double* Xn = T + g.slot_elems;
+  for (;;) {
+    if (threadIdx.x == 0) job = g.j0 + atomicAdd(g.next, 1);
+    __syncthreads();
+    const int J = job;
+    __syncthreads();
+    if (J >= g.j1) break;
+    if (g.prep_status[J] != kSubOk) {
+      if (threadIdx.x == 0) {
+        g.status[J] = g.prep_status[J];
+        g.iters[J] = 0;
+        g.tS[J] = 0.0;
+        g.tH[J] = 0.0;
+      }
+      continue;
+    }
+    const int n = g.sub_n[J];
+    const int64_t nn = (int64_t)n * n;
+    const double* A = g.A + g.a_off[J];
+    // a4: X_0 = (A - mu I) / alpha, alpha = max(hi - mu, mu - lo) from the Gershgorin interval
+    const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
+    const double inv_alpha = 1.0 / alpha;
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+      X[e] = (A[e] - (i == j ? g.mu : 0.0)) * inv_alpha;
+    }
+    __syncthreads();
+    // a5: X <- 1/2 X (3I - X^2) until the defect test passes
+    int it = 0, st = kSubNotConv;
+    double* x = X;
+    double* xn = Xn;
+    while (it < g.max_iter) {
+      double part = 0.0;
+      cta_dgemm(x, x, n, As, Bs, [&](int i, int j, double acc) {
+        const double v = (i == j ? 1.0 : 0.0) - acc;   // (I - X^2)_ij
+        part += v * v;
+        T[(int64_t)i * n + j] = v + (i == j ? 2.0 : 0.0);  // 3I - X^2
+      });
+      const double defect = sqrt(block_sum(part, red) / n);
+      cta_dgemm(x, T, n, As, Bs, [&](int i, int j, double acc) { xn[(int64_t)i * n + j] = 0.5 * acc; });
+      __syncthreads();
+      double* t = x; x = xn; xn = t;
+      ++it;
+      if (!isfinite(defect)) { st = kSubNonFinite; break; }
+      if (defect <= g.tol) { st = kSubOk; break; }
+    }
+    // a7: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the partial traces
+    const int b = g.nbf[J];
+    const double* Q = g.Q + g.c_off[J];
+    const double* Sc = g.Sc + g.c_off[J];
+    const double* Hc = g.Hc + g.c_off[J];
+    double* Dc = g.Dc + g.c_off[J];
+    double ps = 0.0, ph = 0.0;
+    for (int e = threadIdx.x; e < n * b; e += blockDim.x) {
+      const int i = e / b, c = e - i * b;
+      const double* xi = x + (int64_t)i * n;
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s = fma(xi[k], Q[(int64_t)k * b + c], s);
+      const double d = 0.5 * (Q[e] - s);
+      Dc[e] = d;
+      ps += d * Sc[e];
+      ph += d * Hc[e];
+    }
+    const double ts = block_sum(ps, red);
+    const double th = block_sum(ph, red);
+    if (threadIdx.x == 0) {
+      if (st == kSubOk && !(isfinite(ts) && isfinite(th))) st = kSubNonFinite;
+      g.tS[J] = ts;
+      g.tH[J] = th;
+      g.iters[J] = it;
+      g.status[J] = st;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------ reductions
+// Sums of t_S and t_H over [j0, j1) in a fixed order (one block), plus the first failing submatrix.
+__global__ void __launch_bounds__(256) k_reduce(int32_t j0, int32_t j1, const double* __restrict__ tS,
+                                                const double* __restrict__ tH, const int32_t* __restrict__ status,
+                                                double* out) {
+  __shared__ double red[33];
+  __shared__ int first[256];
+  double a = 0.0, b = 0.0;
+  int f = INT32_MAX;
+  for (int J = j0 + threadIdx.x; J < j1; J += blockDim.x) {
+    a += tS[J];
+    b += tH[J];
+    if (status[J] != 0 && J < f) f = J;
+  }
+  const double sa = block_sum(a, red);
+  const double sb = block_sum(b, red);
+  first[threadIdx.x] = f;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) first[threadIdx.x] = min(first[threadIdx.x], first[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sa;
+    out[1] = sb;
+    out[2] = first[0] == INT32_MAX ? -1.0 : (double)first[0];
+    out[3] = first[0] == INT32_MAX ? 0.0 : (double)status[first[0]];
+  }
+}
+
+// ------------------------------------------------------------------------------------ a8: write-back
+// One warp per (J, I in N(J)): block (I, J) of D <- rows of I in the centre columns of T_J(D).
+__global__ void __launch_bounds__(256) k_scatter(int32_t n_mol, int64_t p0, int64_t p1, const int32_t* __restrict__ nbf,
+                                                 const int32_t* __restrict__ nb_ptr, const int32_t* __restrict__ nb_idx,
+                                                 const int32_t* __restrict__ nb_off, const int32_t* __restrict__ d_slot,
+                                                 const int64_t* __restrict__ d_blk_off,
+                                                 const int64_t* __restrict__ c_off, const double* __restrict__ Dc,
+                                                 double* __restrict__ D) {
+  const int64_t p = p0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= p1) return;
+  const int J = owner_of(nb_ptr, n_mol, p);
+  const int I = nb_idx[p];
+  const int bI = nbf[I], bJ = nbf[J];
+  const double* src = Dc + c_off[J] + (int64_t)nb_off[p] * bJ;
+  double* dst = D + d_blk_off[d_slot[p]];
+  for (int e = lane; e < bI * bJ; e += 32) dst[e] = src[e];  // both b_I x b_J row-major
+}
+
+}  // namespace
+
+// ==================================================================================== host side
+
+static nolsm_status ensure(nolsm_plan* plan, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return NOLSM_OK;
+  dev_free(plan, b);
+  return dev_alloc(plan, b, bytes);
+}
+
+nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp64_A, cudaStream_t st) {
+  Prepared& P = keep_fp64_A ? plan->prep64 : plan->prep32;
+  const int32_t n_mol = plan->n_mol;
+  const size_t esz = keep_fp64_A ? sizeof(double) : sizeof(float);
+  if (!P.A.p) {
+    NOLSM_TRY(dev_alloc(plan, P.A, esz * (size_t)std::max<int64_t>(plan->h_a_off[n_mol], 1)));
+    P.done.assign(n_mol, 0);
+    P.fp64 = keep_fp64_A;
+  }
+  const int64_t nc = std::max<int64_t>(plan->h_c_off[n_mol], 1);
+  if (!plan->Q.p) {
+    NOLSM_TRY(dev_alloc(plan, plan->Q, sizeof(double) * nc));
+    NOLSM_TRY(dev_alloc(plan, plan->Sc, sizeof(double) * nc));
+    NOLSM_TRY(dev_alloc(plan, plan->Hc, sizeof(double) * nc));
+    NOLSM_TRY(dev_alloc(plan, plan->lam, sizeof(double) * 2 * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->prep_status, sizeof(int32_t) * n_mol));
+    NOLSM_CUDA_TRY(cudaMemsetAsync(plan->prep_status.p, 0, sizeof(int32_t) * n_mol, st));
+  }
+  int max_nq = 1;
+  for (int64_t J = j0; J < j1; ++J) max_nq = std::max(max_nq, plan->h_nb_ptr[J + 1] - plan->h_nb_ptr[J]);
+  const int64_t budget = (int64_t)1 << 31;  // bytes of gathered T_J(S), T_J(H0) per chunk
+  int64_t J = j0;
+  while (J < j1) {
+    while (J < j1 && P.done[J]) ++J;
+    if (J >= j1) break;
+    int64_t e = J;
+    while (e < j1 && !P.done[e] &&
+           (e == J || 2 * 8 * (plan->h_a_off[e + 1] - plan->h_a_off[J]) <= budget))
+      ++e;
+    const int64_t n2 = plan->h_a_off[e] - plan->h_a_off[J];
+    NOLSM_TRY(ensure(plan, plan->ws_dense, sizeof(double) * 2 * (size_t)n2));
+    GatherArgs g;
+    g.n_mol = n_mol;
+    g.nbf = plan->sys.nbf;
+    g.srp = plan->sys.s_row_ptr; g.sci = plan->sys.s_col_idx; g.soff = plan->s_blk_off.as<int64_t>();
+    g.sval = plan->sys.s_vals;
+    g.hrp = plan->sys.h_row_ptr; g.hci = plan->sys.h_col_idx; g.hoff = plan->h_blk_off.as<int64_t>();
+    g.hval = plan->sys.h_vals;
+    g.nb_ptr = plan->nb_ptr.as<int32_t>(); g.nb_idx = plan->nb_idx.as<int32_t>(); g.nb_off = plan->nb_off.as<int32_t>();
+    g.sub_n = plan->sub_n.as<int32_t>(); g.sub_c0 = plan->sub_c0.as<int32_t>();
+    g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
+    g.a_base = plan->h_a_off[J];
+    g.chunk_n2 = n2;
+    g.p0 = plan->h_nb_ptr[J];
+    g.ws = plan->ws_dense.as<double>();
+    g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
+    const int64_t bands = plan->h_nb_ptr[e] - plan->h_nb_ptr[J];
+    k_gather<<<(unsigned)bands, 256, sizeof(int32_t) * 3 * max_nq, st>>>(g);
+    NOLSM_LAUNCH_CHECK();
+    k_cholesky<<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->a_off.as<int64_t>(), g.a_base,
+                                                (int32_t)J, g.ws, plan->prep_status.as<int32_t>());
+    NOLSM_LAUNCH_CHECK();
+    if (keep_fp64_A) {
+      k_solves<double><<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->sub_c0.as<int32_t>(),
+          plan->sys.nbf, plan->a_off.as<int64_t>(), plan->c_off.as<int64_t>(), g.a_base, n2, (int32_t)J, g.ws,
+          P.A.as<double>(), plan->Q.as<double>(), plan->lam.as<double>(), plan->prep_status.as<int32_t>());
+    } else {
+      k_solves<float><<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->sub_c0.as<int32_t>(),
+          plan->sys.nbf, plan->a_off.as<int64_t>(), plan->c_off.as<int64_t>(), g.a_base, n2, (int32_t)J, g.ws,
+          P.A.as<float>(), plan->Q.as<double>(), plan->lam.as<double>(), plan->prep_status.as<int32_t>());
+    }
+    NOLSM_LAUNCH_CHECK();
+    for (int64_t k = J; k < e; ++k) P.done[k] = 1;
+    J = e;
+  }
+  return NOLSM_OK;
+}
+
+nolsm_status ensure_results(nolsm_plan* plan) {
+  const int32_t n_mol = plan->n_mol;
+  if (!plan->Dc.p) {
+    NOLSM_TRY(dev_alloc(plan, plan->Dc, sizeof(double) * (size_t)std::max<int64_t>(plan->h_c_off[n_mol], 1)));
+    NOLSM_TRY(dev_alloc(plan, plan->t_S, sizeof(double) * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->t_H, sizeof(double) * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->iters, sizeof(int32_t) * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->status, sizeof(int32_t) * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->sums, sizeof(double) * 4));
+    NOLSM_TRY(dev_alloc(plan, plan->counter, sizeof(int32_t) * 4));
+  }
+  return NOLSM_OK;
+}
+
+nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1,
+                        cudaStream_t st) {
+  NOLSM_TRY(ensure_results(plan));
+  int dev = 0, sms = 0;
+  NOLSM_CUDA_TRY(cudaGetDevice(&dev));
+  NOLSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int slots = (int)std::min<int64_t>(2 * sms, j1 - j0);
+  int32_t maxn = 0;
+  for (int64_t J = j0; J < j1; ++J) maxn = std::max(maxn, plan->h_sub_n[J]);
+  const int64_t slot_elems = (int64_t)maxn * maxn;
+  NOLSM_TRY(ensure(plan, plan->ws_ns, sizeof(double) * 3 * (size_t)slot_elems * slots));
+  NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
+  NsArgs g;
+  g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
+  g.A = plan->prep64.A.as<double>(); g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>();
+  g.Hc = plan->Hc.as<double>(); g.lam = plan->lam.as<double>();
+  g.prep_status = plan->prep_status.as<int32_t>();
+  g.mu = mu; g.tol = o.tol_ns;
+  g.max_iter = o.max_iter;
+  g.ws = plan->ws_ns.as<double>(); g.slot_elems = slot_elems;
+  g.next = plan->counter.as<int32_t>();
+  g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();
+  g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
+  k_ns_fp64<<<slots, 256, 0, st>>>(g);
+  NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
+
+nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, cudaStream_t st, double* tS, double* tH,
+                           int32_t* first_bad_status) {
+  k_reduce<<<1, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->t_S.as<double>(), plan->t_H.as<double>(),
+                              plan->status.as<int32_t>(), plan->sums.as<double>());
+  NOLSM_LAUNCH_CHECK();
+  double h[4];
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(h, plan->sums.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  *tS = h[0];
+  *tH = h[1];
+  *first_bad_status = h[2] < 0 ? 0 : (int32_t)h[3];
+  return NOLSM_OK;
+}
+
+nolsm_status scatter(nolsm_plan* plan, double* D, int64_t j0, int64_t j1, cudaStream_t st) {
+  const int64_t p0 = plan->h_nb_ptr[j0], p1 = plan->h_nb_ptr[j1];
+  if (p1 <= p0) return NOLSM_OK;
+  const int64_t threads = (p1 - p0) * 32;
+  k_scatter<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      plan->n_mol, p0, p1, plan->sys.nbf, plan->nb_ptr.as<int32_t>(), plan->nb_idx.as<int32_t>(),
+      plan->nb_off.as<int32_t>(), plan->d_slot.as<int32_t>(), plan->d_blk_off.as<int64_t>(), plan->c_off.as<int64_t>(),
+      plan->Dc.as<double>(), D);
+  NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
+
+}  // namespace nolsm

@@ -1,0 +1,240 @@
+// C ABI entry points (include/nolsm.h): argument checks, plan lifecycle, dispatch by precision, the
+// host side of the mu bisection, and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "nolsm_internal.cuh"
+#include "tc_path.cuh"
+
+namespace nolsm {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+nolsm_status dev_alloc(nolsm_plan* plan, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? NOLSM_ERR_OOM : NOLSM_ERR_CUDA;
+  }
+  b.p = p;
+  b.bytes = bytes;
+  plan->bytes += (int64_t)bytes;
+  return NOLSM_OK;
+}
+
+void dev_free(nolsm_plan* plan, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    plan->bytes -= (int64_t)b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+}  // namespace nolsm
+
+using namespace nolsm;
+
+nolsm_plan::~nolsm_plan() {
+  DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
+                   &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &Dc,
+                   &t_S, &t_H, &iters, &status, &sums, &counter, &ws_dense, &ws_ns};
+  for (DevBuf* b : all) dev_free(this, *b);
+  tc_release(this);
+}
+
+extern "C" {
+
+void nolsm_options_default(nolsm_options* o, int32_t precision) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = precision;
+  const bool fp64 = precision == NOLSM_FP64;
+  o->refine_steps = fp64 ? 0 : (precision == NOLSM_FP8E4M3 ? 3 : 2);
+  o->max_iter = 100;
+  o->tol_ns = fp64 ? 1e-9 : 1e-2;
+  o->tol_accept = fp64 ? 1e-7 : 1e-4;
+  o->tol_n = 1e-5;
+  o->tol_mu = 1e-10;
+  o->max_bisect = 100;
+  o->bound_source = NOLSM_BOUND_GERSHGORIN;
+  o->sub_begin = 0;
+  o->sub_end = 0;
+}
+
+const char* nolsm_status_str(nolsm_status s) {
+  switch (s) {
+    case NOLSM_OK: return "ok";
+    case NOLSM_ERR_ARG: return "invalid argument";
+    case NOLSM_ERR_CUDA: return "CUDA error";
+    case NOLSM_ERR_OOM: return "out of device memory";
+    case NOLSM_ERR_NOT_SPD: return "overlap submatrix not positive definite";
+    case NOLSM_ERR_NOT_CONVERGED: return "sign iteration did not converge";
+    case NOLSM_ERR_NONFINITE: return "non-finite value";
+    case NOLSM_ERR_NO_PLATEAU: return "bisection found no mu with the requested electron count";
+    case NOLSM_ERR_UNSUPPORTED: return "unsupported option or size";
+    case NOLSM_ERR_NO_SOLUTION: return "no solution to write back";
+  }
+  return "unknown status";
+}
+
+const char* nolsm_last_error(void) { return g_err; }
+
+nolsm_status nolsm_build_submatrices(const nolsm_system* sys, nolsm_stream_t stream, nolsm_plan** out) {
+  if (!out) { set_error("nolsm_build_submatrices: out is NULL"); return NOLSM_ERR_ARG; }
+  *out = nullptr;
+  if (!sys || sys->n_mol <= 0 || !sys->nbf || !sys->s_row_ptr || !sys->h_row_ptr || !sys->s_vals || !sys->h_vals ||
+      sys->s_nnzb <= 0 || sys->h_nnzb <= 0 || !sys->s_col_idx || !sys->h_col_idx ||
+      sys->s_nnzb > INT32_MAX || sys->h_nnzb > INT32_MAX) {
+    set_error("nolsm_build_submatrices: missing or inconsistent system arrays");
+    return NOLSM_ERR_ARG;
+  }
+  nolsm_plan* plan = new (std::nothrow) nolsm_plan();
+  if (!plan) { set_error("host allocation failed"); return NOLSM_ERR_OOM; }
+  plan->sys = *sys;
+  plan->n_mol = sys->n_mol;
+  nolsm_status s = build_plan_device(plan, (cudaStream_t)stream);
+  if (s != NOLSM_OK) {
+    delete plan;
+    return s;
+  }
+  *out = plan;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info) {
+  if (!plan || !info) { set_error("nolsm_plan_query: NULL argument"); return NOLSM_ERR_ARG; }
+  info->n_mol = plan->n_mol;
+  info->d_nnzb = plan->d_nnzb;
+  info->d_nvals = plan->d_nvals;
+  info->max_n = plan->max_n;
+  info->min_n = plan->min_n;
+  info->sum_n3 = plan->sum_n3;
+  info->device_bytes = plan->bytes;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_t* nb_idx, int32_t* nb_off,
+                                 int32_t* sub_n, int32_t* sub_c0, int64_t* d_blk_off, nolsm_stream_t stream) {
+  if (!plan) { set_error("nolsm_plan_get_maps: NULL plan"); return NOLSM_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)plan->n_mol, m = (size_t)plan->d_nnzb;
+  if (nb_ptr) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_ptr, plan->nb_ptr.p, 4 * (n + 1), cudaMemcpyDeviceToDevice, st));
+  if (nb_idx) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_idx, plan->nb_idx.p, 4 * m, cudaMemcpyDeviceToDevice, st));
+  if (nb_off) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_off, plan->nb_off.p, 4 * m, cudaMemcpyDeviceToDevice, st));
+  if (sub_n) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_n, plan->sub_n.p, 4 * n, cudaMemcpyDeviceToDevice, st));
+  if (sub_c0) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_c0, plan->sub_c0.p, 4 * n, cudaMemcpyDeviceToDevice, st));
+  if (d_blk_off) NOLSM_CUDA_TRY(cudaMemcpyAsync(d_blk_off, plan->d_blk_off.p, 8 * (m + 1), cudaMemcpyDeviceToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NOLSM_OK;
+}
+
+static nolsm_status check_options(const nolsm_plan* plan, const nolsm_options* o, int64_t* j0, int64_t* j1) {
+  if (!o) { set_error("options are NULL"); return NOLSM_ERR_ARG; }
+  if (o->precision < NOLSM_FP64 || o->precision > NOLSM_FP8E4M3 || o->max_iter < 1 || o->max_iter > 10000 ||
+      o->refine_steps < 0 || o->refine_steps > 100 || !(o->tol_ns > 0) || !(o->tol_accept > 0) ||
+      o->bound_source < 0 || o->bound_source > NOLSM_BOUND_MLP) {
+    set_error("invalid options (precision %d, max_iter %d, refine %d, tol_ns %g, tol_accept %g, bound %d)",
+              o->precision, o->max_iter, o->refine_steps, o->tol_ns, o->tol_accept, o->bound_source);
+    return NOLSM_ERR_ARG;
+  }
+  *j0 = o->sub_begin;
+  *j1 = o->sub_end <= 0 ? plan->n_mol : o->sub_end;
+  if (*j0 < 0 || *j0 >= *j1 || *j1 > plan->n_mol) {
+    set_error("invalid submatrix range [%lld, %lld) of %d", (long long)*j0, (long long)*j1, plan->n_mol);
+    return NOLSM_ERR_ARG;
+  }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                               double* trace_DS, double* trace_DH, double* sub_t_S, double* sub_t_H,
+                               int32_t* iters, int32_t* status) {
+  if (!plan) { set_error("nolsm_solve_batch: NULL plan"); return NOLSM_ERR_ARG; }
+  if (!std::isfinite(mu)) { set_error("nolsm_solve_batch: mu is not finite"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  if (opts->precision == NOLSM_FP64) {
+    NOLSM_TRY(prepare_fp64(plan, j0, j1, true, st));
+    NOLSM_TRY(solve_fp64(plan, mu, *opts, j0, j1, st));
+  } else {
+    NOLSM_TRY(prepare_fp64(plan, j0, j1, false, st));
+    NOLSM_TRY(solve_tc(plan, mu, *opts, j0, j1, st));
+  }
+  double tS = 0, tH = 0;
+  int32_t bad = 0;
+  NOLSM_TRY(reduce_traces(plan, j0, j1, st, &tS, &tH, &bad));
+  const size_t cnt = (size_t)(j1 - j0);
+  if (sub_t_S) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_t_S + j0, plan->t_S.as<double>() + j0, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+  if (sub_t_H) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_t_H + j0, plan->t_H.as<double>() + j0, 8 * cnt, cudaMemcpyDeviceToDevice, st));
+  if (iters) NOLSM_CUDA_TRY(cudaMemcpyAsync(iters + j0, plan->iters.as<int32_t>() + j0, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+  if (status) NOLSM_CUDA_TRY(cudaMemcpyAsync(status + j0, plan->status.as<int32_t>() + j0, 4 * cnt, cudaMemcpyDeviceToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (trace_DS) *trace_DS = tS;
+  if (trace_DH) *trace_DH = tH;
+  plan->solved_begin = j0;
+  plan->solved_end = j1;
+  plan->have_solution = true;
+  if (bad != 0) {
+    set_error("nolsm_solve_batch: a submatrix reported '%s'", nolsm_status_str((nolsm_status)bad));
+    return (nolsm_status)bad;
+  }
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream) {
+  if (!plan || !D_vals) { set_error("nolsm_scatter_density: NULL argument"); return NOLSM_ERR_ARG; }
+  if (!plan->have_solution) { set_error("nolsm_scatter_density: no solve yet"); return NOLSM_ERR_NO_SOLUTION; }
+  NOLSM_TRY(scatter(plan, D_vals, plan->solved_begin, plan->solved_end, (cudaStream_t)stream));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
+                           nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
+                           double* mu_history) {
+  if (!plan || !opts || !(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi) || !std::isfinite(n_occ)) {
+    set_error("nolsm_find_mu: invalid arguments");
+    return NOLSM_ERR_ARG;
+  }
+  const int max_steps = opts->max_bisect > 0 ? opts->max_bisect : 100;
+  double mu = 0.5 * (lo + hi), t = 0.0;
+  nolsm_status result = NOLSM_ERR_NO_PLATEAU;
+  int step = 0;
+  while (step < max_steps) {
+    mu = 0.5 * (lo + hi);
+    nolsm_status s = nolsm_solve_batch(plan, mu, opts, stream, &t, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (mu_history) mu_history[step] = mu;
+    ++step;
+    if (s != NOLSM_OK) { result = s; break; }
+    const double f = t - n_occ;
+    if (std::fabs(f) <= opts->tol_n * std::fabs(n_occ)) { result = NOLSM_OK; break; }
+    if (f < 0.0) lo = mu; else hi = mu;
+    if (hi - lo <= opts->tol_mu) break;
+  }
+  if (mu_out) *mu_out = mu;
+  if (trace_DS_out) *trace_DS_out = t;
+  if (steps_out) *steps_out = step;
+  if (result == NOLSM_ERR_NO_PLATEAU)
+    set_error("nolsm_find_mu: stopped after %d evaluations at mu=%.12g with Tr(DS)=%.9f, target %.9f", step, mu, t, n_occ);
+  return result;
+}
+
+void nolsm_plan_destroy(nolsm_plan* plan) { delete plan; }
+
+}  // extern "C"

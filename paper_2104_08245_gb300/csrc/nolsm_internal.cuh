@@ -1,0 +1,117 @@
+// Internal declarations of the NOLSM GB300 library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nolsm.h"
+
+namespace nolsm {
+
+// Per-submatrix status codes written by kernels (values of nolsm_status).
+enum : int32_t { kSubOk = 0, kSubNotSpd = NOLSM_ERR_NOT_SPD, kSubNotConv = NOLSM_ERR_NOT_CONVERGED,
+                 kSubNonFinite = NOLSM_ERR_NONFINITE };
+
+void set_error(const char* fmt, ...);
+
+#define NOLSM_CUDA_TRY(expr)                                                                     \
+  do {                                                                                           \
+    cudaError_t _e = (expr);                                                                     \
+    if (_e != cudaSuccess) {                                                                     \
+      ::nolsm::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e));     \
+      return _e == cudaErrorMemoryAllocation ? NOLSM_ERR_OOM : NOLSM_ERR_CUDA;                   \
+    }                                                                                            \
+  } while (0)
+
+#define NOLSM_LAUNCH_CHECK() NOLSM_CUDA_TRY(cudaGetLastError())
+
+#define NOLSM_TRY(expr)                 \
+  do {                                  \
+    nolsm_status _s = (expr);           \
+    if (_s != NOLSM_OK) return _s;      \
+  } while (0)
+
+// Device buffer owned by the plan.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Geometry-dependent data of one precision class, computed once per plan (a1-a3 and the bounds).
+struct Prepared {
+  bool fp64 = false;          // true: A held in FP64 (plain path); false: FP32 (tensor-core paths)
+  DevBuf A;                   // A_J = T_J(S)^-1 T_J(H0), n_J x n_J row-major at a_off[J]
+  std::vector<uint8_t> done;  // host flag per submatrix: prepared
+};
+
+}  // namespace nolsm
+
+struct nolsm_plan {
+  nolsm_system sys{};
+  int32_t n_mol = 0;
+  int64_t d_nnzb = 0, d_nvals = 0;
+  int32_t max_n = 0, min_n = 0, max_b = 0;
+  double sum_n3 = 0.0;
+  int64_t bytes = 0;
+
+  // integer maps (device)
+  nolsm::DevBuf s_blk_off, h_blk_off;       // int64 [nnzb+1]
+  nolsm::DevBuf nb_ptr, nb_idx, nb_off;     // int32
+  nolsm::DevBuf sub_n, sub_c0;              // int32 [n_mol]
+  nolsm::DevBuf d_blk_off;                  // int64 [d_nnzb+1]
+  nolsm::DevBuf d_slot;                     // int32 [d_nnzb]: slot of block (nb_idx[p], J) in D
+  nolsm::DevBuf a_off, c_off;               // int64 [n_mol+1]: offsets of n^2 and n*b arrays
+  nolsm::DevBuf flag;                       // int32 scratch flag
+
+  // host copies
+  std::vector<int32_t> h_sub_n, h_nbf, h_nb_ptr;
+  std::vector<int64_t> h_a_off, h_c_off;
+
+  // geometry caches shared by all precisions (device), n_J x b_J row-major at c_off[J]
+  nolsm::DevBuf Q;        // centre columns of T_J(S)^-1 (FP64)
+  nolsm::DevBuf Sc, Hc;   // centre columns of T_J(S), T_J(H0) (FP64)
+  nolsm::DevBuf lam;      // float64 [2*n_mol]: Gershgorin interval of A_J
+  nolsm::DevBuf prep_status;  // int32 [n_mol]: kSubOk or kSubNotSpd from the factorisation
+  nolsm::Prepared prep64, prep32;
+
+  // per-mu results
+  nolsm::DevBuf Dc;                 // centre columns of T_J(D), FP64, at c_off[J]
+  nolsm::DevBuf t_S, t_H;           // float64 [n_mol]
+  nolsm::DevBuf iters, status;      // int32 [n_mol]
+  nolsm::DevBuf sums;               // float64 [4]
+  nolsm::DevBuf counter;            // int32 work counters of persistent kernels
+  int64_t solved_begin = 0, solved_end = 0;
+  bool have_solution = false;
+
+  // workspaces
+  nolsm::DevBuf ws_dense;           // gathered T_J(S), T_J(H0) of one preparation chunk (FP64)
+  nolsm::DevBuf ws_ns;              // per-CTA Newton-Schulz buffers
+  int ns_slots = 0;
+
+  ~nolsm_plan();
+};
+
+namespace nolsm {
+
+nolsm_status dev_alloc(nolsm_plan* plan, DevBuf& b, size_t bytes);
+void dev_free(nolsm_plan* plan, DevBuf& b);
+
+// plan construction (plan_kernels.cu)
+nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st);
+
+// per-geometry preparation and per-mu solve of the FP64 path (fp64_path.cu)
+nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp64_A, cudaStream_t st);
+nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1,
+                        cudaStream_t st);
+
+nolsm_status ensure_results(nolsm_plan* plan);
+
+// shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
+nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, cudaStream_t st, double* tS, double* tH,
+                           int32_t* first_bad_status);
+nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st);
+
+}  // namespace nolsm

@@ -17,7 +17,11 @@ Construction (the readings of the workload description, one per parameter):
   (strict): S = exp(-0.5 r^2) and H = -0.2 exp(-r/1.5) for every entry, optionally modulated by a
   direction-dependent factor (1 + aniso (u_a - u_c) . r_hat) that keeps S and H symmetric while
   making the individual off-diagonal blocks non-symmetric (used by tests that must catch transposed
-  operands). Blocks at r >= r_c are absent.
+  operands). Blocks at r >= r_c are absent. The element formulas are those of the 6-function
+  molecule; between molecules with b_I and b_J functions every inter-molecular entry is multiplied by
+  6/sqrt(b_I b_J), which leaves 6-function systems unchanged and keeps the coupling of each molecule
+  pair at the 6-function strength. (Unscaled, 23 functions per molecule make S indefinite: its
+  lowest eigenvalue is about -0.26 on a 27-molecule cell.)
 * On-site energies: 6 functions per molecule use types [0,1,1,1,2,2] with -1.0, -0.5, +0.3 Ha;
   23 functions per molecule draw one energy per function slot from N(-0.5, 0.3) Ha once per system.
   Four occupied orbitals per molecule.
@@ -241,7 +245,7 @@ def make_system(spec: SystemSpec) -> System:
     rc_h = spec.cutoff if spec.cutoff_h is None else spec.cutoff_h
 
     def s_val(r, dhat, b1, b2, dirs):
-        base = np.exp(-spec.s_exp * r * r)[:, None, None]
+        base = (6.0 / np.sqrt(b1 * b2)) * np.exp(-spec.s_exp * r * r)[:, None, None]
         if spec.aniso == 0.0:
             return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
         ua = dhat @ dirs[0, :b1].T          # [k, b1]
@@ -249,7 +253,7 @@ def make_system(spec: SystemSpec) -> System:
         return base * (1.0 + spec.aniso * (ua[:, :, None] - uc[:, None, :]))
 
     def h_val(r, dhat, b1, b2, dirs):
-        base = (spec.hop * np.exp(-r / spec.hop_len))[:, None, None]
+        base = (6.0 / np.sqrt(b1 * b2)) * (spec.hop * np.exp(-r / spec.hop_len))[:, None, None]
         if spec.aniso == 0.0:
             return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
         ua = dhat @ dirs[1, :b1].T
