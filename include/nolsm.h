@@ -45,7 +45,8 @@ typedef enum {
   NOLSM_ERR_NONFINITE = 6,     /* NaN/Inf met in some submatrix */
   NOLSM_ERR_NO_PLATEAU = 7,    /* find_mu: bracket narrowed below tol_mu with |Tr(DS)-N| > tol_n */
   NOLSM_ERR_UNSUPPORTED = 8,   /* option combination or size this build does not handle */
-  NOLSM_ERR_NO_SOLUTION = 9    /* scatter_density called before any solve_batch */
+  NOLSM_ERR_NO_SOLUTION = 9,   /* scatter_density called before any solve_batch */
+  NOLSM_ERR_TIMEOUT = 10       /* a bounded device-side wait gave up (the kernel returned early) */
 } nolsm_status;
 
 /* Arithmetic of the sign-iteration products (a5/a6). The overlap factorisation, the centre columns of
@@ -82,7 +83,7 @@ typedef enum {
  * them is destroyed. */
 typedef struct {
   int32_t n_mol;
-  const int32_t* nbf;       /* (device) [n_mol], basis functions per molecule, 1..32 */
+  const int32_t* nbf;       /* (device) [n_mol], basis functions per molecule, 1..64 */
   int64_t s_nnzb;
   const int32_t* s_row_ptr; /* (device) [n_mol+1] */
   const int32_t* s_col_idx; /* (device) [s_nnzb] */
@@ -169,12 +170,41 @@ nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_strea
 /* a9: chemical potential by bisection (Sec. "Simulation Details"): f(mu) = Tr(DS) - n_occ with
  * Tr(DS) from nolsm_solve_batch over the options' range; mu = (lo+hi)/2; f < 0 raises lo, otherwise
  * hi is lowered; stops at the first |f| <= tol_n * n_occ (NOLSM_OK), when hi - lo <= tol_mu
- * (NOLSM_ERR_NO_PLATEAU) or after max_bisect evaluations (NOLSM_ERR_NO_PLATEAU). The plan keeps the
- * solution at the returned mu for nolsm_scatter_density. mu_history (host, may be NULL) receives up
+ * (NOLSM_ERR_NO_PLATEAU) or after max_bisect evaluations (NOLSM_ERR_NO_PLATEAU). If lo >= hi the
+ * bracket is the union of the Gershgorin intervals of all A_J in the range (prepared first). The plan
+ * keeps the solution at the returned mu for nolsm_scatter_density. mu_history (host, may be NULL) receives up
  * to max_bisect evaluated mu values. */
 nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
                            nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
                            double* mu_history);
+
+/* The union [lo, hi] of the Gershgorin intervals of A_J = T_J(S)^-1 T_J(H0) over the options' range
+ * of submatrices (prepares a1-a3 for the range first): a bracket of every submatrix eigenvalue, used
+ * as the default bisection bracket (Sec. "Simulation Details" gives no bracket). lo, hi: host. */
+nolsm_status nolsm_spectral_bracket(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, double* lo,
+                                    double* hi);
+
+/* Accumulated per-phase device times (CUDA events on the caller's stream) and work counters of a
+ * plan since it was built or last reset; no paper counterpart (the paper times the whole method and
+ * counts 2 n^3 per product, Sec. "FLOPs in the NOLSM method"). */
+typedef struct {
+  double ms_plan;              /* a0 */
+  double ms_prepare;           /* a1-a3: gather, FP64 Cholesky, solves, bounds */
+  double ms_sign;              /* a4-a7: the sign-iteration kernel (all solve_batch calls) */
+  double ms_reduce;            /* trace sums */
+  double ms_scatter;           /* a8 */
+  int64_t solves;              /* nolsm_solve_batch calls */
+  int64_t sub_solves;          /* submatrices solved, summed over calls */
+  int64_t ns_steps;            /* Newton-Schulz steps, summed over submatrices and calls */
+  double flops_paper;          /* 4 n^3 per Newton-Schulz step on the unpadded n (2 n^3 per product) */
+  double flops_tensor;         /* tensor-core flops the products need (x3 for split steps), unpadded n */
+  double flops_tensor_padded;  /* same on the padded tile shapes the kernel executes */
+  double flops_fp64;           /* FP64 flops of the factorisation and solves (a2, a3) */
+  int64_t launches;            /* kernels launched for this plan */
+} nolsm_stats;
+
+nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);
+nolsm_status nolsm_plan_stats_reset(nolsm_plan* plan);
 
 void nolsm_plan_destroy(nolsm_plan* plan);
 const char* nolsm_status_str(nolsm_status s);

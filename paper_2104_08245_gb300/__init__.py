@@ -13,11 +13,12 @@ from typing import Optional
 
 from . import _abi
 from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP32, FP64,  # noqa: F401
-                   PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmSystem)
+                   PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmStats, NolsmSystem)
 
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
-           "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "options", "NolsmError", "Plan",
-           "SolveResult", "MuResult"]
+           "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
+           "nolsm_spectral_bracket",
+           "options", "NolsmError", "Plan", "SolveResult", "MuResult"]
 
 
 class NolsmError(RuntimeError):
@@ -122,6 +123,29 @@ def nolsm_plan_get_maps(plan: "Plan", stream=None) -> dict:
     return out
 
 
+def nolsm_spectral_bracket(plan: "Plan", opts: NolsmOptions, stream=None):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    rc = _abi.load().nolsm_spectral_bracket(plan.handle, ctypes.byref(opts), _stream(stream), ctypes.byref(lo),
+                                            ctypes.byref(hi))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_spectral_bracket")
+    return lo.value, hi.value
+
+
+def nolsm_plan_stats(plan: "Plan") -> dict:
+    st = NolsmStats()
+    rc = _abi.load().nolsm_plan_stats(plan.handle, ctypes.byref(st))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_stats")
+    return st.as_dict()
+
+
+def nolsm_plan_stats_reset(plan: "Plan") -> None:
+    rc = _abi.load().nolsm_plan_stats_reset(plan.handle)
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_stats_reset")
+
+
 @dataclasses.dataclass
 class SolveResult:
     status: int
@@ -221,3 +245,9 @@ class Plan:
 
     def find_mu(self, n_occ, lo, hi, opts, **kw):
         return nolsm_find_mu(self, n_occ, lo, hi, opts, **kw)
+
+    def stats(self):
+        return nolsm_plan_stats(self)
+
+    def stats_reset(self):
+        nolsm_plan_stats_reset(self)

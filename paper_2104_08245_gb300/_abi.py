@@ -10,7 +10,7 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 
 # nolsm_status
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_NO_PLATEAU, \
-    ERR_UNSUPPORTED, ERR_NO_SOLUTION = range(10)
+    ERR_UNSUPPORTED, ERR_NO_SOLUTION, ERR_TIMEOUT = range(11)
 # nolsm_precision
 FP64, FP32, BF16, BF16X3, FP8E4M3 = range(5)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8e4m3": FP8E4M3}
@@ -35,6 +35,16 @@ class NolsmPlanInfo(ctypes.Structure):
                 ("min_n", c_int32), ("sum_n3", c_double), ("device_bytes", c_int64)]
 
 
+class NolsmStats(ctypes.Structure):
+    _fields_ = [("ms_plan", c_double), ("ms_prepare", c_double), ("ms_sign", c_double), ("ms_reduce", c_double),
+                ("ms_scatter", c_double), ("solves", c_int64), ("sub_solves", c_int64), ("ns_steps", c_int64),
+                ("flops_paper", c_double), ("flops_tensor", c_double), ("flops_tensor_padded", c_double),
+                ("flops_fp64", c_double), ("launches", c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # (name, restype, argtypes) of every entry point of include/nolsm.h
 SIGNATURES = [
     ("nolsm_options_default", None, [ctypes.POINTER(NolsmOptions), c_int32]),
@@ -49,6 +59,10 @@ SIGNATURES = [
     ("nolsm_find_mu", c_int32, [c_void_p, c_double, c_double, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
                                 ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int32),
                                 ctypes.POINTER(c_double)]),
+    ("nolsm_spectral_bracket", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p,
+                                         ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    ("nolsm_plan_stats", c_int32, [c_void_p, ctypes.POINTER(NolsmStats)]),
+    ("nolsm_plan_stats_reset", c_int32, [c_void_p]),
     ("nolsm_plan_destroy", None, [c_void_p]),
     ("nolsm_status_str", ctypes.c_char_p, [c_int32]),
     ("nolsm_last_error", ctypes.c_char_p, []),

@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "nolsm_internal.cuh"
+#include "prep.cuh"
 
 namespace nolsm {
 
@@ -101,118 +102,6 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
   }
 }
 
-// ------------------------------------------------------------------------------------ a2: Cholesky
-// T_J(S) = L L^T in FP64, right-looking, one block per submatrix, in place (lower triangle).
-__global__ void __launch_bounds__(256) k_cholesky(const int32_t* __restrict__ sub_n, const int64_t* __restrict__ a_off,
-                                                  int64_t a_base, int32_t j0, double* ws, int32_t* prep_status) {
-  const int J = j0 + blockIdx.x;
-  const int n = sub_n[J];
-  double* S = ws + (a_off[J] - a_base);
-  __shared__ double piv;
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = S[(int64_t)k * n + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-      } else {
-        piv = sqrt(d);
-        S[(int64_t)k * n + k] = piv;
-      }
-    }
-    __syncthreads();
-    if (bad) break;
-    const double inv = 1.0 / piv;
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[(int64_t)i * n + k] *= inv;
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) S[(int64_t)i * n + j] -= S[(int64_t)i * n + k] * S[(int64_t)j * n + k];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) prep_status[J] = bad ? kSubNotSpd : kSubOk;
-}
-
-// ------------------------------------------------------------------------------------ a3: solves
-// A_J = L^-T (L^-1 T_J(H0)) with one thread per right-hand-side column (forward then backward
-// substitution), in FP64 (TA = double) or FP32 from the FP64 factor (TA = float); the b_J centre
-// columns of T_J(S)^-1 = L^-T L^-1 E_c are always FP64. Then the Gershgorin interval of A_J.
-template <typename TA>
-__global__ void __launch_bounds__(256) k_solves(const int32_t* __restrict__ sub_n, const int32_t* __restrict__ sub_c0,
-                                                const int32_t* __restrict__ nbf, const int64_t* __restrict__ a_off,
-                                                const int64_t* __restrict__ c_off, int64_t a_base, int64_t chunk_n2,
-                                                int32_t j0, const double* __restrict__ ws, TA* __restrict__ Acache,
-                                                double* __restrict__ Q, double* __restrict__ lam,
-                                                const int32_t* __restrict__ prep_status) {
-  const int J = j0 + blockIdx.x;
-  if (prep_status[J] != kSubOk) return;
-  const int n = sub_n[J];
-  const int bJ = nbf[J];
-  const int c0 = sub_c0[J];
-  const double* L = ws + (a_off[J] - a_base);
-  const double* TH = L + chunk_n2;
-  TA* A = Acache + a_off[J];
-  double* QJ = Q + c_off[J];
-  for (int t = threadIdx.x; t < n + bJ; t += blockDim.x) {
-    if (t < n) {
-      for (int i = 0; i < n; ++i) {  // forward: L y = h_t
-        TA s = (TA)TH[(int64_t)i * n + t];
-        const double* Li = L + (int64_t)i * n;
-        for (int k = 0; k < i; ++k) s -= (TA)Li[k] * A[(int64_t)k * n + t];
-        A[(int64_t)i * n + t] = s / (TA)Li[i];
-      }
-      for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
-        TA s = A[(int64_t)i * n + t];
-        for (int k = i + 1; k < n; ++k) s -= (TA)L[(int64_t)k * n + i] * A[(int64_t)k * n + t];
-        A[(int64_t)i * n + t] = s / (TA)L[(int64_t)i * n + i];
-      }
-    } else {
-      const int c = t - n, col = c0 + c;
-      for (int i = 0; i < n; ++i) {
-        double s = (i == col) ? 1.0 : 0.0;
-        const double* Li = L + (int64_t)i * n;
-        for (int k = 0; k < i; ++k) s -= Li[k] * QJ[(int64_t)k * bJ + c];
-        QJ[(int64_t)i * bJ + c] = s / Li[i];
-      }
-      for (int i = n - 1; i >= 0; --i) {
-        double s = QJ[(int64_t)i * bJ + c];
-        for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * QJ[(int64_t)k * bJ + c];
-        QJ[(int64_t)i * bJ + c] = s / L[(int64_t)i * n + i];
-      }
-    }
-  }
-  __syncthreads();
-  // Gershgorin interval of A_J
-  __shared__ double rlo[256], rhi[256];
-  double lo = INFINITY, hi = -INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double r = 0.0;
-    const TA* Ai = A + (int64_t)i * n;
-    for (int j = 0; j < n; ++j)
-      if (j != i) r += fabs((double)Ai[j]);
-    lo = fmin(lo, (double)Ai[i] - r);
-    hi = fmax(hi, (double)Ai[i] + r);
-  }
-  rlo[threadIdx.x] = lo;
-  rhi[threadIdx.x] = hi;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      rlo[threadIdx.x] = fmin(rlo[threadIdx.x], rlo[threadIdx.x + s]);
-      rhi[threadIdx.x] = fmax(rhi[threadIdx.x], rhi[threadIdx.x + s]);
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    lam[2 * J] = rlo[0];
-    lam[2 * J + 1] = rhi[0];
-  }
-}
-
 // ------------------------------------------------------------------------------------ FP64 GEMM in one CTA
 // C = A B for n x n row-major matrices (leading dimension n), 256 threads, 64 x 64 output tiles, each
 // thread 4 x 4 outputs at rows ty + 16 i and columns tx + 16 j; epi(i, j, acc) consumes each output.
@@ -292,7 +181,7 @@ struct NsArgs {
   int32_t max_iter;
   double* ws; int64_t slot_elems;
   int32_t* next;               // work counter
-  double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status;
+  double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
 };
 
 __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
@@ -313,6 +202,7 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
       if (threadIdx.x == 0) {
         g.status[J] = g.prep_status[J];
         g.iters[J] = 0;
+        g.rsteps[J] = 0;
         g.tS[J] = 0.0;
         g.tH[J] = 0.0;
       }
@@ -372,6 +262,7 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
       g.tS[J] = ts;
       g.tH[J] = th;
       g.iters[J] = it;
+      g.rsteps[J] = 0;
       g.status[J] = st;
     }
     __syncthreads();
@@ -379,21 +270,35 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
 }
 
 // ------------------------------------------------------------------------------------ reductions
-// Sums of t_S and t_H over [j0, j1) in a fixed order (one block), plus the first failing submatrix.
+// Sums of t_S and t_H over [j0, j1) in a fixed order (one block), the first failing submatrix, and
+// the work counters: sum of steps n^3 (paper convention), of the tensor products' n^3 (x3 for split
+// steps) on unpadded and padded shapes, and of steps.
 __global__ void __launch_bounds__(256) k_reduce(int32_t j0, int32_t j1, const double* __restrict__ tS,
                                                 const double* __restrict__ tH, const int32_t* __restrict__ status,
-                                                double* out) {
+                                                const int32_t* __restrict__ iters, const int32_t* __restrict__ rsteps,
+                                                const int32_t* __restrict__ sub_n, int terms_main, double* out) {
   __shared__ double red[33];
   __shared__ int first[256];
-  double a = 0.0, b = 0.0;
+  double a = 0.0, b = 0.0, w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
   int f = INT32_MAX;
   for (int J = j0 + threadIdx.x; J < j1; J += blockDim.x) {
     a += tS[J];
     b += tH[J];
     if (status[J] != 0 && J < f) f = J;
+    const double n = sub_n[J];
+    const double n64 = (double)((sub_n[J] + 63) & ~63), R = (double)((sub_n[J] + 127) & ~127);
+    const double prod = (double)terms_main * (iters[J] - rsteps[J]) + 3.0 * rsteps[J];
+    w0 += iters[J] * n * n * n;
+    w1 += prod * n * n * n;
+    w2 += prod * R * n64 * n64;
+    w3 += iters[J];
   }
   const double sa = block_sum(a, red);
   const double sb = block_sum(b, red);
+  const double s0 = block_sum(w0, red);
+  const double s1 = block_sum(w1, red);
+  const double s2 = block_sum(w2, red);
+  const double s3 = block_sum(w3, red);
   first[threadIdx.x] = f;
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
@@ -405,6 +310,10 @@ __global__ void __launch_bounds__(256) k_reduce(int32_t j0, int32_t j1, const do
     out[1] = sb;
     out[2] = first[0] == INT32_MAX ? -1.0 : (double)first[0];
     out[3] = first[0] == INT32_MAX ? 0.0 : (double)status[first[0]];
+    out[4] = 4.0 * s0;
+    out[5] = 4.0 * s1;
+    out[6] = 4.0 * s2;
+    out[7] = s3;
   }
 }
 
@@ -486,20 +395,19 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     const int64_t bands = plan->h_nb_ptr[e] - plan->h_nb_ptr[J];
     k_gather<<<(unsigned)bands, 256, sizeof(int32_t) * 3 * max_nq, st>>>(g);
     NOLSM_LAUNCH_CHECK();
-    k_cholesky<<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->a_off.as<int64_t>(), g.a_base,
-                                                (int32_t)J, g.ws, plan->prep_status.as<int32_t>());
-    NOLSM_LAUNCH_CHECK();
-    if (keep_fp64_A) {
-      k_solves<double><<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->sub_c0.as<int32_t>(),
-          plan->sys.nbf, plan->a_off.as<int64_t>(), plan->c_off.as<int64_t>(), g.a_base, n2, (int32_t)J, g.ws,
-          P.A.as<double>(), plan->Q.as<double>(), plan->lam.as<double>(), plan->prep_status.as<int32_t>());
-    } else {
-      k_solves<float><<<(unsigned)(e - J), 256, 0, st>>>(plan->sub_n.as<int32_t>(), plan->sub_c0.as<int32_t>(),
-          plan->sys.nbf, plan->a_off.as<int64_t>(), plan->c_off.as<int64_t>(), g.a_base, n2, (int32_t)J, g.ws,
-          P.A.as<float>(), plan->Q.as<double>(), plan->lam.as<double>(), plan->prep_status.as<int32_t>());
+    PrepArgs pa;
+    pa.j0 = (int32_t)J;
+    pa.sub_n = plan->sub_n.as<int32_t>(); pa.sub_c0 = plan->sub_c0.as<int32_t>(); pa.nbf = plan->sys.nbf;
+    pa.a_off = plan->a_off.as<int64_t>(); pa.c_off = plan->c_off.as<int64_t>();
+    pa.a_base = g.a_base; pa.chunk_n2 = n2; pa.ws = g.ws;
+    pa.Q = plan->Q.as<double>(); pa.lam = plan->lam.as<double>(); pa.prep_status = plan->prep_status.as<int32_t>();
+    NOLSM_TRY(launch_prepare(pa, (int)(e - J), keep_fp64_A, P.A.p, st));
+    plan->stats.launches += 2;
+    for (int64_t k = J; k < e; ++k) {
+      const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
+      plan->stats.flops_fp64 += m * m * m / 3.0 + 2.0 * m * m * b + (keep_fp64_A ? 2.0 * m * m * m : 0.0);
+      P.done[k] = 1;
     }
-    NOLSM_LAUNCH_CHECK();
-    for (int64_t k = J; k < e; ++k) P.done[k] = 1;
     J = e;
   }
   return NOLSM_OK;
@@ -513,7 +421,8 @@ nolsm_status ensure_results(nolsm_plan* plan) {
     NOLSM_TRY(dev_alloc(plan, plan->t_H, sizeof(double) * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->iters, sizeof(int32_t) * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->status, sizeof(int32_t) * n_mol));
-    NOLSM_TRY(dev_alloc(plan, plan->sums, sizeof(double) * 4));
+    NOLSM_TRY(dev_alloc(plan, plan->sums, sizeof(double) * 8));
+    NOLSM_TRY(dev_alloc(plan, plan->rsteps, sizeof(int32_t) * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->counter, sizeof(int32_t) * 4));
   }
   return NOLSM_OK;
@@ -544,22 +453,30 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
   g.next = plan->counter.as<int32_t>();
   g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
+  g.rsteps = plan->rsteps.as<int32_t>();
   k_ns_fp64<<<slots, 256, 0, st>>>(g);
   NOLSM_LAUNCH_CHECK();
+  plan->stats.launches += 1;
   return NOLSM_OK;
 }
 
-nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, cudaStream_t st, double* tS, double* tH,
-                           int32_t* first_bad_status) {
+nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
+                           double* tH, int32_t* first_bad_status) {
   k_reduce<<<1, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->t_S.as<double>(), plan->t_H.as<double>(),
-                              plan->status.as<int32_t>(), plan->sums.as<double>());
+                              plan->status.as<int32_t>(), plan->iters.as<int32_t>(), plan->rsteps.as<int32_t>(),
+                              plan->sub_n.as<int32_t>(), terms_main, plan->sums.as<double>());
   NOLSM_LAUNCH_CHECK();
-  double h[4];
+  plan->stats.launches += 1;
+  double h[8];
   NOLSM_CUDA_TRY(cudaMemcpyAsync(h, plan->sums.p, sizeof(h), cudaMemcpyDeviceToHost, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   *tS = h[0];
   *tH = h[1];
   *first_bad_status = h[2] < 0 ? 0 : (int32_t)h[3];
+  plan->stats.flops_paper += h[4];
+  plan->stats.flops_tensor += h[5];
+  plan->stats.flops_tensor_padded += h[6];
+  plan->stats.ns_steps += (int64_t)h[7];
   return NOLSM_OK;
 }
 
@@ -572,6 +489,7 @@ nolsm_status scatter(nolsm_plan* plan, double* D, int64_t j0, int64_t j1, cudaSt
       plan->nb_off.as<int32_t>(), plan->d_slot.as<int32_t>(), plan->d_blk_off.as<int64_t>(), plan->c_off.as<int64_t>(),
       plan->Dc.as<double>(), D);
   NOLSM_LAUNCH_CHECK();
+  plan->stats.launches += 1;
   return NOLSM_OK;
 }
 

@@ -4,7 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "nolsm_internal.cuh"
 #include "tc_path.cuh"
@@ -44,6 +46,20 @@ void dev_free(nolsm_plan* plan, DevBuf& b) {
   b.bytes = 0;
 }
 
+void mark(nolsm_plan* plan, int i, cudaStream_t st) {
+  if (plan->ev_ok) cudaEventRecord(plan->ev[i], st);
+}
+
+double elapsed(nolsm_plan* plan, int i, int j) {
+  if (!plan->ev_ok) return 0.0;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, plan->ev[i], plan->ev[j]) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return (double)ms;
+}
+
 }  // namespace nolsm
 
 using namespace nolsm;
@@ -51,9 +67,11 @@ using namespace nolsm;
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &Dc,
-                   &t_S, &t_H, &iters, &status, &sums, &counter, &ws_dense, &ws_ns};
+                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_ns};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
+  if (ev_ok)
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
 }
 
 extern "C" {
@@ -87,6 +105,7 @@ const char* nolsm_status_str(nolsm_status s) {
     case NOLSM_ERR_NO_PLATEAU: return "bisection found no mu with the requested electron count";
     case NOLSM_ERR_UNSUPPORTED: return "unsupported option or size";
     case NOLSM_ERR_NO_SOLUTION: return "no solution to write back";
+    case NOLSM_ERR_TIMEOUT: return "device-side wait timed out";
   }
   return "unknown status";
 }
@@ -106,11 +125,19 @@ nolsm_status nolsm_build_submatrices(const nolsm_system* sys, nolsm_stream_t str
   if (!plan) { set_error("host allocation failed"); return NOLSM_ERR_OOM; }
   plan->sys = *sys;
   plan->n_mol = sys->n_mol;
+  plan->ev_ok = true;
+  for (cudaEvent_t& e : plan->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) plan->ev_ok = false;
+  if (!plan->ev_ok) cudaGetLastError();
+  mark(plan, 0, (cudaStream_t)stream);
   nolsm_status s = build_plan_device(plan, (cudaStream_t)stream);
   if (s != NOLSM_OK) {
     delete plan;
     return s;
   }
+  mark(plan, 1, (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  plan->stats.ms_plan += elapsed(plan, 0, 1);
   *out = plan;
   return NOLSM_OK;
 }
@@ -169,22 +196,31 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   NOLSM_TRY(check_options(plan, opts, &j0, &j1));
   cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
-  if (opts->precision == NOLSM_FP64) {
-    NOLSM_TRY(prepare_fp64(plan, j0, j1, true, st));
+  const bool fp64 = opts->precision == NOLSM_FP64;
+  mark(plan, 0, st);
+  NOLSM_TRY(prepare_fp64(plan, j0, j1, fp64, st));
+  mark(plan, 1, st);
+  if (fp64) {
     NOLSM_TRY(solve_fp64(plan, mu, *opts, j0, j1, st));
   } else {
-    NOLSM_TRY(prepare_fp64(plan, j0, j1, false, st));
     NOLSM_TRY(solve_tc(plan, mu, *opts, j0, j1, st));
   }
+  mark(plan, 2, st);
   double tS = 0, tH = 0;
   int32_t bad = 0;
-  NOLSM_TRY(reduce_traces(plan, j0, j1, st, &tS, &tH, &bad));
+  NOLSM_TRY(reduce_traces(plan, j0, j1, fp64 ? 1 : main_terms(opts->precision), st, &tS, &tH, &bad));
+  mark(plan, 3, st);
   const size_t cnt = (size_t)(j1 - j0);
   if (sub_t_S) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_t_S + j0, plan->t_S.as<double>() + j0, 8 * cnt, cudaMemcpyDeviceToDevice, st));
   if (sub_t_H) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_t_H + j0, plan->t_H.as<double>() + j0, 8 * cnt, cudaMemcpyDeviceToDevice, st));
   if (iters) NOLSM_CUDA_TRY(cudaMemcpyAsync(iters + j0, plan->iters.as<int32_t>() + j0, 4 * cnt, cudaMemcpyDeviceToDevice, st));
   if (status) NOLSM_CUDA_TRY(cudaMemcpyAsync(status + j0, plan->status.as<int32_t>() + j0, 4 * cnt, cudaMemcpyDeviceToDevice, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  plan->stats.ms_prepare += elapsed(plan, 0, 1);
+  plan->stats.ms_sign += elapsed(plan, 1, 2);
+  plan->stats.ms_reduce += elapsed(plan, 2, 3);
+  plan->stats.solves += 1;
+  plan->stats.sub_solves += j1 - j0;
   if (trace_DS) *trace_DS = tS;
   if (trace_DH) *trace_DH = tH;
   plan->solved_begin = j0;
@@ -200,17 +236,56 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
 nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream) {
   if (!plan || !D_vals) { set_error("nolsm_scatter_density: NULL argument"); return NOLSM_ERR_ARG; }
   if (!plan->have_solution) { set_error("nolsm_scatter_density: no solve yet"); return NOLSM_ERR_NO_SOLUTION; }
+  mark(plan, 4, (cudaStream_t)stream);
   NOLSM_TRY(scatter(plan, D_vals, plan->solved_begin, plan->solved_end, (cudaStream_t)stream));
+  mark(plan, 5, (cudaStream_t)stream);
   NOLSM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  plan->stats.ms_scatter += elapsed(plan, 4, 5);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_spectral_bracket(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, double* lo,
+                                    double* hi) {
+  if (!plan || !lo || !hi) { set_error("nolsm_spectral_bracket: NULL argument"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  mark(plan, 0, st);
+  NOLSM_TRY(prepare_fp64(plan, j0, j1, opts->precision == NOLSM_FP64, st));
+  mark(plan, 1, st);
+  std::vector<double> lam((size_t)(2 * (j1 - j0)));
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(lam.data(), plan->lam.as<double>() + 2 * j0, sizeof(double) * lam.size(),
+                                 cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  plan->stats.ms_prepare += elapsed(plan, 0, 1);
+  std::vector<int32_t> pst((size_t)(j1 - j0));
+  NOLSM_CUDA_TRY(cudaMemcpy(pst.data(), plan->prep_status.as<int32_t>() + j0, sizeof(int32_t) * pst.size(),
+                            cudaMemcpyDeviceToHost));
+  double a = INFINITY, b = -INFINITY;
+  for (size_t k = 0; k < pst.size(); ++k) {
+    if (pst[k] != kSubOk) continue;
+    a = std::min(a, lam[2 * k]);
+    b = std::max(b, lam[2 * k + 1]);
+  }
+  if (!(a < b) || !std::isfinite(a) || !std::isfinite(b)) {
+    set_error("nolsm_spectral_bracket: no submatrix with a usable spectrum in the range");
+    return NOLSM_ERR_NOT_SPD;
+  }
+  *lo = a;
+  *hi = b;
   return NOLSM_OK;
 }
 
 nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
                            nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
                            double* mu_history) {
-  if (!plan || !opts || !(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi) || !std::isfinite(n_occ)) {
+  if (!plan || !opts || !std::isfinite(lo) || !std::isfinite(hi) || !std::isfinite(n_occ)) {
     set_error("nolsm_find_mu: invalid arguments");
     return NOLSM_ERR_ARG;
+  }
+  if (!(lo < hi)) {
+    NOLSM_TRY(nolsm_spectral_bracket(plan, opts, stream, &lo, &hi));
   }
   const int max_steps = opts->max_bisect > 0 ? opts->max_bisect : 100;
   double mu = 0.5 * (lo + hi), t = 0.0;
@@ -233,6 +308,18 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
   if (result == NOLSM_ERR_NO_PLATEAU)
     set_error("nolsm_find_mu: stopped after %d evaluations at mu=%.12g with Tr(DS)=%.9f, target %.9f", step, mu, t, n_occ);
   return result;
+}
+
+nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats) {
+  if (!plan || !stats) { set_error("nolsm_plan_stats: NULL argument"); return NOLSM_ERR_ARG; }
+  *stats = plan->stats;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_plan_stats_reset(nolsm_plan* plan) {
+  if (!plan) { set_error("nolsm_plan_stats_reset: NULL plan"); return NOLSM_ERR_ARG; }
+  plan->stats = nolsm_stats{};
+  return NOLSM_OK;
 }
 
 void nolsm_plan_destroy(nolsm_plan* plan) { delete plan; }

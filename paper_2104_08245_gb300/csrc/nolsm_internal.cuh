@@ -12,7 +12,7 @@ namespace nolsm {
 
 // Per-submatrix status codes written by kernels (values of nolsm_status).
 enum : int32_t { kSubOk = 0, kSubNotSpd = NOLSM_ERR_NOT_SPD, kSubNotConv = NOLSM_ERR_NOT_CONVERGED,
-                 kSubNonFinite = NOLSM_ERR_NONFINITE };
+                 kSubNonFinite = NOLSM_ERR_NONFINITE, kSubTimeout = NOLSM_ERR_TIMEOUT };
 
 void set_error(const char* fmt, ...);
 
@@ -81,6 +81,7 @@ struct nolsm_plan {
   nolsm::DevBuf Dc;                 // centre columns of T_J(D), FP64, at c_off[J]
   nolsm::DevBuf t_S, t_H;           // float64 [n_mol]
   nolsm::DevBuf iters, status;      // int32 [n_mol]
+  nolsm::DevBuf rsteps;             // int32 [n_mol]: steps taken in the refinement format
   nolsm::DevBuf sums;               // float64 [4]
   nolsm::DevBuf counter;            // int32 work counters of persistent kernels
   int64_t solved_begin = 0, solved_end = 0;
@@ -88,8 +89,13 @@ struct nolsm_plan {
 
   // workspaces
   nolsm::DevBuf ws_dense;           // gathered T_J(S), T_J(H0) of one preparation chunk (FP64)
-  nolsm::DevBuf ws_ns;              // per-CTA Newton-Schulz buffers
-  int ns_slots = 0;
+  nolsm::DevBuf ws_ns;              // per-CTA Newton-Schulz buffers (FP64 path)
+  void* tc = nullptr;               // tensor-core path state (tc_path.cu)
+
+  // tracing: accumulated stats and the events that time one ABI call's phases
+  nolsm_stats stats{};
+  cudaEvent_t ev[8] = {};
+  bool ev_ok = false;
 
   ~nolsm_plan();
 };
@@ -109,9 +115,14 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
 
 nolsm_status ensure_results(nolsm_plan* plan);
 
+// Times phases of one ABI call: mark(i) records event i on the stream; after the stream has been
+// synchronised, elapsed(i, j) is the device time between marks i and j in ms (0 if unavailable).
+void mark(nolsm_plan* plan, int i, cudaStream_t st);
+double elapsed(nolsm_plan* plan, int i, int j);
+
 // shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
-nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, cudaStream_t st, double* tS, double* tH,
-                           int32_t* first_bad_status);
+nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
+                           double* tH, int32_t* first_bad_status);
 nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st);
 
 }  // namespace nolsm

@@ -385,6 +385,7 @@ nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st) {
   dev_free(plan, cnt);
   dev_free(plan, nb_sz);
 
+  plan->stats.launches += 28;   // validation, block sizes, scans (3 kernels each), merge, slots
   plan->max_n = 0;
   plan->min_n = INT32_MAX;
   plan->max_b = 0;

@@ -1,0 +1,22 @@
+// Preparation kernels (prep_kernels.cu): arguments shared with the host driver in fp64_path.cu.
+#pragma once
+#include "nolsm_internal.cuh"
+
+namespace nolsm {
+
+struct PrepArgs {
+  int32_t j0;                 // first submatrix of the chunk (one CTA per submatrix)
+  const int32_t* sub_n; const int32_t* sub_c0; const int32_t* nbf;
+  const int64_t* a_off; const int64_t* c_off;
+  int64_t a_base;             // a_off of the chunk's first submatrix
+  int64_t chunk_n2;           // offset of the gathered T_J(H0) half of the workspace
+  double* ws;                 // gathered T_J(S) (factored in place) and T_J(H0)
+  double* Q;                  // centre columns of T_J(S)^-1, n x b row-major at c_off
+  double* lam;                // Gershgorin interval of A_J
+  int32_t* prep_status;
+};
+
+// a2-a3 for `count` submatrices starting at g.j0; A in FP64 (fp64_A) or FP32.
+nolsm_status launch_prepare(const PrepArgs& g, int count, bool fp64_A, void* Acache, cudaStream_t st);
+
+}  // namespace nolsm

@@ -1,9 +1,593 @@
+// a4-a7 on the 5th-generation tensor cores (tcgen05) for the low-precision modes.
+//
+// Newton-Schulz sign iteration (Eq. NS1): X_{k+1} = 1/2 X_k (3I - X_k^2), two products per step:
+//   GEMM0: Y = X X      -> epilogue writes T = 3I - Y and sums the defect ||I - X^2||_F^2
+//   GEMM1: Z = X T      -> epilogue writes X_{k+1} = Z / 2 (FP32 after the last step)
+// Each product is either one tensor-core product of the rounded operands (BF16 or FP16) or the
+// three-term split hi*hi + hi*lo + lo*hi with x = hi + lo (hi = round(x), lo = round(x - hi)),
+// accumulated in FP32 in tensor memory.
+//
+// One persistent CTA per SM works on one submatrix at a time (submatrices taken largest first from
+// a work counter). Operands live in a per-CTA scratch slot in global memory (L2-resident) as 2-byte
+// planes [X0 hi, X0 lo, X1 hi, X1 lo, T hi, T lo], each R x LD (R = n rounded up to 128 rows,
+// LD = n rounded up to 64 columns, zero padded). Output tiles are 128 rows x up to 256 columns; the
+// K dimension streams in slices of 64 through a two-stage TMA pipeline with 128-byte swizzle.
+// Warp roles: warp 0 issues TMA, warp 1 (one thread) issues tcgen05.mma, warps 4-7 drain the
+// double-buffered TMEM accumulators (2 x 256 columns). All waits are bounded by the global timer.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "nolsm_internal.cuh"
 #include "tc_path.cuh"
+#include "tcgen05.cuh"
+#include "tmap.cuh"
 
 namespace nolsm {
-nolsm_status solve_tc(nolsm_plan*, double, const nolsm_options&, int64_t, int64_t, cudaStream_t) {
-  set_error("tensor-core path not built");
-  return NOLSM_ERR_UNSUPPORTED;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kStages = 2;
+constexpr uint32_t kABytes = 128 * 64 * 2;        // one A plane slice: 128 rows x 64 K
+constexpr uint32_t kBBytes = 64 * 256 * 2;        // one B plane slice: 64 K x up to 256 columns
+constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr int kPlanes = 6;
+constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
+
+enum : int { FMT_F16 = 0, FMT_BF16 = 1 };
+
+struct Fmt {
+  int fmt;    // FMT_F16 / FMT_BF16
+  int terms;  // 1 or 3
+};
+
+struct TcArgs {
+  int32_t j0, j1;
+  const int32_t* order;       // submatrices of [j0, j1), largest first
+  const int32_t* sub_n; const int32_t* nbf;
+  const int64_t* a_off; const int64_t* c_off;
+  const float* A;             // FP32 A_J
+  const double* Q; const double* Sc; const double* Hc; const double* lam;
+  const int32_t* prep_status;
+  double mu;
+  float tol_ns, tol_accept;
+  int32_t max_iter, refine_steps;
+  Fmt main_fmt, refine_fmt;
+  uint16_t* planes;           // [slots*6][R][LD]
+  float* xf;                  // [slots][R][LD]
+  int32_t R, LD;
+  int32_t* next;              // work counter
+  int32_t* err;               // global error flag (timeouts)
+  double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
+};
+
+struct Shared {
+  uint64_t full[kStages], empty[kStages], accf[2], acce[2], idle;
+  uint32_t tmem;
+  int job;
+  int err;
+  // decisions made after each GEMM0 (read by every role after the block-wide barrier that ends it)
+  int last, status, phase, refine_left, steps, rsteps;
+  Fmt cur, nxt;
+  float red[4];
+  double dred[2][8];
+};
+
+__device__ __forceinline__ uint16_t to_bits(float x, int fmt) {
+  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  return __half_as_ushort(__float2half_rn(x));
 }
-void tc_release(nolsm_plan*) {}
+__device__ __forceinline__ float from_bits(uint16_t b, int fmt) {
+  if (fmt == FMT_BF16) return __bfloat162float(__ushort_as_bfloat16(b));
+  return __half2float(__ushort_as_half(b));
+}
+
+// Two values rounded to the 2-byte format (packed) and their low parts x - round(x) rounded likewise.
+__device__ __forceinline__ void split2(float a, float b, int fmt, uint32_t& hi, uint32_t& lo) {
+  if (fmt == FMT_BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+// Writes 32 consecutive values of one row as hi (and lo) planes.
+__device__ __forceinline__ void store_split(uint16_t* hi, uint16_t* lo, const float (&v)[32], Fmt f) {
+  uint32_t h[16], l[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) split2(v[2 * j], v[2 * j + 1], f.fmt, h[j], l[j]);
+  uint4* H = reinterpret_cast<uint4*>(hi);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) H[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+  if (f.terms > 1) {
+    uint4* L = reinterpret_cast<uint4*>(lo);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L[q] = make_uint4(l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
+  }
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ Shared sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = blockIdx.x;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      tc::mbar_init(&sh.full[s], 1);
+      tc::mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&sh.accf[b], 1);
+      tc::mbar_init(&sh.acce[b], 128);
+    }
+    tc::mbar_init(&sh.idle, 1);
+    tc::fence_mbar_init();
+    sh.err = 0;
+    tc::prefetch_tmap(&mapA);
+    tc::prefetch_tmap(&mapB);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&sh.tmem, 512);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = sh.tmem;
+
+  // pipeline counters (each role keeps the ones it uses; all roles walk the same schedule)
+  uint32_t kcount = 0;   // K slices issued (producer) / consumed (MMA)
+  uint32_t tcount = 0;   // tiles accumulated (MMA) / drained (epilogue)
+  uint32_t arm_phase[kStages] = {0, 0};  // producer: parity of the last load armed per stage
+  bool armed[kStages] = {false, false};
+  const size_t plane_elems = (size_t)g.R * g.LD;
+
+  for (;;) {
+    if (tid == 0) {
+      const int k = atomicAdd(g.next, 1);
+      sh.job = (k < g.j1 - g.j0 && !sh.err) ? g.order[k] : -1;
+    }
+    __syncthreads();
+    const int J = sh.job;
+    if (J < 0) break;
+    if (g.prep_status[J] != kSubOk) {
+      if (tid == 0) {
+        g.status[J] = g.prep_status[J];
+        g.iters[J] = 0;
+        g.rsteps[J] = 0;
+        g.tS[J] = 0.0;
+        g.tH[J] = 0.0;
+      }
+      __syncthreads();
+      continue;
+    }
+    const int n = g.sub_n[J];
+    const int n64 = (n + 63) & ~63;
+    const int R = (n + 127) & ~127;
+    const int nrb = R / 128, ncb = (n64 + 255) / 256;
+    const int nks = n64 / 64;
+
+    // ---- a4: X_0 = (A - mu I) / alpha into plane X0 (hi, lo) in the main format, zero padded
+    {
+      const float* A = g.A + g.a_off[J];
+      const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
+      const float inv = (float)(1.0 / alpha);
+      const float fmu = (float)g.mu;
+      uint16_t* hi = g.planes + ((size_t)slot * kPlanes + 0) * plane_elems;
+      uint16_t* lo = g.planes + ((size_t)slot * kPlanes + 1) * plane_elems;
+      const Fmt f = g.main_fmt;
+      for (int e = tid; e < R * n64; e += kThreads) {
+        const int i = e / n64, j = e - i * n64;
+        float x = 0.0f;
+        if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
+        const uint16_t h = to_bits(x, f.fmt);
+        hi[(size_t)i * g.LD + j] = h;
+        if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+      }
+      if (tid == 0) {
+        sh.last = 0;
+        sh.status = kSubNotConv;
+        sh.phase = 0;
+        sh.refine_left = g.refine_steps;
+        sh.steps = 0;
+        sh.rsteps = 0;
+        sh.cur = g.main_fmt;
+        sh.nxt = g.main_fmt;
+      }
+      tc::fence_proxy_async_global();
+      __syncthreads();
+    }
+
+    // ---- a5/a6: the iteration; every role walks the same sequence of GEMMs
+    int cur = 0;          // X ping-pong index
+    bool stop = false;
+    for (int step = 0; !stop; ++step) {
+      for (int kind = 0; kind < 2; ++kind) {
+        const Fmt f = sh.cur;                 // stable during this step (written only before GEMM0 ends)
+        const int two = f.terms > 1 ? 2 : 1;
+        const int a_plane = 2 * cur;          // X_cur hi (lo = +1)
+        const int b_plane = kind == 0 ? 2 * cur : 4;
+        if (warp == 0 && lane == 0) {
+          // ------------------------------------------------ producer
+          for (int mb = 0; mb < nrb && !sh.err; ++mb)
+            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
+              const int nt = min(256, n64 - 256 * cb);
+              const uint32_t bytes = (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
+              for (int ks = 0; ks < nks; ++ks) {
+                const int s = kcount % kStages;
+                const uint32_t ph = (kcount / kStages) & 1;
+                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+                uint8_t* st = stage_mem + s * kStageBytes;
+                tc::mbar_arrive_expect_tx(&sh.full[s], bytes);
+                armed[s] = true;
+                arm_phase[s] = ph;
+                for (int z = 0; z < two; ++z) {
+                  tc::tma_load_3d(st + z * kABytes, &mapA, &sh.full[s], 64 * ks, 128 * mb, slot * kPlanes + a_plane + z);
+                  uint8_t* bdst = st + 2 * kABytes + z * kBBytes;
+                  for (int c = 0; c < nt / 64; ++c)
+                    tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[s], 256 * cb + 64 * c, 64 * ks,
+                                    slot * kPlanes + b_plane + z);
+                }
+                ++kcount;
+              }
+            }
+        } else if (warp == 1 && lane == 0) {
+          // ------------------------------------------------ MMA issuer
+          for (int mb = 0; mb < nrb && !sh.err; ++mb)
+            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
+              const int nt = min(256, n64 - 256 * cb);
+              const uint32_t id = tc::idesc(f.fmt, f.fmt, 0, 1, 128, nt);
+              const int buf = tcount & 1;
+              if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + kWaitNs)) {
+                sh.err = 1;
+                break;
+              }
+              tc::tc_fence_after();
+              const uint32_t dt = tmem + (uint32_t)buf * 256;
+              for (int ks = 0; ks < nks; ++ks) {
+                const int s = kcount % kStages;
+                const uint32_t ph = (kcount / kStages) & 1;
+                if (!tc::mbar_wait(&sh.full[s], ph, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+                tc::tc_fence_after();
+                const uint32_t a0 = tc::smem_u32(stage_mem + s * kStageBytes);
+                const uint32_t b0 = a0 + 2 * kABytes;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint64_t ah = tc::sdesc_sw128(a0 + kk * 32, 16, 1024);
+                  const uint64_t bh = tc::sdesc_sw128(b0 + kk * 2048, 8192, 1024);
+                  tc::mma_f16(dt, ah, bh, id, (ks > 0 || kk > 0) ? 1u : 0u);
+                  if (f.terms > 1) {
+                    const uint64_t al = tc::sdesc_sw128(a0 + kABytes + kk * 32, 16, 1024);
+                    const uint64_t bl = tc::sdesc_sw128(b0 + kBBytes + kk * 2048, 8192, 1024);
+                    tc::mma_f16(dt, ah, bl, id, 1u);
+                    tc::mma_f16(dt, al, bh, id, 1u);
+                  }
+                }
+                tc::mma_commit(&sh.empty[s]);
+                ++kcount;
+              }
+              tc::mma_commit(&sh.accf[buf]);
+              ++tcount;
+            }
+        } else if (warp >= 4) {
+          // ------------------------------------------------ epilogue
+          const int q = warp - 4;
+          float part = 0.0f;
+          const bool last = kind == 1 && sh.last;   // decided after this step's GEMM0
+          const Fmt fo = kind == 0 ? f : sh.nxt;    // format of the written operand
+          const int out_plane = kind == 0 ? 4 : 2 * (cur ^ 1);
+          uint16_t* ohi = g.planes + ((size_t)slot * kPlanes + out_plane) * plane_elems;
+          uint16_t* olo = ohi + plane_elems;
+          float* xf = g.xf + (size_t)slot * plane_elems;
+          for (int mb = 0; mb < nrb && !sh.err; ++mb)
+            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
+              const int nt = min(256, n64 - 256 * cb);
+              const int buf = tcount & 1;
+              if (!tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + kWaitNs)) {
+                sh.err = 1;
+                break;
+              }
+              tc::tc_fence_after();
+              const int row = 128 * mb + 32 * q + lane;
+              for (int c0 = 0; c0 < nt / 32; ++c0) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256 + 32 * c0, r);
+                tc::tmem_wait_ld();
+                const int col0 = 256 * cb + 32 * c0;
+                float v[32];
+                if (kind == 0) {
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) {
+                    const int col = col0 + j;
+                    const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
+                    if (row < n && col < n) part += e * e;
+                    v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
+                  }
+                  store_split(ohi + (size_t)row * g.LD + col0, olo + (size_t)row * g.LD + col0, v, fo);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
+                  if (last) {
+                    float4* d = reinterpret_cast<float4*>(xf + (size_t)row * g.LD + col0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                  } else {
+                    store_split(ohi + (size_t)row * g.LD + col0, olo + (size_t)row * g.LD + col0, v, fo);
+                  }
+                }
+              }
+              tc::tc_fence_before();
+              tc::mbar_arrive(&sh.acce[buf]);
+              ++tcount;
+            }
+          tc::fence_proxy_async_global();
+          if (kind == 0) {
+            // defect of X_step and the decision about the following steps
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) sh.red[q] = part;
+            epi_bar();
+            if (tid == 128) {
+              const float d = sqrtf((sh.red[0] + sh.red[1] + sh.red[2] + sh.red[3]) / (float)n);
+              const int steps = sh.steps + 1;
+              if (sh.phase == 1) sh.rsteps += 1;   // this step ran in the refinement format
+              int last_ = 0, status = kSubNotConv;
+              Fmt nxt = sh.cur;
+              if (!isfinite(d)) {
+                last_ = 1;
+                status = kSubNonFinite;
+              } else if (sh.phase == 0) {
+                if (d <= g.tol_ns) {
+                  if (g.refine_steps == 0) {
+                    last_ = 1;
+                    status = d <= g.tol_accept ? kSubOk : kSubNotConv;
+                  } else {
+                    sh.phase = 1;
+                    sh.refine_left = g.refine_steps;
+                    nxt = g.refine_fmt;
+                  }
+                }
+              } else {
+                if (--sh.refine_left == 0) {
+                  last_ = 1;
+                  status = d <= g.tol_accept ? kSubOk : kSubNotConv;
+                }
+              }
+              if (!last_ && steps >= g.max_iter) {
+                last_ = 1;
+                status = kSubNotConv;
+              }
+              sh.steps = steps;
+              sh.last = last_;
+              sh.status = status;
+              sh.nxt = nxt;
+            }
+          }
+        }
+        // every role: this GEMM's epilogue (written and fenced for TMA) feeds the next GEMM; the
+        // block-wide OR makes the error decision uniform
+        if (__syncthreads_or(sh.err)) { stop = true; break; }
+      }
+      if (stop) break;
+      // after GEMM1: swap the ping-pong X and adopt the next format
+      cur ^= 1;
+      stop = sh.last != 0;
+      __syncthreads();   // all roles have read sh.last / sh.nxt for this step
+      if (tid == 0) sh.cur = sh.nxt;
+      __syncthreads();
+    }
+
+    // ---- a7: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the FP64 partial traces
+    {
+      const int b = g.nbf[J];
+      const float* xf = g.xf + (size_t)slot * plane_elems;
+      const double* Q = g.Q + g.c_off[J];
+      const double* Sc = g.Sc + g.c_off[J];
+      const double* Hc = g.Hc + g.c_off[J];
+      double* Dc = g.Dc + g.c_off[J];
+      double ps = 0.0, ph = 0.0;
+      if (!sh.err) {
+        // T_J(S)^-1 centre columns staged as FP32 in the (now idle) pipeline buffers when they fit
+        float* Qs = reinterpret_cast<float*>(stage_mem);
+        const bool staged = (size_t)n * b * sizeof(float) <= (size_t)kStages * kStageBytes;
+        if (staged)
+          for (int e = tid; e < n * b; e += kThreads) Qs[e] = (float)Q[e];
+        __syncthreads();
+        for (int e = tid; e < n * b; e += kThreads) {
+          const int i = e / b, c = e - i * b;
+          const float* xi = xf + (size_t)i * g.LD;
+          // FP32 partial sums of 16 products, combined with Kahan compensation
+          float sum = 0.0f, comp = 0.0f;
+          for (int k0 = 0; k0 < n; k0 += 16) {
+            float p = 0.0f;
+            const int k1 = min(n, k0 + 16);
+            if (staged) {
+              for (int k = k0; k < k1; ++k) p = fmaf(xi[k], Qs[k * b + c], p);
+            } else {
+              for (int k = k0; k < k1; ++k) p = fmaf(xi[k], (float)Q[(size_t)k * b + c], p);
+            }
+            const float y = p - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+          }
+          const double d = 0.5 * (Q[e] - ((double)sum - (double)comp));
+          Dc[e] = d;
+          ps += d * Sc[e];
+          ph += d * Hc[e];
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        ps += __shfl_xor_sync(0xffffffffu, ps, o);
+        ph += __shfl_xor_sync(0xffffffffu, ph, o);
+      }
+      if (lane == 0) {
+        sh.dred[0][warp] = ps;
+        sh.dred[1][warp] = ph;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double ts = 0.0, th = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+          ts += sh.dred[0][w];
+          th += sh.dred[1][w];
+        }
+        int st = sh.err ? kSubTimeout : sh.status;
+        if (st == kSubOk && !(isfinite(ts) && isfinite(th))) st = kSubNonFinite;
+        g.tS[J] = ts;
+        g.tH[J] = th;
+        g.iters[J] = sh.steps;
+        g.rsteps[J] = sh.rsteps;
+        g.status[J] = st;
+        if (sh.err) atomicExch(g.err, 1);
+      }
+      __syncthreads();
+    }
+  }
+
+  // teardown after a timeout: wait (bounded) for this CTA's TMA copies and MMAs still in flight
+  if (sh.err) {
+    if (warp == 0 && lane == 0)
+      for (int s = 0; s < kStages; ++s)
+        if (armed[s]) tc::mbar_wait(&sh.full[s], arm_phase[s], tc::globaltimer() + 50000000ull);
+    if (warp == 1 && lane == 0) {
+      tc::mma_commit(&sh.idle);
+      tc::mbar_wait(&sh.idle, 0, tc::globaltimer() + 50000000ull);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+// ==================================================================================== host side
+
+struct TcState {
+  DevBuf planes, xf, order, err;
+  int R = 0, LD = 0, slots = 0;
+  int64_t ord_j0 = -1, ord_j1 = -1;
+};
+
+static TcState* state(nolsm_plan* plan) {
+  if (!plan->tc) plan->tc = new TcState();
+  return static_cast<TcState*>(plan->tc);
+}
+
+void tc_release(nolsm_plan* plan) {
+  if (!plan->tc) return;
+  TcState* s = static_cast<TcState*>(plan->tc);
+  dev_free(plan, s->planes);
+  dev_free(plan, s->xf);
+  dev_free(plan, s->order);
+  dev_free(plan, s->err);
+  delete s;
+  plan->tc = nullptr;
+}
+
+int main_terms(int precision) {
+  return precision == NOLSM_FP32 || precision == NOLSM_BF16X3 ? 3 : 1;
+}
+
+static bool formats(int precision, Fmt* main_fmt, Fmt* refine_fmt) {
+  *refine_fmt = Fmt{FMT_F16, 3};
+  switch (precision) {
+    case NOLSM_FP32: *main_fmt = Fmt{FMT_F16, 3}; return true;
+    case NOLSM_BF16X3: *main_fmt = Fmt{FMT_BF16, 3}; return true;
+    case NOLSM_BF16: *main_fmt = Fmt{FMT_BF16, 1}; return true;
+    default: return false;
+  }
+}
+
+nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1, cudaStream_t st) {
+  Fmt mf, rf;
+  if (!formats(o.precision, &mf, &rf)) {
+    set_error("precision %d is not available on the tensor-core path in this build", o.precision);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  NOLSM_TRY(ensure_results(plan));
+  TcState* S = state(plan);
+  int dev = 0, sms = 0;
+  NOLSM_CUDA_TRY(cudaGetDevice(&dev));
+  NOLSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int32_t maxn = 0;
+  for (int64_t J = j0; J < j1; ++J) maxn = std::max(maxn, plan->h_sub_n[J]);
+  const int LD = (maxn + 63) & ~63, R = (maxn + 127) & ~127;
+  const int slots = (int)std::min<int64_t>(sms, j1 - j0);
+  if (!S->planes.p || S->R < R || S->LD < LD || S->slots < slots) {
+    const int nR = std::max(R, S->R), nLD = std::max(LD, S->LD), nS = std::max(slots, S->slots);
+    dev_free(plan, S->planes);
+    dev_free(plan, S->xf);
+    NOLSM_TRY(dev_alloc(plan, S->planes, sizeof(uint16_t) * (size_t)kPlanes * nS * nR * nLD));
+    NOLSM_TRY(dev_alloc(plan, S->xf, sizeof(float) * (size_t)nS * nR * nLD));
+    S->R = nR;
+    S->LD = nLD;
+    S->slots = nS;
+  }
+  if (!S->err.p) NOLSM_TRY(dev_alloc(plan, S->err, sizeof(int32_t) * 4));
+  if (S->ord_j0 != j0 || S->ord_j1 != j1) {
+    std::vector<int32_t> ord((size_t)(j1 - j0));
+    for (int64_t J = j0; J < j1; ++J) ord[(size_t)(J - j0)] = (int32_t)J;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return plan->h_sub_n[a] > plan->h_sub_n[b]; });
+    if (S->order.bytes < sizeof(int32_t) * ord.size()) {
+      dev_free(plan, S->order);
+      NOLSM_TRY(dev_alloc(plan, S->order, sizeof(int32_t) * (size_t)plan->n_mol));
+    }
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(S->order.p, ord.data(), sizeof(int32_t) * ord.size(), cudaMemcpyHostToDevice, st));
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+    S->ord_j0 = j0;
+    S->ord_j1 = j1;
+  }
+  CUtensorMap mA, mB;
+  if (!tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
+      !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64)) {
+    set_error("cuTensorMapEncodeTiled rejected the scratch layout (R %d, LD %d, slots %d)", S->R, S->LD, S->slots);
+    return NOLSM_ERR_CUDA;
+  }
+  NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
+  NOLSM_CUDA_TRY(cudaMemsetAsync(S->err.p, 0, sizeof(int32_t), st));
+  TcArgs g;
+  g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
+  g.order = S->order.as<int32_t>();
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
+  g.A = plan->prep32.A.as<float>();
+  g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
+  g.lam = plan->lam.as<double>();
+  g.prep_status = plan->prep_status.as<int32_t>();
+  g.mu = mu;
+  g.tol_ns = (float)o.tol_ns; g.tol_accept = (float)o.tol_accept;
+  g.max_iter = o.max_iter; g.refine_steps = o.refine_steps;
+  g.main_fmt = mf; g.refine_fmt = rf;
+  g.planes = S->planes.as<uint16_t>(); g.xf = S->xf.as<float>();
+  g.R = S->R; g.LD = S->LD;
+  g.next = plan->counter.as<int32_t>();
+  g.err = S->err.as<int32_t>();
+  g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();
+  g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
+  g.rsteps = plan->rsteps.as<int32_t>();
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  k_ns_tc<<<slots, kThreads, kSmemBytes, st>>>(mA, mB, g);
+  NOLSM_LAUNCH_CHECK();
+  plan->stats.launches += 1;
+  return NOLSM_OK;
+}
+
 }  // namespace nolsm

@@ -17,14 +17,18 @@ Construction (the readings of the workload description, one per parameter):
   (strict): S = exp(-0.5 r^2) and H = -0.2 exp(-r/1.5) for every entry, optionally modulated by a
   direction-dependent factor (1 + aniso (u_a - u_c) . r_hat) that keeps S and H symmetric while
   making the individual off-diagonal blocks non-symmetric (used by tests that must catch transposed
-  operands). Blocks at r >= r_c are absent. The element formulas are those of the 6-function
-  molecule; between molecules with b_I and b_J functions every inter-molecular entry is multiplied by
-  6/sqrt(b_I b_J), which leaves 6-function systems unchanged and keeps the coupling of each molecule
-  pair at the 6-function strength. (Unscaled, 23 functions per molecule make S indefinite: its
-  lowest eigenvalue is about -0.26 on a 27-molecule cell.)
-* On-site energies: 6 functions per molecule use types [0,1,1,1,2,2] with -1.0, -0.5, +0.3 Ha;
-  23 functions per molecule draw one energy per function slot from N(-0.5, 0.3) Ha once per system.
-  Four occupied orbitals per molecule.
+  operands). Blocks at r >= r_c are absent. Between molecules with b_I and b_J functions every
+  inter-molecular entry carries the factor 1/sqrt(b_I b_J): with it, the block of S seen by the
+  normalised all-ones vector of each molecule is exactly the Gaussian-kernel matrix exp(-0.5 r_IJ^2),
+  which is positive definite for every geometry, so S is positive definite (up to the cutoff
+  truncation of terms below exp(-18)). Without the factor, b coincident functions multiply the
+  coupling by b and S turns indefinite wherever two molecules come close (the +-20 % density field
+  produces contacts at 1.8 Angstrom).
+* On-site energies: 6 functions per molecule use types [0,1,1,1,2,2] with -1.0, -0.5, +0.3 Ha and
+  four occupied orbitals per molecule. 23 functions per molecule draw one energy per function slot
+  from N(-0.5, 0.3) Ha once per system; their occupied count (not given for that workload) is the m
+  in 2..8 with the widest gap between the m-th and (m+1)-th lowest drawn energies, so the system is
+  an insulator like the 6-function one.
 
 Block-CSR layout (shared input format): block row I lists the molecules J with a stored block (I, J)
 in ascending order; block (I, J) is b_I x b_J, row-major, and blocks are concatenated in CSR order,
@@ -56,7 +60,7 @@ class SystemSpec:
     s_exp: float = 0.5
     hop: float = -0.2
     hop_len: float = 1.5
-    occ_per_mol: int = 4
+    occ_per_mol: int = 4        # occupied orbitals of a 6-function molecule
     seed: int = 0
 
     @property
@@ -94,9 +98,11 @@ class System:
     def n_basis(self) -> int:
         return int(self.nbf.sum())
 
+    occ: Optional[np.ndarray] = None   # int32 [n_mol], occupied orbitals per molecule
+
     @property
     def n_occ(self) -> float:
-        return float(self.spec.occ_per_mol * self.n_mol)
+        return float(np.sum(self.occ))
 
 
 # ------------------------------------------------------------------------------------ geometry
@@ -239,13 +245,16 @@ def make_system(spec: SystemSpec) -> System:
     else:
         raise ValueError(f"unknown nbf mode {spec.nbf!r}")
     onsite = [ONSITE_6 if b == 6 else eps23 for b in nbf]
+    srt = np.sort(eps23)
+    m23 = int(2 + np.argmax(srt[2:9] - srt[1:8]))      # widest gap after the m-th level, m in 2..8
+    occ = np.where(nbf == 6, spec.occ_per_mol, m23).astype(np.int32)
     # fixed per-slot direction vectors for the optional anisotropic modulation (S: 0, H: 1)
     dirs = rng.normal(size=(2, 23, 3))
 
     rc_h = spec.cutoff if spec.cutoff_h is None else spec.cutoff_h
 
     def s_val(r, dhat, b1, b2, dirs):
-        base = (6.0 / np.sqrt(b1 * b2)) * np.exp(-spec.s_exp * r * r)[:, None, None]
+        base = (1.0 / np.sqrt(b1 * b2)) * np.exp(-spec.s_exp * r * r)[:, None, None]
         if spec.aniso == 0.0:
             return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
         ua = dhat @ dirs[0, :b1].T          # [k, b1]
@@ -253,7 +262,7 @@ def make_system(spec: SystemSpec) -> System:
         return base * (1.0 + spec.aniso * (ua[:, :, None] - uc[:, None, :]))
 
     def h_val(r, dhat, b1, b2, dirs):
-        base = (6.0 / np.sqrt(b1 * b2)) * (spec.hop * np.exp(-r / spec.hop_len))[:, None, None]
+        base = (1.0 / np.sqrt(b1 * b2)) * (spec.hop * np.exp(-r / spec.hop_len))[:, None, None]
         if spec.aniso == 0.0:
             return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
         ua = dhat @ dirs[1, :b1].T
@@ -268,7 +277,7 @@ def make_system(spec: SystemSpec) -> System:
                       lambda i, b: np.eye(b), n)
     H = _build_blocks(I[sel_h], J[sel_h], d[sel_h], nbf, onsite, dirs, h_val,
                       lambda i, b: np.diag(onsite[i]), n)
-    return System(spec=spec, pos=pos, cell=cell, nbf=nbf, onsite=onsite, S=S, H=H)
+    return System(spec=spec, pos=pos, cell=cell, nbf=nbf, onsite=onsite, S=S, H=H, occ=occ)
 
 
 # ------------------------------------------------------------------------------------ named workloads
@@ -281,6 +290,11 @@ def spec_small_fp64(**kw) -> SystemSpec:
 def spec_batched_uneven(**kw) -> SystemSpec:
     """32,768 molecules (32x32x32) with a +-20 % local density field."""
     return SystemSpec(32, 32, 32, **{"density_amp": 0.2, "seed": 1002, **kw})
+
+
+def spec_batched_uneven_4096(**kw) -> SystemSpec:
+    """4,096 molecules (16x16x16) with the same +-20 % field: a smaller case of the same workload."""
+    return SystemSpec(16, 16, 16, **{"density_amp": 0.2, "seed": 1012, **kw})
 
 
 def spec_streamed_bf16(**kw) -> SystemSpec:
