@@ -207,6 +207,39 @@ nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);
 nolsm_status nolsm_plan_stats_reset(nolsm_plan* plan);
 
 void nolsm_plan_destroy(nolsm_plan* plan);
+
+/* Allocation-free sign iteration. No counterpart in the paper.
+ *
+ * For callers that cannot call cudaMalloc when they need a result: a host application or MD engine
+ * that owns all device memory through its own pool (a stray cudaMalloc would bypass its accounting or
+ * fail against its reservation), or code with a fixed device-memory budget that must not allocate
+ * while it runs. It runs the same tensor-core kernel as nolsm_solve_batch (a4-a7: scale, Newton-Schulz
+ * sign iteration with the defect test and refinement, centre columns of D and the partial traces) on
+ * inputs the caller already holds, using scratch that lives in a static device array inside the
+ * library (about 6.3 MB; every GPU that loads the library keeps it until the process exits).
+ *
+ * Inputs (device, caller-owned) for submatrix i in [0, count):
+ *   sub_n[i] dimension n_i (1..192), nbf[i] number b_i of centre columns,
+ *   a_off[i] element offset of A_i in A, c_off[i] element offset of the n_i x b_i arrays,
+ *   A    FP32, A_i = T(S)^-1 T(H0) row-major n_i x n_i,
+ *   Q    FP64, the centre columns of T(S)^-1 (n_i x b_i row-major),
+ *   Sc, Hc FP64, the centre columns of T(S) and T(H0),
+ *   lam  FP64 [2*count], an interval [lam[2i], lam[2i+1]] that contains the spectrum of A_i,
+ *   mu, opts (precision NOLSM_FP32, NOLSM_BF16X3 or NOLSM_BF16; tolerances, caps; range fields unused).
+ * Outputs (device, caller-owned): Dc (n_i x b_i at c_off[i], the centre columns of T(D)), t_S[i], t_H[i],
+ *   iters[i], status[i] (per-submatrix nolsm_status).
+ * Limits: 1 <= count <= 4096 and every n_i <= 192, else NOLSM_ERR_UNSUPPORTED with a message; the sizes
+ * are read back to the host first (this synchronises the stream), then the work is enqueued and the call
+ * returns; results are ready when the stream reaches that point.
+ * The first call on a device looks up the device address of the static array; make that first call
+ * before any stream capture. All calls share the one array (the call resets its counters on the stream
+ * first), so calls that overlap on the GPU, from different streams or host threads on one device, race:
+ * the caller must serialise them. */
+nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, const int32_t* nbf, const int64_t* a_off,
+                                const int64_t* c_off, const float* A, const double* Q, const double* Sc,
+                                const double* Hc, const double* lam, double mu, const nolsm_options* opts,
+                                nolsm_stream_t stream, double* Dc, double* t_S, double* t_H, int32_t* iters,
+                                int32_t* status);
 const char* nolsm_status_str(nolsm_status s);
 const char* nolsm_last_error(void);
 

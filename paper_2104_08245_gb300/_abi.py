@@ -64,6 +64,8 @@ SIGNATURES = [
     ("nolsm_plan_stats", c_int32, [c_void_p, ctypes.POINTER(NolsmStats)]),
     ("nolsm_plan_stats_reset", c_int32, [c_void_p]),
     ("nolsm_plan_destroy", None, [c_void_p]),
+    ("nolsm_sign_noalloc", c_int32, [c_int32] + [c_void_p] * 9 + [c_double, ctypes.POINTER(NolsmOptions), c_void_p]
+     + [c_void_p] * 5),
     ("nolsm_status_str", ctypes.c_char_p, [c_int32]),
     ("nolsm_last_error", ctypes.c_char_p, []),
 ]

@@ -590,4 +590,127 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   return NOLSM_OK;
 }
 
+// ==================================================================================== no-allocation entry point
+// Some callers cannot call cudaMalloc at the moment they need a sign iteration: an MD engine or other
+// host framework that owns every byte of device memory through its own pool, or code that must not
+// allocate while it runs (fixed memory budgets, allocation-free inner loops). For them the tensor-core
+// kernel above can also run on scratch that lives in this file's static device array instead of a
+// plan's workspaces. Every GPU that loads the library holds the array until the process exits.
+
+namespace {
+
+constexpr int kNaMaxN = 192;                  // largest submatrix dimension accepted
+constexpr int kNaR = 256, kNaLD = 192;        // scratch plane shape: rows rounded to 128, columns to 64
+constexpr int kNaSlots = 8;                   // CTAs (one scratch slot each)
+constexpr int kNaMaxSub = 4096;               // submatrices per call
+constexpr size_t kNaPlaneElems = (size_t)kNaR * kNaLD;
+constexpr size_t kNaPlanesBytes = sizeof(uint16_t) * kPlanes * kNaSlots * kNaPlaneElems;
+constexpr size_t kNaXfBytes = sizeof(float) * kNaSlots * kNaPlaneElems;
+constexpr size_t kNaIntBytes = sizeof(int32_t) * (3 * (size_t)kNaMaxSub + 64);
+constexpr size_t kNaBytes = kNaPlanesBytes + kNaXfBytes + kNaIntBytes;   // about 6.3 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Identity work order, zero factorisation status, zero counters: what the kernel expects to find.
+__global__ void k_noalloc_reset(unsigned char* base, int count) {
+  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes + kNaXfBytes);
+  int32_t* order = ints;
+  int32_t* prep = ints + kNaMaxSub;
+  int32_t* rst = ints + 2 * kNaMaxSub;
+  int32_t* ctr = ints + 3 * kNaMaxSub;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    order[i] = i;
+    prep[i] = kSubOk;
+    rst[i] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 64) ctr[threadIdx.x] = 0;
+}
+
+void* g_na_addr[64] = {};
+
+}  // namespace
+
 }  // namespace nolsm
+
+extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, const int32_t* nbf,
+                                           const int64_t* a_off, const int64_t* c_off, const float* A, const double* Q,
+                                           const double* Sc, const double* Hc, const double* lam, double mu,
+                                           const nolsm_options* opts, nolsm_stream_t stream, double* Dc,
+                                           double* t_S, double* t_H, int32_t* iters, int32_t* status) {
+  using namespace nolsm;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!opts || !sub_n || !nbf || !a_off || !c_off || !A || !Q || !Sc || !Hc || !lam || !Dc || !t_S || !t_H ||
+      !iters || !status || !std::isfinite(mu)) {
+    set_error("nolsm_sign_noalloc: NULL argument or non-finite mu");
+    return NOLSM_ERR_ARG;
+  }
+  if (count < 1 || count > kNaMaxSub) {
+    set_error("nolsm_sign_noalloc: %d submatrices requested; this entry point takes 1..%d per call", count,
+              kNaMaxSub);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  Fmt mf, rf;
+  if (!formats(opts->precision, &mf, &rf)) {
+    set_error("nolsm_sign_noalloc: precision %d is not a tensor-core mode", opts->precision);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  if (opts->max_iter < 1 || opts->refine_steps < 0 || !(opts->tol_ns > 0) || !(opts->tol_accept > 0)) {
+    set_error("nolsm_sign_noalloc: invalid options");
+    return NOLSM_ERR_ARG;
+  }
+  // sizes are checked against the static scratch before anything is launched
+  int32_t h_n[kNaMaxSub];
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(h_n, sub_n, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) {
+    if (h_n[i] < 1 || h_n[i] > kNaMaxN) {
+      set_error("nolsm_sign_noalloc: submatrix %d has dimension %d; this entry point takes 1..%d", i, h_n[i],
+                kNaMaxN);
+      return NOLSM_ERR_UNSUPPORTED;
+    }
+  }
+  // once per device: the device address of this file's static scratch array
+  int dev = 0;
+  NOLSM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("nolsm_sign_noalloc: device ordinal %d out of range", dev);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  if (!g_na_addr[dev]) {
+    void* p = nullptr;
+    NOLSM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_na_addr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_na_addr[dev]);
+  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes + kNaXfBytes);
+
+  CUtensorMap mA, mB;
+  if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
+      !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64)) {
+    set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
+    return NOLSM_ERR_CUDA;
+  }
+  k_noalloc_reset<<<(count + 255) / 256, 256, 0, st>>>(base, count);
+  NOLSM_LAUNCH_CHECK();
+  TcArgs g;
+  g.j0 = 0; g.j1 = count;
+  g.order = ints;
+  g.sub_n = sub_n; g.nbf = nbf; g.a_off = a_off; g.c_off = c_off;
+  g.A = A; g.Q = Q; g.Sc = Sc; g.Hc = Hc; g.lam = lam;
+  g.prep_status = ints + kNaMaxSub;
+  g.mu = mu;
+  g.tol_ns = (float)opts->tol_ns; g.tol_accept = (float)opts->tol_accept;
+  g.max_iter = opts->max_iter; g.refine_steps = opts->refine_steps;
+  g.main_fmt = mf; g.refine_fmt = rf;
+  g.planes = reinterpret_cast<uint16_t*>(base);
+  g.xf = reinterpret_cast<float*>(base + kNaPlanesBytes);
+  g.R = kNaR; g.LD = kNaLD;
+  g.next = ints + 3 * kNaMaxSub;
+  g.err = ints + 3 * kNaMaxSub + 32;
+  g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
+  g.rsteps = ints + 2 * kNaMaxSub;
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  k_ns_tc<<<std::min(kNaSlots, count), kThreads, kSmemBytes, st>>>(mA, mB, g);
+  NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
