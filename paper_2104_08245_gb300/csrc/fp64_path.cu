@@ -401,7 +401,9 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     pa.a_off = plan->a_off.as<int64_t>(); pa.c_off = plan->c_off.as<int64_t>();
     pa.a_base = g.a_base; pa.chunk_n2 = n2; pa.ws = g.ws;
     pa.Q = plan->Q.as<double>(); pa.lam = plan->lam.as<double>(); pa.prep_status = plan->prep_status.as<int32_t>();
-    NOLSM_TRY(launch_prepare(pa, (int)(e - J), keep_fp64_A, P.A.p, st));
+    int chunk_max_n = 1;
+    for (int64_t k = J; k < e; ++k) chunk_max_n = std::max(chunk_max_n, plan->h_sub_n[k]);
+    NOLSM_TRY(launch_prepare(pa, (int)(e - J), chunk_max_n, keep_fp64_A, P.A.p, st));
     plan->stats.launches += 2;
     for (int64_t k = J; k < e; ++k) {
       const double m = plan->h_sub_n[k], b = plan->h_nbf[k];

@@ -16,7 +16,7 @@ struct PrepArgs {
   int32_t* prep_status;
 };
 
-// a2-a3 for `count` submatrices starting at g.j0; A in FP64 (fp64_A) or FP32.
-nolsm_status launch_prepare(const PrepArgs& g, int count, bool fp64_A, void* Acache, cudaStream_t st);
+// a2-a3 for `count` submatrices starting at g.j0 (largest dimension max_n); A in FP64 (fp64_A) or FP32.
+nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A, void* Acache, cudaStream_t st);
 
 }  // namespace nolsm
