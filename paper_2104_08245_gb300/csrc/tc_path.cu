@@ -29,12 +29,13 @@ namespace nolsm {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;   // warp 0 TMA, warp 1 MMA, warps 4-11 two epilogue groups
 constexpr int kStages = 2;
 constexpr uint32_t kABytes = 128 * 64 * 2;        // one A plane slice: 128 rows x 64 K
 constexpr uint32_t kBBytes = 64 * 256 * 2;        // one B plane slice: 64 K x up to 256 columns
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint32_t kStgBytes = 128 * 64;                // one 128 x 32 chunk of one 2-byte plane
+constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + hi/lo staging per epilogue group
 constexpr int kPlanes = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
 
@@ -73,8 +74,8 @@ struct Shared {
   // decisions made after each GEMM0 (read by every role after the block-wide barrier that ends it)
   int last, status, phase, refine_left, steps, rsteps;
   Fmt cur, nxt;
-  float red[4];
-  double dred[2][8];
+  float red[8];
+  double dred[2][kThreads / 32];
 };
 
 __device__ __forceinline__ uint16_t to_bits(float x, int fmt) {
@@ -103,22 +104,15 @@ __device__ __forceinline__ void split2(float a, float b, int fmt, uint32_t& hi, 
   }
 }
 
-// Writes 32 consecutive values of one row as hi (and lo) planes.
-__device__ __forceinline__ void store_split(uint16_t* hi, uint16_t* lo, const float (&v)[32], Fmt f) {
-  uint32_t h[16], l[16];
+// 32 consecutive values of one row as packed hi (and lo) pairs.
+__device__ __forceinline__ void split_pack(const float (&v)[32], Fmt f, uint32_t (&h)[16], uint32_t (&l)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) split2(v[2 * j], v[2 * j + 1], f.fmt, h[j], l[j]);
-  uint4* H = reinterpret_cast<uint4*>(hi);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) H[q] = make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-  if (f.terms > 1) {
-    uint4* L = reinterpret_cast<uint4*>(lo);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) L[q] = make_uint4(l[4 * q], l[4 * q + 1], l[4 * q + 2], l[4 * q + 3]);
-  }
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// named barriers: 1 + group for one epilogue group (128 threads), 3 for both groups (256 threads)
+__device__ __forceinline__ void group_bar(int grp) { asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 3, 256;" ::: "memory"); }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
@@ -135,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sh.accf[b], 1);
-      tc::mbar_init(&sh.acce[b], 128);
+      tc::mbar_init(&sh.acce[b], 256);
     }
     tc::mbar_init(&sh.idle, 1);
     tc::fence_mbar_init();
@@ -155,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // pipeline counters (each role keeps the ones it uses; all roles walk the same schedule)
   uint32_t kcount = 0;   // K slices issued (producer) / consumed (MMA)
   uint32_t tcount = 0;   // tiles accumulated (MMA) / drained (epilogue)
+  uint8_t* const stg = stage_mem + kStages * kStageBytes;   // per epilogue group: hi, lo chunks of 128 x 32 x 2 B
   uint32_t arm_phase[kStages] = {0, 0};  // producer: parity of the last load armed per stage
   bool armed[kStages] = {false, false};
   const size_t plane_elems = (size_t)g.R * g.LD;
@@ -288,13 +283,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         } else if (warp >= 4) {
           // ------------------------------------------------ epilogue
-          const int q = warp - 4;
+          const int q = warp & 3;                // TMEM lane quarter of this warp
+          const int grp = (warp - 4) >> 2;       // epilogue group: even or odd 32-column chunks
+          const int gbase = 128 + 128 * grp;     // first thread of this epilogue group
           float part = 0.0f;
           const bool last = kind == 1 && sh.last;   // decided after this step's GEMM0
           const Fmt fo = kind == 0 ? f : sh.nxt;    // format of the written operand
           const int out_plane = kind == 0 ? 4 : 2 * (cur ^ 1);
-          uint16_t* ohi = g.planes + ((size_t)slot * kPlanes + out_plane) * plane_elems;
-          uint16_t* olo = ohi + plane_elems;
           float* xf = g.xf + (size_t)slot * plane_elems;
           for (int mb = 0; mb < nrb && !sh.err; ++mb)
             for (int cb = 0; cb < ncb && !sh.err; ++cb) {
@@ -306,30 +301,69 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               tc::tc_fence_after();
               const int row = 128 * mb + 32 * q + lane;
-              for (int c0 = 0; c0 < nt / 32; ++c0) {
-                uint32_t r[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256 + 32 * c0, r);
-                tc::tmem_wait_ld();
+              const bool live = 128 * mb + 32 * q < n64;   // rows >= n64 are never read back
+              const int nch = nt / 32;
+              const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
+              uint32_t r[32];
+              if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
+              for (int c0 = grp; c0 < nch; c0 += 2) {
                 const int col0 = 256 * cb + 32 * c0;
                 float v[32];
-                if (kind == 0) {
+                if (live) {
+                  tc::tmem_wait_ld();
+                  if (kind == 0) {
 #pragma unroll
-                  for (int j = 0; j < 32; ++j) {
-                    const int col = col0 + j;
-                    const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
-                    if (row < n && col < n) part += e * e;
-                    v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
+                    for (int j = 0; j < 32; ++j) {
+                      const int col = col0 + j;
+                      const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
+                      if (row < n && col < n) part += e * e;
+                      v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
+                    }
+                  } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
                   }
-                  store_split(ohi + (size_t)row * g.LD + col0, olo + (size_t)row * g.LD + col0, v, fo);
-                } else {
-#pragma unroll
-                  for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
-                  if (last) {
+                  if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
+                }
+                if (last) {
+                  if (live) {
                     float4* d = reinterpret_cast<float4*>(xf + (size_t)row * g.LD + col0);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                  } else {
-                    store_split(ohi + (size_t)row * g.LD + col0, olo + (size_t)row * g.LD + col0, v, fo);
+                  }
+                } else {
+                  // transpose the 128 x 32 chunk through shared memory so that the global stores are
+                  // row-contiguous across the warp; 64-byte rows, 16-byte unit c of row r stored at unit
+                  // c ^ ((r >> 1) & 3) (conflict-free for the row-per-thread writes and the reads)
+                  uint8_t* shi = stg + grp * 2 * kStgBytes;
+                  uint8_t* slo = shi + kStgBytes;
+                  group_bar(grp);   // the group's previous chunk has been read out of the staging buffer
+                  if (live) {
+                    uint32_t h[16], l[16];
+                    split_pack(v, fo, h, l);
+                    const int lr = 32 * q + lane;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                      const int off = lr * 64 + ((c ^ ((lr >> 1) & 3)) << 4);
+                      *reinterpret_cast<uint4*>(shi + off) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                      if (fo.terms > 1)
+                        *reinterpret_cast<uint4*>(slo + off) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                    }
+                  }
+                  group_bar(grp);
+                  const int gt = tid - gbase;    // 0..127 within the group
+                  uint16_t* ghi = g.planes + ((size_t)slot * kPlanes + out_plane) * plane_elems;
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    const int lr = 32 * k + (gt >> 2), u = gt & 3;
+                    const int grow = 128 * mb + lr;
+                    if (grow < n64) {
+                      const size_t at = (size_t)grow * g.LD + col0 + 8 * u;
+                      const int off = lr * 64 + ((u ^ ((lr >> 1) & 3)) << 4);
+                      *reinterpret_cast<uint4*>(ghi + at) = *reinterpret_cast<const uint4*>(shi + off);
+                      if (fo.terms > 1)
+                        *reinterpret_cast<uint4*>(ghi + plane_elems + at) = *reinterpret_cast<const uint4*>(slo + off);
+                    }
                   }
                 }
               }
@@ -341,10 +375,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (kind == 0) {
             // defect of X_step and the decision about the following steps
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) sh.red[q] = part;
+            if (lane == 0) sh.red[warp - 4] = part;
             epi_bar();
             if (tid == 128) {
-              const float d = sqrtf((sh.red[0] + sh.red[1] + sh.red[2] + sh.red[3]) / (float)n);
+              float dsum = 0.0f;
+              for (int w = 0; w < 8; ++w) dsum += sh.red[w];
+              const float d = sqrtf(dsum / (float)n);
               const int steps = sh.steps + 1;
               if (sh.phase == 1) sh.rsteps += 1;   // this step ran in the refinement format
               int last_ = 0, status = kSubNotConv;
