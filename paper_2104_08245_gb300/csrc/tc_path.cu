@@ -7,13 +7,20 @@
 // three-term split hi*hi + hi*lo + lo*hi with x = hi + lo (hi = round(x), lo = round(x - hi)),
 // accumulated in FP32 in tensor memory.
 //
-// One persistent CTA per SM works on one submatrix at a time (submatrices taken largest first from
-// a work counter). Operands live in a per-CTA scratch slot in global memory (L2-resident) as 2-byte
-// planes [X0 hi, X0 lo, X1 hi, X1 lo, T hi, T lo], each R x LD (R = n rounded up to 128 rows,
-// LD = n rounded up to 64 columns, zero padded). Output tiles are 128 rows x up to 256 columns; the
-// K dimension streams in slices of 64 through a two-stage TMA pipeline with 128-byte swizzle.
-// Warp roles: warp 0 issues TMA, warp 1 (one thread) issues tcgen05.mma, warps 4-7 drain the
-// double-buffered TMEM accumulators (2 x 256 columns). All waits are bounded by the global timer.
+// One persistent CTA per SM keeps two submatrices in flight ("slots", taken largest first from a
+// work counter) and interleaves their products: while the tensor cores run a product of one slot,
+// the epilogue drains, rounds and stores the previous product of the other, so neither the operand
+// fill nor the epilogue of a product serialises the CTA. Operands live in per-slot scratch in global
+// memory (L2-resident) as 2-byte planes [X0 hi, X0 lo, X1 hi, X1 lo, T hi, T lo], each R x LD
+// (R = n rounded up to 128 rows, LD = n rounded up to 64 columns, zero padded). Output tiles are
+// 128 rows x up to 256 columns; the K dimension streams in slices of 64 through a two-stage TMA
+// pipeline with 128-byte swizzle; the epilogue writes the rounded planes back with TMA stores.
+// Warp roles: warp 0 (one thread) schedules the products of both slots and issues their TMA loads,
+// publishing one descriptor per product in a small ring; warp 1 (one thread) issues tcgen05.mma in
+// that order; warps 4-11 (two groups of four, even and odd 32-column chunks) drain the
+// double-buffered TMEM accumulators (2 x 256 columns), decide convergence and start and finish the
+// slots' submatrices. All waits are bounded by the global timer; a wait that runs out marks the
+// submatrices in flight as timed out.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -66,16 +73,39 @@ struct TcArgs {
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
 };
 
+constexpr int kSlots = 2;   // submatrices in flight per CTA (their products interleave)
+constexpr int kRing = 4;    // product descriptors between the scheduler and the MMA / epilogue warps
+
+// Iteration state of one in-flight submatrix. Written by the epilogue (thread 128) before it arrives
+// on the slot's epi_done barrier; read by the scheduler after waiting on that barrier.
+struct SlotState {
+  int job;                       // submatrix index, -1 when the slot has retired
+  int n, n64, R, nrb, ncb, nks;  // dimension and tiling
+  int kind;                      // next product: 0 (X X) or 1 (X T)
+  int cur;                       // which X plane pair holds the current iterate
+  int phase, refine_left, steps, rsteps, status, last;
+  Fmt fcur, fnxt;
+};
+
+// One product as scheduled by the producer: read in order by the MMA issuer and the epilogue.
+struct Desc {
+  int term;                      // 1: no more products, exit
+  int slot, kind, last;
+  Fmt f, fo;                     // format of the operands; of the operand the epilogue writes
+  int n, n64, nrb, ncb, nks;
+  int za, zb, zo;                // plane indices (hi planes) of A, B and the output
+};
+
 struct Shared {
   uint64_t full[kStages], empty[kStages], accf[2], acce[2], idle;
+  uint64_t epi_done[kSlots], desc_full[kRing];
   uint32_t tmem;
-  int job;
   int err;
-  // decisions made after each GEMM0 (read by every role after the block-wide barrier that ends it)
-  int last, status, phase, refine_left, steps, rsteps;
-  Fmt cur, nxt;
-  float red[8];
-  double dred[2][kThreads / 32];
+  int fetch;
+  SlotState slot[kSlots];
+  Desc ring[kRing];
+  float red[2][8];               // defect partial sums, by product parity
+  double dred[2][8];
 };
 
 __device__ __forceinline__ uint16_t to_bits(float x, int fmt) {
@@ -113,14 +143,24 @@ __device__ __forceinline__ void split_pack(const float (&v)[32], Fmt f, uint32_t
 // named barriers: 1 + group for one epilogue group (128 threads), 3 for both groups (256 threads)
 __device__ __forceinline__ void group_bar(int grp) { asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 3, 256;" ::: "memory"); }
+// barrier 3 with an OR over the 256 epilogue threads' predicates
+__device__ __forceinline__ bool epi_bar_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred P, Q;\n\tsetp.ne.u32 P, %1, 0;\n\tbar.red.or.pred Q, 3, 256, P;\n\tselp.u32 %0, 1, 0, Q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs g) {
+    k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+            const __grid_constant__ CUtensorMap mapS, TcArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Shared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int slot = blockIdx.x;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -131,11 +171,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&sh.accf[b], 1);
       tc::mbar_init(&sh.acce[b], 256);
     }
+    for (int s = 0; s < kSlots; ++s) tc::mbar_init(&sh.epi_done[s], 256);
+    for (int r = 0; r < kRing; ++r) tc::mbar_init(&sh.desc_full[r], 1);
     tc::mbar_init(&sh.idle, 1);
     tc::fence_mbar_init();
     sh.err = 0;
     tc::prefetch_tmap(&mapA);
     tc::prefetch_tmap(&mapB);
+    tc::prefetch_tmap(&mapS);
   }
   if (warp == 0) {
     tc::tmem_alloc(&sh.tmem, 512);
@@ -145,359 +188,417 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = sh.tmem;
-
-  // pipeline counters (each role keeps the ones it uses; all roles walk the same schedule)
-  uint32_t kcount = 0;   // K slices issued (producer) / consumed (MMA)
-  uint32_t tcount = 0;   // tiles accumulated (MMA) / drained (epilogue)
-  uint8_t* const stg = stage_mem + kStages * kStageBytes;   // per epilogue group: hi, lo chunks of 128 x 32 x 2 B
-  uint32_t arm_phase[kStages] = {0, 0};  // producer: parity of the last load armed per stage
-  bool armed[kStages] = {false, false};
   const size_t plane_elems = (size_t)g.R * g.LD;
+  uint8_t* const stg = stage_mem + kStages * kStageBytes;   // per epilogue group: hi, lo chunks of 128 x 32 x 2 B
+  const int sub0 = blockIdx.x * kSlots;                      // scratch sub-slot of this CTA's slot 0
+  uint32_t arm_phase[kStages] = {0, 0};                      // producer: parity of the last load armed per stage
+  bool armed[kStages] = {false, false};
 
-  for (;;) {
-    if (tid == 0) {
-      const int k = atomicAdd(g.next, 1);
-      sh.job = (k < g.j1 - g.j0 && !sh.err) ? g.order[k] : -1;
-    }
-    __syncthreads();
-    const int J = sh.job;
-    if (J < 0) break;
-    if (g.prep_status[J] != kSubOk) {
-      if (tid == 0) {
-        g.status[J] = g.prep_status[J];
-        g.iters[J] = 0;
-        g.rsteps[J] = 0;
-        g.tS[J] = 0.0;
-        g.tH[J] = 0.0;
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ producer: schedules the products of both slots
+    // round robin over live slots; a slot's next product is issued once the epilogue of its previous
+    // product (or its initialisation) has arrived on the slot's epi_done barrier
+    bool alive[kSlots] = {true, true};
+    uint32_t epar[kSlots] = {0, 0};
+    uint32_t kcount = 0;
+    int s = 0;
+    for (uint32_t i = 0;; ++i) {
+      int pick = -1;
+      while (!sh.err && (alive[0] || alive[1])) {
+        if (alive[s]) {
+          if (!tc::mbar_wait(&sh.epi_done[s], epar[s], tc::globaltimer() + 4 * kWaitNs)) { sh.err = 1; break; }
+          epar[s] ^= 1;
+          tc::fence_proxy_async_global();   // the epilogue's plane writes, before TMA reads them
+          if (sh.slot[s].job >= 0) { pick = s; break; }
+          alive[s] = false;
+        }
+        s ^= 1;
       }
-      __syncthreads();
-      continue;
-    }
-    const int n = g.sub_n[J];
-    const int n64 = (n + 63) & ~63;
-    const int R = (n + 127) & ~127;
-    const int nrb = R / 128, ncb = (n64 + 255) / 256;
-    const int nks = n64 / 64;
-
-    // ---- a4: X_0 = (A - mu I) / alpha into plane X0 (hi, lo) in the main format, zero padded
-    {
-      const float* A = g.A + g.a_off[J];
-      const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
-      const float inv = (float)(1.0 / alpha);
-      const float fmu = (float)g.mu;
-      uint16_t* hi = g.planes + ((size_t)slot * kPlanes + 0) * plane_elems;
-      uint16_t* lo = g.planes + ((size_t)slot * kPlanes + 1) * plane_elems;
-      const Fmt f = g.main_fmt;
-      for (int e = tid; e < R * n64; e += kThreads) {
-        const int i = e / n64, j = e - i * n64;
-        float x = 0.0f;
-        if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
-        const uint16_t h = to_bits(x, f.fmt);
-        hi[(size_t)i * g.LD + j] = h;
-        if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+      Desc d;
+      d.term = pick < 0 ? 1 : 0;
+      if (pick >= 0) {
+        const SlotState& st = sh.slot[pick];
+        d.slot = pick;
+        d.kind = st.kind;
+        d.last = st.kind == 1 && st.last;
+        d.f = st.fcur;
+        d.fo = st.kind == 0 ? st.fcur : st.fnxt;
+        d.n = st.n; d.n64 = st.n64; d.nrb = st.nrb; d.ncb = st.ncb; d.nks = st.nks;
+        const int zb = (sub0 + pick) * kPlanes;
+        d.za = zb + 2 * st.cur;
+        d.zb = st.kind == 0 ? d.za : zb + 4;
+        d.zo = st.kind == 0 ? zb + 4 : zb + 2 * (st.cur ^ 1);
       }
-      if (tid == 0) {
-        sh.last = 0;
-        sh.status = kSubNotConv;
-        sh.phase = 0;
-        sh.refine_left = g.refine_steps;
-        sh.steps = 0;
-        sh.rsteps = 0;
-        sh.cur = g.main_fmt;
-        sh.nxt = g.main_fmt;
-      }
-      tc::fence_proxy_async_global();
-      __syncthreads();
-    }
-
-    // ---- a5/a6: the iteration; every role walks the same sequence of GEMMs
-    int cur = 0;          // X ping-pong index
-    bool stop = false;
-    for (int step = 0; !stop; ++step) {
-      for (int kind = 0; kind < 2; ++kind) {
-        const Fmt f = sh.cur;                 // stable during this step (written only before GEMM0 ends)
-        const int two = f.terms > 1 ? 2 : 1;
-        const int a_plane = 2 * cur;          // X_cur hi (lo = +1)
-        const int b_plane = kind == 0 ? 2 * cur : 4;
-        if (warp == 0 && lane == 0) {
-          // ------------------------------------------------ producer
-          for (int mb = 0; mb < nrb && !sh.err; ++mb)
-            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
-              const int nt = min(256, n64 - 256 * cb);
-              const uint32_t bytes = (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
-              for (int ks = 0; ks < nks; ++ks) {
-                const int s = kcount % kStages;
-                const uint32_t ph = (kcount / kStages) & 1;
-                if (!tc::mbar_wait(&sh.empty[s], ph ^ 1, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
-                uint8_t* st = stage_mem + s * kStageBytes;
-                tc::mbar_arrive_expect_tx(&sh.full[s], bytes);
-                armed[s] = true;
-                arm_phase[s] = ph;
-                for (int z = 0; z < two; ++z) {
-                  tc::tma_load_3d(st + z * kABytes, &mapA, &sh.full[s], 64 * ks, 128 * mb, slot * kPlanes + a_plane + z);
-                  uint8_t* bdst = st + 2 * kABytes + z * kBBytes;
-                  for (int c = 0; c < nt / 64; ++c)
-                    tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[s], 256 * cb + 64 * c, 64 * ks,
-                                    slot * kPlanes + b_plane + z);
-                }
-                ++kcount;
-              }
+      sh.ring[i % kRing] = d;
+      tc::mbar_arrive(&sh.desc_full[i % kRing]);
+      if (d.term) break;
+      const int two = d.f.terms > 1 ? 2 : 1;
+      for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
+        for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
+          const int nt = min(256, d.n64 - 256 * cb);
+          const uint32_t bytes = (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
+          for (int ks = 0; ks < d.nks; ++ks) {
+            const int st = kcount % kStages;
+            const uint32_t ph = (kcount / kStages) & 1;
+            if (!tc::mbar_wait(&sh.empty[st], ph ^ 1, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+            uint8_t* sm = stage_mem + st * kStageBytes;
+            tc::mbar_arrive_expect_tx(&sh.full[st], bytes);
+            armed[st] = true;
+            arm_phase[st] = ph;
+            for (int z = 0; z < two; ++z) {
+              tc::tma_load_3d(sm + z * kABytes, &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
+              uint8_t* bdst = sm + 2 * kABytes + z * kBBytes;
+              for (int c = 0; c < nt / 64; ++c)
+                tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], 256 * cb + 64 * c, 64 * ks, d.zb + z);
             }
-        } else if (warp == 1 && lane == 0) {
-          // ------------------------------------------------ MMA issuer
-          for (int mb = 0; mb < nrb && !sh.err; ++mb)
-            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
-              const int nt = min(256, n64 - 256 * cb);
-              const uint32_t id = tc::idesc(f.fmt, f.fmt, 0, 1, 128, nt);
-              const int buf = tcount & 1;
-              if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + kWaitNs)) {
-                sh.err = 1;
-                break;
-              }
-              tc::tc_fence_after();
-              const uint32_t dt = tmem + (uint32_t)buf * 256;
-              for (int ks = 0; ks < nks; ++ks) {
-                const int s = kcount % kStages;
-                const uint32_t ph = (kcount / kStages) & 1;
-                if (!tc::mbar_wait(&sh.full[s], ph, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
-                tc::tc_fence_after();
-                const uint32_t a0 = tc::smem_u32(stage_mem + s * kStageBytes);
-                const uint32_t b0 = a0 + 2 * kABytes;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                  const uint64_t ah = tc::sdesc_sw128(a0 + kk * 32, 16, 1024);
-                  const uint64_t bh = tc::sdesc_sw128(b0 + kk * 2048, 8192, 1024);
-                  tc::mma_f16(dt, ah, bh, id, (ks > 0 || kk > 0) ? 1u : 0u);
-                  if (f.terms > 1) {
-                    const uint64_t al = tc::sdesc_sw128(a0 + kABytes + kk * 32, 16, 1024);
-                    const uint64_t bl = tc::sdesc_sw128(b0 + kBBytes + kk * 2048, 8192, 1024);
-                    tc::mma_f16(dt, ah, bl, id, 1u);
-                    tc::mma_f16(dt, al, bh, id, 1u);
-                  }
-                }
-                tc::mma_commit(&sh.empty[s]);
-                ++kcount;
-              }
-              tc::mma_commit(&sh.accf[buf]);
-              ++tcount;
-            }
-        } else if (warp >= 4) {
-          // ------------------------------------------------ epilogue
-          const int q = warp & 3;                // TMEM lane quarter of this warp
-          const int grp = (warp - 4) >> 2;       // epilogue group: even or odd 32-column chunks
-          const int gbase = 128 + 128 * grp;     // first thread of this epilogue group
-          float part = 0.0f;
-          const bool last = kind == 1 && sh.last;   // decided after this step's GEMM0
-          const Fmt fo = kind == 0 ? f : sh.nxt;    // format of the written operand
-          const int out_plane = kind == 0 ? 4 : 2 * (cur ^ 1);
-          float* xf = g.xf + (size_t)slot * plane_elems;
-          for (int mb = 0; mb < nrb && !sh.err; ++mb)
-            for (int cb = 0; cb < ncb && !sh.err; ++cb) {
-              const int nt = min(256, n64 - 256 * cb);
-              const int buf = tcount & 1;
-              if (!tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + kWaitNs)) {
-                sh.err = 1;
-                break;
-              }
-              tc::tc_fence_after();
-              const int row = 128 * mb + 32 * q + lane;
-              const bool live = 128 * mb + 32 * q < n64;   // rows >= n64 are never read back
-              const int nch = nt / 32;
-              const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
-              uint32_t r[32];
-              if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
-              for (int c0 = grp; c0 < nch; c0 += 2) {
-                const int col0 = 256 * cb + 32 * c0;
-                float v[32];
-                if (live) {
-                  tc::tmem_wait_ld();
-                  if (kind == 0) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                      const int col = col0 + j;
-                      const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
-                      if (row < n && col < n) part += e * e;
-                      v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
-                    }
-                  } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
-                  }
-                  if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
-                }
-                if (last) {
-                  if (live) {
-                    float4* d = reinterpret_cast<float4*>(xf + (size_t)row * g.LD + col0);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) d[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                  }
-                } else {
-                  // transpose the 128 x 32 chunk through shared memory so that the global stores are
-                  // row-contiguous across the warp; 64-byte rows, 16-byte unit c of row r stored at unit
-                  // c ^ ((r >> 1) & 3) (conflict-free for the row-per-thread writes and the reads)
-                  uint8_t* shi = stg + grp * 2 * kStgBytes;
-                  uint8_t* slo = shi + kStgBytes;
-                  group_bar(grp);   // the group's previous chunk has been read out of the staging buffer
-                  if (live) {
-                    uint32_t h[16], l[16];
-                    split_pack(v, fo, h, l);
-                    const int lr = 32 * q + lane;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                      const int off = lr * 64 + ((c ^ ((lr >> 1) & 3)) << 4);
-                      *reinterpret_cast<uint4*>(shi + off) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
-                      if (fo.terms > 1)
-                        *reinterpret_cast<uint4*>(slo + off) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
-                    }
-                  }
-                  group_bar(grp);
-                  const int gt = tid - gbase;    // 0..127 within the group
-                  uint16_t* ghi = g.planes + ((size_t)slot * kPlanes + out_plane) * plane_elems;
-#pragma unroll
-                  for (int k = 0; k < 4; ++k) {
-                    const int lr = 32 * k + (gt >> 2), u = gt & 3;
-                    const int grow = 128 * mb + lr;
-                    if (grow < n64) {
-                      const size_t at = (size_t)grow * g.LD + col0 + 8 * u;
-                      const int off = lr * 64 + ((u ^ ((lr >> 1) & 3)) << 4);
-                      *reinterpret_cast<uint4*>(ghi + at) = *reinterpret_cast<const uint4*>(shi + off);
-                      if (fo.terms > 1)
-                        *reinterpret_cast<uint4*>(ghi + plane_elems + at) = *reinterpret_cast<const uint4*>(slo + off);
-                    }
-                  }
-                }
-              }
-              tc::tc_fence_before();
-              tc::mbar_arrive(&sh.acce[buf]);
-              ++tcount;
-            }
-          tc::fence_proxy_async_global();
-          if (kind == 0) {
-            // defect of X_step and the decision about the following steps
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) sh.red[warp - 4] = part;
-            epi_bar();
-            if (tid == 128) {
-              float dsum = 0.0f;
-              for (int w = 0; w < 8; ++w) dsum += sh.red[w];
-              const float d = sqrtf(dsum / (float)n);
-              const int steps = sh.steps + 1;
-              if (sh.phase == 1) sh.rsteps += 1;   // this step ran in the refinement format
-              int last_ = 0, status = kSubNotConv;
-              Fmt nxt = sh.cur;
-              if (!isfinite(d)) {
-                last_ = 1;
-                status = kSubNonFinite;
-              } else if (sh.phase == 0) {
-                if (d <= g.tol_ns) {
-                  if (g.refine_steps == 0) {
-                    last_ = 1;
-                    status = d <= g.tol_accept ? kSubOk : kSubNotConv;
-                  } else {
-                    sh.phase = 1;
-                    sh.refine_left = g.refine_steps;
-                    nxt = g.refine_fmt;
-                  }
-                }
-              } else {
-                if (--sh.refine_left == 0) {
-                  last_ = 1;
-                  status = d <= g.tol_accept ? kSubOk : kSubNotConv;
-                }
-              }
-              if (!last_ && steps >= g.max_iter) {
-                last_ = 1;
-                status = kSubNotConv;
-              }
-              sh.steps = steps;
-              sh.last = last_;
-              sh.status = status;
-              sh.nxt = nxt;
-            }
+            ++kcount;
           }
         }
-        // every role: this GEMM's epilogue (written and fenced for TMA) feeds the next GEMM; the
-        // block-wide OR makes the error decision uniform
-        if (__syncthreads_or(sh.err)) { stop = true; break; }
-      }
-      if (stop) break;
-      // after GEMM1: swap the ping-pong X and adopt the next format
-      cur ^= 1;
-      stop = sh.last != 0;
-      __syncthreads();   // all roles have read sh.last / sh.nxt for this step
-      if (tid == 0) sh.cur = sh.nxt;
-      __syncthreads();
+      s = pick ^ 1;
     }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issuer: the products in the scheduler's order
+    uint32_t kcount = 0, tcount = 0;
+    for (uint32_t i = 0; !sh.err; ++i) {
+      if (!tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * kWaitNs)) {
+        sh.err = 1;
+        break;
+      }
+      const Desc d = sh.ring[i % kRing];
+      if (d.term) break;
+      for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
+        for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
+          const int nt = min(256, d.n64 - 256 * cb);
+          const uint32_t id = tc::idesc(d.f.fmt, d.f.fmt, 0, 1, 128, nt);
+          const int buf = tcount & 1;
+          if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + kWaitNs)) {
+            sh.err = 1;
+            break;
+          }
+          tc::tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)buf * 256;
+          for (int ks = 0; ks < d.nks; ++ks) {
+            const int st = kcount % kStages;
+            const uint32_t ph = (kcount / kStages) & 1;
+            if (!tc::mbar_wait(&sh.full[st], ph, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_u32(stage_mem + st * kStageBytes);
+            const uint32_t b0 = a0 + 2 * kABytes;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ah = tc::sdesc_sw128(a0 + kk * 32, 16, 1024);
+              const uint64_t bh = tc::sdesc_sw128(b0 + kk * 2048, 8192, 1024);
+              tc::mma_f16(dt, ah, bh, id, (ks > 0 || kk > 0) ? 1u : 0u);
+              if (d.f.terms > 1) {
+                const uint64_t al = tc::sdesc_sw128(a0 + kABytes + kk * 32, 16, 1024);
+                const uint64_t bl = tc::sdesc_sw128(b0 + kBBytes + kk * 2048, 8192, 1024);
+                tc::mma_f16(dt, ah, bl, id, 1u);
+                tc::mma_f16(dt, al, bh, id, 1u);
+              }
+            }
+            tc::mma_commit(&sh.empty[st]);
+            ++kcount;
+          }
+          tc::mma_commit(&sh.accf[buf]);
+          ++tcount;
+        }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------ epilogue: drains products, decides, finishes and starts slots
+    const int etid = tid - 128;              // 0..255
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
+    const int gbase = 128 + 128 * grp;       // first thread of this epilogue group (issues its TMA stores)
+    uint32_t tcount = 0;
 
-    // ---- a7: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the FP64 partial traces
-    {
-      const int b = g.nbf[J];
-      const float* xf = g.xf + (size_t)slot * plane_elems;
+    // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
+    auto start_slot = [&](int s) {
+      SlotState& st = sh.slot[s];
+      for (;;) {
+        if (tid == 128) {
+          const int k = atomicAdd(g.next, 1);
+          sh.fetch = (k < g.j1 - g.j0 && !sh.err) ? g.order[k] : -1;
+        }
+        epi_bar();
+        const int J = sh.fetch;
+        epi_bar();
+        if (J < 0) {
+          if (tid == 128) st.job = -1;
+          break;
+        }
+        if (g.prep_status[J] != kSubOk) {
+          if (tid == 128) {
+            g.status[J] = g.prep_status[J];
+            g.iters[J] = 0;
+            g.rsteps[J] = 0;
+            g.tS[J] = 0.0;
+            g.tH[J] = 0.0;
+          }
+          continue;
+        }
+        const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
+        const float* A = g.A + g.a_off[J];
+        const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
+        const float inv = (float)(1.0 / alpha), fmu = (float)g.mu;
+        uint16_t* hi = g.planes + (size_t)(sub0 + s) * kPlanes * plane_elems;
+        uint16_t* lo = hi + plane_elems;
+        const Fmt f = g.main_fmt;
+        for (int e = etid; e < R * n64; e += 256) {
+          const int i = e / n64, j = e - i * n64;
+          float x = 0.0f;
+          if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
+          const uint16_t h = to_bits(x, f.fmt);
+          hi[(size_t)i * g.LD + j] = h;
+          if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+        }
+        if (tid == 128) {
+          st.job = J;
+          st.n = n; st.n64 = n64; st.R = R;
+          st.nrb = R / 128; st.ncb = (n64 + 255) / 256; st.nks = n64 / 64;
+          st.kind = 0; st.cur = 0;
+          st.phase = 0; st.refine_left = g.refine_steps; st.steps = 0; st.rsteps = 0;
+          st.status = kSubNotConv; st.last = 0;
+          st.fcur = g.main_fmt; st.fnxt = g.main_fmt;
+        }
+        break;
+      }
+      tc::fence_proxy_async_global();
+      tc::mbar_arrive(&sh.epi_done[s]);
+    };
+
+    // a7 for the finished submatrix of slot s: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the
+    // FP64 partial traces
+    auto finish_slot = [&](int s) {
+      SlotState& st = sh.slot[s];
+      const int J = st.job, n = st.n, b = g.nbf[J];
+      const float* xf = g.xf + (size_t)(sub0 + s) * plane_elems;
       const double* Q = g.Q + g.c_off[J];
       const double* Sc = g.Sc + g.c_off[J];
       const double* Hc = g.Hc + g.c_off[J];
       double* Dc = g.Dc + g.c_off[J];
+      float* Qs = reinterpret_cast<float*>(stg);   // staging is idle between products
+      const bool staged = (size_t)n * b * sizeof(float) <= 4 * kStgBytes;
+      epi_bar();   // the final X (written by both groups) is visible
+      if (staged)
+        for (int e = etid; e < n * b; e += 256) Qs[e] = (float)Q[e];
+      epi_bar();
       double ps = 0.0, ph = 0.0;
-      if (!sh.err) {
-        // T_J(S)^-1 centre columns staged as FP32 in the (now idle) pipeline buffers when they fit
-        float* Qs = reinterpret_cast<float*>(stage_mem);
-        const bool staged = (size_t)n * b * sizeof(float) <= (size_t)kStages * kStageBytes;
-        if (staged)
-          for (int e = tid; e < n * b; e += kThreads) Qs[e] = (float)Q[e];
-        __syncthreads();
-        for (int e = tid; e < n * b; e += kThreads) {
-          const int i = e / b, c = e - i * b;
-          const float* xi = xf + (size_t)i * g.LD;
-          // FP32 partial sums of 16 products, combined with Kahan compensation
-          float sum = 0.0f, comp = 0.0f;
-          for (int k0 = 0; k0 < n; k0 += 16) {
-            float p = 0.0f;
-            const int k1 = min(n, k0 + 16);
-            if (staged) {
-              for (int k = k0; k < k1; ++k) p = fmaf(xi[k], Qs[k * b + c], p);
-            } else {
-              for (int k = k0; k < k1; ++k) p = fmaf(xi[k], (float)Q[(size_t)k * b + c], p);
-            }
-            const float y = p - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
+      for (int e = etid; e < n * b; e += 256) {
+        const int i = e / b, c = e - i * b;
+        const float* xi = xf + (size_t)i * g.LD;
+        // FP32 partial sums of 16 products, combined with Kahan compensation
+        float sum = 0.0f, comp = 0.0f;
+        for (int k0 = 0; k0 < n; k0 += 16) {
+          float p = 0.0f;
+          const int k1 = min(n, k0 + 16);
+          if (staged) {
+            for (int k = k0; k < k1; ++k) p = fmaf(xi[k], Qs[k * b + c], p);
+          } else {
+            for (int k = k0; k < k1; ++k) p = fmaf(xi[k], (float)Q[(size_t)k * b + c], p);
           }
-          const double d = 0.5 * (Q[e] - ((double)sum - (double)comp));
-          Dc[e] = d;
-          ps += d * Sc[e];
-          ph += d * Hc[e];
+          const float y = p - comp;
+          const float t = sum + y;
+          comp = (t - sum) - y;
+          sum = t;
         }
+        const double dv = 0.5 * (Q[e] - ((double)sum - (double)comp));
+        Dc[e] = dv;
+        ps += dv * Sc[e];
+        ph += dv * Hc[e];
       }
       for (int o = 16; o > 0; o >>= 1) {
         ps += __shfl_xor_sync(0xffffffffu, ps, o);
         ph += __shfl_xor_sync(0xffffffffu, ph, o);
       }
       if (lane == 0) {
-        sh.dred[0][warp] = ps;
-        sh.dred[1][warp] = ph;
+        sh.dred[0][warp - 4] = ps;
+        sh.dred[1][warp - 4] = ph;
       }
-      __syncthreads();
-      if (tid == 0) {
+      epi_bar();
+      if (tid == 128) {
         double ts = 0.0, th = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = 0; w < 8; ++w) {
           ts += sh.dred[0][w];
           th += sh.dred[1][w];
         }
-        int st = sh.err ? kSubTimeout : sh.status;
-        if (st == kSubOk && !(isfinite(ts) && isfinite(th))) st = kSubNonFinite;
+        int stt = st.status;
+        if (stt == kSubOk && !(isfinite(ts) && isfinite(th))) stt = kSubNonFinite;
         g.tS[J] = ts;
         g.tH[J] = th;
-        g.iters[J] = sh.steps;
-        g.rsteps[J] = sh.rsteps;
-        g.status[J] = st;
-        if (sh.err) atomicExch(g.err, 1);
+        g.iters[J] = st.steps;
+        g.rsteps[J] = st.rsteps;
+        g.status[J] = stt;
       }
-      __syncthreads();
+      epi_bar();   // staging and dred free again
+    };
+
+    start_slot(0);
+    start_slot(1);
+    for (uint32_t i = 0;; ++i) {
+      // every epilogue thread waits for the descriptor; a wait that ran out in any of them ends all
+      const bool got = tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * kWaitNs);
+      if (epi_bar_or(!got || sh.err)) {
+        if (tid == 128) sh.err = 1;
+        break;
+      }
+      const Desc d = sh.ring[i % kRing];
+      if (d.term) break;
+      SlotState& st = sh.slot[d.slot];
+      const int n = d.n, n64 = d.n64;
+      float part = 0.0f;
+      bool bad = false;   // a wait of this warp ran out: keep the barrier schedule, skip the work
+      float* xf = g.xf + (size_t)(sub0 + d.slot) * plane_elems;
+      for (int mb = 0; mb < d.nrb; ++mb)
+        for (int cb = 0; cb < d.ncb; ++cb) {
+          const int nt = min(256, n64 - 256 * cb);
+          const int buf = tcount & 1;
+          if (!bad) bad = !tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + kWaitNs);
+          bad = __any_sync(0xffffffffu, bad);   // tcgen05.ld needs the whole warp
+          tc::tc_fence_after();
+          const int row = 128 * mb + 32 * q + lane;
+          const bool live = 128 * mb + 32 * q < n64 && !bad;   // rows >= n64 are never read back
+          const int nch = nt / 32;
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
+          uint32_t r[32];
+          if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
+          for (int c0 = grp; c0 < nch; c0 += 2) {
+            const int col0 = 256 * cb + 32 * c0;
+            float v[32];
+            if (live) {
+              tc::tmem_wait_ld();
+              if (d.kind == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int col = col0 + j;
+                  const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
+                  if (row < n && col < n) part += e * e;
+                  v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
+              }
+              if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
+            }
+            if (d.last) {
+              if (live) {
+                float4* dst = reinterpret_cast<float4*>(xf + (size_t)row * g.LD + col0);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+              }
+            } else {
+              // stage the chunk in shared memory (64-byte swizzle: 16-byte unit c of row r sits at
+              // unit c ^ ((r >> 1) & 3)) and write it with TMA tensor stores
+              uint8_t* shi = stg + grp * 2 * kStgBytes;
+              uint8_t* slo = shi + kStgBytes;
+              if (tid == gbase) tc::bulk_wait_read<0>();   // the group's previous store has read the buffer
+              group_bar(grp);
+              if (live) {
+                uint32_t h[16], l[16];
+                split_pack(v, d.fo, h, l);
+                const int lr = 32 * q + lane;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int off = lr * 64 + ((c ^ ((lr >> 1) & 3)) << 4);
+                  *reinterpret_cast<uint4*>(shi + off) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                  if (d.fo.terms > 1)
+                    *reinterpret_cast<uint4*>(slo + off) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                }
+              }
+              tc::fence_proxy_async_smem();
+              group_bar(grp);
+              if (tid == gbase && !bad) {
+                tc::tma_store_3d(&mapS, shi, col0, 128 * mb, d.zo);
+                if (d.fo.terms > 1) tc::tma_store_3d(&mapS, slo, col0, 128 * mb, d.zo + 1);
+                tc::bulk_commit();
+              }
+            }
+          }
+          tc::tc_fence_before();
+          if (!bad) tc::mbar_arrive(&sh.acce[buf]);
+          ++tcount;
+        }
+      if (tid == gbase) tc::bulk_wait<0>();   // this product's stores are written before anyone reads them
+      tc::fence_proxy_async_global();
+      // ---- end of the product: one uniform error decision, then the slot's next state
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) sh.red[i & 1][warp - 4] = part;
+      if (epi_bar_or(bad)) {
+        if (tid == 128) sh.err = 1;
+        break;
+      }
+      if (tid == 128) {
+        if (d.kind == 0) {
+          // defect of X_step and the decision about the following steps
+          float dsum = 0.0f;
+          for (int w = 0; w < 8; ++w) dsum += sh.red[i & 1][w];
+          const float dd = sqrtf(dsum / (float)n);
+          const int steps = st.steps + 1;
+          if (st.phase == 1) st.rsteps += 1;   // this step ran in the refinement format
+          int last_ = 0, status = kSubNotConv;
+          Fmt nxt = st.fcur;
+          if (!isfinite(dd)) {
+            last_ = 1;
+            status = kSubNonFinite;
+          } else if (st.phase == 0) {
+            if (dd <= g.tol_ns) {
+              if (g.refine_steps == 0) {
+                last_ = 1;
+                status = dd <= g.tol_accept ? kSubOk : kSubNotConv;
+              } else {
+                st.phase = 1;
+                st.refine_left = g.refine_steps;
+                nxt = g.refine_fmt;
+              }
+            }
+          } else {
+            if (--st.refine_left == 0) {
+              last_ = 1;
+              status = dd <= g.tol_accept ? kSubOk : kSubNotConv;
+            }
+          }
+          if (!last_ && steps >= g.max_iter) {
+            last_ = 1;
+            status = kSubNotConv;
+          }
+          st.steps = steps;
+          st.last = last_;
+          st.status = status;
+          st.fnxt = nxt;
+          st.kind = 1;
+        } else if (!d.last) {
+          // after X T: swap the ping-pong X and adopt the next format
+          st.cur ^= 1;
+          st.fcur = st.fnxt;
+          st.kind = 0;
+        }
+      }
+      if (d.last) {
+        finish_slot(d.slot);
+        start_slot(d.slot);
+      } else {
+        tc::mbar_arrive(&sh.epi_done[d.slot]);
+      }
+    }
+    if (sh.err && tid == 128) {
+      // a wait ran out: the submatrices in flight are reported as timed out
+      for (int s = 0; s < kSlots; ++s) {
+        const int J = sh.slot[s].job;
+        if (J >= 0) {
+          g.status[J] = kSubTimeout;
+          g.iters[J] = sh.slot[s].steps;
+          g.rsteps[J] = sh.slot[s].rsteps;
+          g.tS[J] = 0.0;
+          g.tH[J] = 0.0;
+        }
+      }
+      atomicExch(g.err, 1);
     }
   }
 
-  // teardown after a timeout: wait (bounded) for this CTA's TMA copies and MMAs still in flight
+  // every role has left its loop, so sh.err is final; after a timeout wait (bounded) for this CTA's
+  // TMA loads and MMAs still in flight before the shared and tensor memory are released
+  __syncthreads();
   if (sh.err) {
     if (warp == 0 && lane == 0)
       for (int s = 0; s < kStages; ++s)
@@ -566,7 +667,9 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   int32_t maxn = 0;
   for (int64_t J = j0; J < j1; ++J) maxn = std::max(maxn, plan->h_sub_n[J]);
   const int LD = (maxn + 63) & ~63, R = (maxn + 127) & ~127;
-  const int slots = (int)std::min<int64_t>(sms, j1 - j0);
+  // one CTA per SM at most, each with kSlots submatrices in flight (one scratch sub-slot each)
+  const int ctas = (int)std::min<int64_t>(sms, (j1 - j0 + kSlots - 1) / kSlots);
+  const int slots = ctas * kSlots;
   if (!S->planes.p || S->R < R || S->LD < LD || S->slots < slots) {
     const int nR = std::max(R, S->R), nLD = std::max(LD, S->LD), nS = std::max(slots, S->slots);
     dev_free(plan, S->planes);
@@ -591,9 +694,11 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     S->ord_j0 = j0;
     S->ord_j1 = j1;
   }
-  CUtensorMap mA, mB;
+  CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
-      !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64)) {
+      !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64) ||
+      !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 128,
+                     CU_TENSOR_MAP_SWIZZLE_64B)) {
     set_error("cuTensorMapEncodeTiled rejected the scratch layout (R %d, LD %d, slots %d)", S->R, S->LD, S->slots);
     return NOLSM_ERR_CUDA;
   }
@@ -620,7 +725,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<<<slots, kThreads, kSmemBytes, st>>>(mA, mB, g);
+  k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;
   return NOLSM_OK;
@@ -637,7 +742,7 @@ namespace {
 
 constexpr int kNaMaxN = 192;                  // largest submatrix dimension accepted
 constexpr int kNaR = 256, kNaLD = 192;        // scratch plane shape: rows rounded to 128, columns to 64
-constexpr int kNaSlots = 8;                   // CTAs (one scratch slot each)
+constexpr int kNaSlots = 8;                   // scratch sub-slots: 4 CTAs with kSlots each
 constexpr int kNaMaxSub = 4096;               // submatrices per call
 constexpr size_t kNaPlaneElems = (size_t)kNaR * kNaLD;
 constexpr size_t kNaPlanesBytes = sizeof(uint16_t) * kPlanes * kNaSlots * kNaPlaneElems;
@@ -720,9 +825,10 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   unsigned char* base = static_cast<unsigned char*>(g_na_addr[dev]);
   int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes + kNaXfBytes);
 
-  CUtensorMap mA, mB;
+  CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
-      !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64)) {
+      !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64) ||
+      !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 128, CU_TENSOR_MAP_SWIZZLE_64B)) {
     set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
     return NOLSM_ERR_CUDA;
   }
@@ -746,7 +852,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
   g.rsteps = ints + 2 * kNaMaxSub;
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<<<std::min(kNaSlots, count), kThreads, kSmemBytes, st>>>(mA, mB, g);
+  k_ns_tc<<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, g);
   NOLSM_LAUNCH_CHECK();
   return NOLSM_OK;
 }
