@@ -403,11 +403,26 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     pa.Q = plan->Q.as<double>(); pa.lam = plan->lam.as<double>(); pa.prep_status = plan->prep_status.as<int32_t>();
     int chunk_max_n = 1;
     for (int64_t k = J; k < e; ++k) chunk_max_n = std::max(chunk_max_n, plan->h_sub_n[k]);
-    NOLSM_TRY(launch_prepare(pa, (int)(e - J), chunk_max_n, keep_fp64_A, P.A.p, st));
-    plan->stats.launches += 2;
+    if (keep_fp64_A) {
+      NOLSM_TRY(launch_prepare(pa, (int)(e - J), chunk_max_n, true, P.A.p, st));
+      plan->stats.launches += 2;
+    } else {
+      // FP32 factor, A in FP32, Q refined to FP64 accuracy; the FP64 factorisation only where flagged
+      const int64_t nbc = plan->h_c_off[e] - plan->h_c_off[J];
+      NOLSM_TRY(ensure(plan, plan->ws_l32, sizeof(float) * (size_t)n2));
+      NOLSM_TRY(ensure(plan, plan->ws_refine, (sizeof(double) + sizeof(float)) * (size_t)std::max<int64_t>(nbc, 1)));
+      pa.L32 = plan->ws_l32.as<float>();
+      pa.c_base = plan->h_c_off[J];
+      pa.R64 = plan->ws_refine.as<double>();
+      pa.W32 = reinterpret_cast<float*>(pa.R64 + std::max<int64_t>(nbc, 1));
+      pa.fallback_max_n = prepare_fp64_max_n();
+      NOLSM_TRY(launch_prepare_mixed(pa, (int)(e - J), chunk_max_n, P.A.as<float>(), st));
+      plan->stats.launches += 3;
+    }
     for (int64_t k = J; k < e; ++k) {
       const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
-      plan->stats.flops_fp64 += m * m * m / 3.0 + 2.0 * m * m * b + (keep_fp64_A ? 2.0 * m * m * m : 0.0);
+      // FP64 flops: the factorisation and Q solves (FP64 path) or one FP64 residual of Q (mixed)
+      plan->stats.flops_fp64 += keep_fp64_A ? m * m * m / 3.0 + 2.0 * m * m * b + 2.0 * m * m * m : 2.0 * m * m * b;
       P.done[k] = 1;
     }
     J = e;

@@ -14,9 +14,21 @@ struct PrepArgs {
   double* Q;                  // centre columns of T_J(S)^-1, n x b row-major at c_off
   double* lam;                // Gershgorin interval of A_J
   int32_t* prep_status;
+  int32_t only_flagged = 0;   // k_prepare: take only submatrices the mixed preparation flagged
+  // mixed preparation (low-precision paths)
+  float* L32 = nullptr;       // FP32 factors, same offsets as ws (a_off - a_base)
+  int64_t c_base = 0;         // c_off of the chunk's first submatrix
+  double* R64 = nullptr;      // FP64 residuals of Q, n x b at c_off - c_base
+  float* W32 = nullptr;       // FP32 corrections of Q, n x b at c_off - c_base
+  int32_t fallback_max_n = 0; // largest n the FP64 preparation takes (shared-memory panel)
 };
 
 // a2-a3 for `count` submatrices starting at g.j0 (largest dimension max_n); A in FP64 (fp64_A) or FP32.
 nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A, void* Acache, cudaStream_t st);
+// The same with the FP32 factor and iterative refinement of Q (A in FP32), followed by the FP64
+// preparation of the submatrices it flagged.
+nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float* Acache, cudaStream_t st);
+// Largest submatrix dimension the FP64 preparation takes.
+int prepare_fp64_max_n();
 
 }  // namespace nolsm

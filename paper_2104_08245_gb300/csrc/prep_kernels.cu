@@ -1,15 +1,24 @@
-// a2-a3: the overlap factorisation T_J(S) = L L^T in FP64 and the solves that give
+// a2-a3: the overlap factorisation T_J(S) = L L^T and the solves that give
 //   A_J = T_J(S)^-1 T_J(H0) = L^-T (L^-1 T_J(H0))            (Eq. purification_submatrix)
-//   Q_J = T_J(S)^-1 [:, centre columns] = L^-T (L^-1 E_c)     (FP64 always)
-// and the Gershgorin interval of A_J. One CTA (128 threads) per submatrix, two CTAs per SM.
+//   Q_J = T_J(S)^-1 [:, centre columns] = L^-T (L^-1 E_c)     (to FP64 accuracy always)
+// and the Gershgorin interval of A_J. One CTA (128 threads) per submatrix.
 //
-// FP64 runs at 2 lanes per clock per SM on this GPU (one full-warp FP64 instruction per 64 cycles per
-// scheduler), so every FP64 instruction here is issued by full warps spread over all schedulers and no
-// FP64 work is a dependent chain: the Cholesky factors a 32-column panel held in shared memory one
-// column at a time in parallel over its rows, and builds the inverse X_r of the panel's diagonal block
-// in the same sweep (column-oriented forward substitution on the identity). The triangular solves then
-// apply X_r as a product instead of substituting row by row. X_r is kept, transposed, in the unused
-// upper triangle of its diagonal block (its diagonal is 1/L_ii).
+// Two preparations share the blocked algorithms below (templated on the factor's type):
+//  - k_prepare (FP64 path, and fallback): L in FP64, factored in place; Q by FP64 solves.
+//    FP64 runs at 2 lanes per clock per SM on this GPU (one full-warp FP64 instruction per 64 cycles per
+//    scheduler), so every FP64 instruction here is issued by full warps spread over all schedulers and no
+//    FP64 work is a dependent chain.
+//  - k_prepare_mixed (low-precision paths): L in FP32 (the FP32 pipe is ~60x the FP64 one), A by FP32
+//    solves as before, and Q by mixed-precision iterative refinement: q <- q + L^-T L^-1 (E_c - T_J(S) q)
+//    with the residual in FP64 and the correction solves in FP32, until the correction is below 1e-6 of
+//    q (the error then contracts by the same factor per step, so the result is FP64-accurate). A
+//    submatrix whose FP32 factor fails or whose refinement does not contract is flagged and prepared
+//    again by k_prepare (FP64 factor).
+// The Cholesky factors a 32-column panel held in shared memory one column at a time in parallel over its
+// rows, and builds the inverse X_r of the panel's diagonal block in the same sweep (column-oriented
+// forward substitution on the identity). The triangular solves then apply X_r as a product instead of
+// substituting row by row. X_r is kept, transposed, in the unused upper triangle of its diagonal block
+// (its diagonal is 1/L_ii).
 #include <algorithm>
 #include <cmath>
 
@@ -21,59 +30,84 @@ namespace nolsm {
 namespace {
 
 constexpr int NB = 32;
-constexpr int kThreads = 128;   // two CTAs (two submatrices) per SM overlap each other's serial phases
+constexpr int kThreads = 128;   // several CTAs (submatrices) per SM overlap each other's serial phases
 constexpr int kMaxB = 64;
+constexpr int kRefineMax = 4;   // refinement steps of Q before a submatrix falls back to the FP64 factor
+constexpr double kRefineTol = 1e-6;
+
+// Row stride of panels and tiles in shared memory: FP64 rows padded by one element (bank spread),
+// FP32 rows by four so that every row starts on a 16-byte boundary (vector loads).
+template <typename T> struct Ld { static constexpr int v = NB + 1; };
+template <> struct Ld<float> { static constexpr int v = NB + 4; };
 
 // X_r[a][t] for a, t < kb: lower-triangular inverse of the diagonal block starting at r0.
-__device__ __forceinline__ double xinv(const double* S, int n, int r0, int a, int t) {
-  if (t > a) return 0.0;
-  if (t == a) return 1.0 / S[(size_t)(r0 + a) * n + r0 + a];
+template <typename T>
+__device__ __forceinline__ T xinv(const T* S, int n, int r0, int a, int t) {
+  if (t > a) return T(0);
+  if (t == a) return T(1) / S[(size_t)(r0 + a) * n + r0 + a];
   return S[(size_t)(r0 + t) * n + r0 + a];  // stored transposed in the upper triangle
 }
 
 // ------------------------------------------------------------------------------------ Cholesky
 // In place: the lower triangle of S receives L; the strict upper triangle of every diagonal block
 // receives X_r^T. Returns false (uniformly) if a pivot is not positive or not finite.
-__device__ bool cholesky(double* __restrict__ S, int n, double* __restrict__ Ps, double (*Xs)[NB + 1],
-                         double* s_rinv /* [2] */, int* s_bad) {
+template <typename T>
+__device__ bool cholesky(T* __restrict__ S, int n, T* __restrict__ Ps, T (*Xs)[NB + 1], T* s_rinv /* [2] */,
+                         int* s_bad) {
   const int tid = threadIdx.x;
-  constexpr int LDP = NB + 1;
+  constexpr int LDP = Ld<T>::v;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0), mt = n - k0;
-    for (int e = tid; e < mt * kb; e += kThreads) {
-      const int i = e / kb, t = e - i * kb;
-      Ps[i * LDP + t] = S[(size_t)(k0 + i) * n + k0 + t];
+    if constexpr (sizeof(T) == 8) {
+      for (int e = tid; e < mt * kb; e += kThreads) {
+        const int i = e / kb, t = e - i * kb;
+        Ps[i * LDP + t] = S[(size_t)(k0 + i) * n + k0 + t];
+      }
+    } else {
+      // full 32-column rows, zero beyond kb (the trailing update reads whole 4-column groups)
+      for (int e = tid; e < mt * NB; e += kThreads) {
+        const int i = e / NB, t = e - i * NB;
+        Ps[i * LDP + t] = t < kb ? S[(size_t)(k0 + i) * n + k0 + t] : T(0);
+      }
     }
-    for (int e = tid; e < NB * NB; e += kThreads) Xs[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? 1.0 : 0.0;
+    for (int e = tid; e < NB * NB; e += kThreads) Xs[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? T(1) : T(0);
     __syncthreads();
     // Column j: phase A scales column j-1 and row j-1 of X by r_{j-1} while thread 0 forms the pivot of
-    // column j (FP32 rsqrt seed, two FP64 Newton steps); phase B updates the panel and X with the
-    // unscaled column j times r_j^2.
+    // column j (FP32 rsqrt seed, Newton steps in the factor's precision); phase B updates the panel and X
+    // with the unscaled column j times r_j^2.
     for (int j = 0; j <= kb; ++j) {
       if (j > 0) {
-        const double rp = *s_rinv;
+        const T rp = *s_rinv;
         for (int i = j + tid; i < mt; i += kThreads) Ps[i * LDP + j - 1] *= rp;
         if (tid < kb) Xs[j - 1][tid] *= rp;
       }
       if (tid == 0 && j < kb) {
-        const double d = Ps[j * LDP + j];
-        if (!(d > 0.0) || !isfinite(d)) *s_bad = 1;
-        const double dd = fmax(d, 1e-300);
-        double r = (double)rsqrtf((float)dd);
-        r = r * fma(-0.5 * dd * r, r, 1.5);
-        r = r * fma(-0.5 * dd * r, r, 1.5);
-        Ps[j * LDP + j] = dd * r;
-        s_rinv[1] = r;
+        const T d = Ps[j * LDP + j];
+        if (!(d > T(0)) || !isfinite(d)) *s_bad = 1;
+        if constexpr (sizeof(T) == 8) {
+          const double dd = fmax(d, 1e-300);
+          double r = (double)rsqrtf((float)dd);
+          r = r * fma(-0.5 * dd * r, r, 1.5);
+          r = r * fma(-0.5 * dd * r, r, 1.5);
+          Ps[j * LDP + j] = dd * r;
+          s_rinv[1] = r;
+        } else {
+          const float dd = fmaxf(d, 1e-30f);
+          float r = rsqrtf(dd);
+          r = r * fmaf(-0.5f * dd * r, r, 1.5f);
+          Ps[j * LDP + j] = dd * r;
+          s_rinv[1] = r;
+        }
       }
       __syncthreads();
       if (j == kb) break;
-      const double r = s_rinv[1], r2 = r * r;
+      const T r = s_rinv[1], r2 = r * r;
       if (tid == 0) s_rinv[0] = r;   // read by phase A of the next column (after the barrier below)
       const int w = kb - j - 1;
       if (w > 0) {
-        // one thread per panel row: a single scaling, then plain DFMAs along the row
+        // one thread per panel row: a single scaling, then plain FMAs along the row
         for (int i = j + 1 + tid; i < mt; i += kThreads) {
-          const double a = r2 * Ps[i * LDP + j];
+          const T a = r2 * Ps[i * LDP + j];
           const int kend = i < kb ? i + 1 : kb;
           for (int k = j + 1; k < kend; ++k) Ps[i * LDP + k] = fma(-a, Ps[k * LDP + j], Ps[i * LDP + k]);
         }
@@ -95,33 +129,55 @@ __device__ bool cholesky(double* __restrict__ S, int n, double* __restrict__ Ps,
     // trailing update of the lower triangle, 32 x 32 tiles, 4 x 2 outputs per thread
     const int r0 = kb, m = mt - kb;   // panel-local first trailing row, trailing size
     if (m > 0) {
-      const int T = (m + 31) / 32;
+      const int TT = (m + 31) / 32;
       const int tx = tid & 15, ty = tid >> 4;   // 16 x 8 threads, rows ty + 8a (a < 4), cols tx + 16b (b < 2)
-      for (int tile = 0; tile < T * (T + 1) / 2; ++tile) {
+      for (int tile = 0; tile < TT * (TT + 1) / 2; ++tile) {
         int ti = 0;
         while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
         const int tj = tile - ti * (ti + 1) / 2;
         const int bi = r0 + 32 * ti, bj = r0 + 32 * tj;
-        double acc[4][2];
+        T acc[4][2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0;
+        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
         int ii[4], jj[2];
         bool vi[4], vj[2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) { ii[a] = bi + ty + 8 * a; vi[a] = ii[a] < mt; }
 #pragma unroll
         for (int b = 0; b < 2; ++b) { jj[b] = bj + tx + 16 * b; vj[b] = jj[b] < mt; }
+        if constexpr (sizeof(T) == 8) {
 #pragma unroll 4
-        for (int t = 0; t < kb; ++t) {
-          double av[4], bv[2];
+          for (int t = 0; t < kb; ++t) {
+            double av[4], bv[2];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = vi[a] ? Ps[ii[a] * LDP + t] : 0.0;
+            for (int a = 0; a < 4; ++a) av[a] = vi[a] ? Ps[ii[a] * LDP + t] : 0.0;
 #pragma unroll
-          for (int b = 0; b < 2; ++b) bv[b] = vj[b] ? Ps[jj[b] * LDP + t] : 0.0;
+            for (int b = 0; b < 2; ++b) bv[b] = vj[b] ? Ps[jj[b] * LDP + t] : 0.0;
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+              for (int b = 0; b < 2; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+          }
+        } else {
+          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int t = 0; t < kb; t += 4) {
+            float4 av[4], bv[2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = vi[a] ? *reinterpret_cast<const float4*>(&Ps[ii[a] * LDP + t]) : z4;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) bv[b] = vj[b] ? *reinterpret_cast<const float4*>(&Ps[jj[b] * LDP + t]) : z4;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int b = 0; b < 2; ++b) {
+                float s = acc[a][b];
+                s = fmaf(av[a].x, bv[b].x, s);
+                s = fmaf(av[a].y, bv[b].y, s);
+                s = fmaf(av[a].z, bv[b].z, s);
+                s = fmaf(av[a].w, bv[b].w, s);
+                acc[a][b] = s;
+              }
+          }
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -136,11 +192,31 @@ __device__ bool cholesky(double* __restrict__ S, int n, double* __restrict__ Ps,
 }
 
 // ------------------------------------------------------------------------------------ A = L^-T L^-1 H
-// One right-hand-side column per thread (columns in batches of kThreads), blocked by 32 rows; L tiles are
-// staged in shared memory in T, the diagonal blocks are applied through X_r.
+// s - sum_t row[t] y[t] over one 32-wide block (row in shared memory; FP32 rows are 16-byte aligned)
 template <typename T>
-__device__ void solve_A(const double* __restrict__ S, const double* __restrict__ H, int n, T* __restrict__ X,
-                        T (*Lp)[NB + 1], T (*Xf)[NB + 1]) {
+__device__ __forceinline__ T row_dot_sub(const T* row, const T (&y)[NB], T s) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int t = 0; t < NB; t += 4) {
+      const float4 l = *reinterpret_cast<const float4*>(row + t);
+      s -= l.x * y[t];
+      s -= l.y * y[t + 1];
+      s -= l.z * y[t + 2];
+      s -= l.w * y[t + 3];
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) s -= row[t] * y[t];
+  }
+  return s;
+}
+
+// One right-hand-side column per thread (columns in batches of kThreads), blocked by 32 rows; L tiles are
+// staged in shared memory in T, the diagonal blocks are applied through X_r. LT is the factor's type.
+template <typename T, typename LT>
+__device__ void solve_A(const LT* __restrict__ S, const double* __restrict__ H, int n, T* __restrict__ X,
+                        T* __restrict__ Lp, T* __restrict__ Xf) {
+  constexpr int LDA = Ld<T>::v;
   const int tid = threadIdx.x;
   const int nblk = (n + NB - 1) / NB;
   for (int cb = 0; cb < n; cb += kThreads) {
@@ -155,7 +231,7 @@ __device__ void solve_A(const double* __restrict__ S, const double* __restrict__
       for (int q0 = 0; q0 < r0; q0 += NB) {
         for (int e = tid; e < NB * NB; e += kThreads) {
           const int i = e >> 5, t = e & 31;
-          Lp[i][t] = i < rb ? (T)S[(size_t)(r0 + i) * n + q0 + t] : T(0);
+          Lp[i * LDA + t] = i < rb ? (T)S[(size_t)(r0 + i) * n + q0 + t] : T(0);
         }
         __syncthreads();
         if (act) {
@@ -163,28 +239,44 @@ __device__ void solve_A(const double* __restrict__ S, const double* __restrict__
 #pragma unroll
           for (int t = 0; t < NB; ++t) y[t] = X[(size_t)(q0 + t) * n + c];
 #pragma unroll
-          for (int i = 0; i < NB; ++i) {
-            T s = acc[i];
-#pragma unroll
-            for (int t = 0; t < NB; ++t) s -= Lp[i][t] * y[t];
-            acc[i] = s;
-          }
+          for (int i = 0; i < NB; ++i) acc[i] = row_dot_sub(Lp + i * LDA, y, acc[i]);
         }
         __syncthreads();
       }
+      // X_r for y = X_r acc (lower triangular)
       for (int e = tid; e < NB * NB; e += kThreads) {
         const int a = e >> 5, t = e & 31;
-        Xf[a][t] = (a < rb && t < rb) ? (T)xinv(S, n, r0, a, t) : T(0);
+        Xf[a * LDA + t] = (a < rb && t < rb) ? (T)xinv(S, n, r0, a, t) : T(0);
       }
       __syncthreads();
       if (act) {
+        if constexpr (sizeof(T) == 4) {
+          T o[NB];
 #pragma unroll
-        for (int a = NB - 1; a >= 0; --a) {   // y = X_r acc (lower triangular: row a uses acc[0..a])
-          T s = T(0);
+          for (int a = 0; a < NB; ++a) {   // row a of X_r is zero beyond a: whole 4-groups up to a
+            float s = 0.0f;
 #pragma unroll
-          for (int t = 0; t <= a; ++t) s += Xf[a][t] * acc[t];
-          if (a < rb) X[(size_t)(r0 + a) * n + c] = s;
-          acc[a] = s;
+            for (int t = 0; t <= (a | 3); t += 4) {
+              const float4 x4 = *reinterpret_cast<const float4*>(Xf + a * LDA + t);
+              s = fmaf(x4.x, acc[t], s);
+              s = fmaf(x4.y, acc[t + 1], s);
+              s = fmaf(x4.z, acc[t + 2], s);
+              s = fmaf(x4.w, acc[t + 3], s);
+            }
+            o[a] = s;
+          }
+#pragma unroll
+          for (int a = 0; a < NB; ++a)
+            if (a < rb) X[(size_t)(r0 + a) * n + c] = o[a];
+        } else {
+#pragma unroll
+          for (int a = NB - 1; a >= 0; --a) {   // y = X_r acc (lower triangular: row a uses acc[0..a])
+            T s = T(0);
+#pragma unroll
+            for (int t = 0; t <= a; ++t) s += Xf[a * LDA + t] * acc[t];
+            if (a < rb) X[(size_t)(r0 + a) * n + c] = s;
+            acc[a] = s;
+          }
         }
       }
       __syncthreads();
@@ -199,7 +291,7 @@ __device__ void solve_A(const double* __restrict__ S, const double* __restrict__
         const int qb = min(NB, n - q0);
         for (int e = tid; e < NB * NB; e += kThreads) {
           const int t = e >> 5, i = e & 31;  // Lp[i][t] = L[q0+t][r0+i]
-          Lp[i][t] = (t < qb && i < rb) ? (T)S[(size_t)(q0 + t) * n + r0 + i] : T(0);
+          Lp[i * LDA + t] = (t < qb && i < rb) ? (T)S[(size_t)(q0 + t) * n + r0 + i] : T(0);
         }
         __syncthreads();
         if (act) {
@@ -207,28 +299,51 @@ __device__ void solve_A(const double* __restrict__ S, const double* __restrict__
 #pragma unroll
           for (int t = 0; t < NB; ++t) x[t] = t < qb ? X[(size_t)(q0 + t) * n + c] : T(0);
 #pragma unroll
-          for (int i = 0; i < NB; ++i) {
-            T s = acc[i];
-#pragma unroll
-            for (int t = 0; t < NB; ++t) s -= Lp[i][t] * x[t];
-            acc[i] = s;
-          }
+          for (int i = 0; i < NB; ++i) acc[i] = row_dot_sub(Lp + i * LDA, x, acc[i]);
         }
         __syncthreads();
       }
-      for (int e = tid; e < NB * NB; e += kThreads) {
-        const int a = e >> 5, t = e & 31;
-        Xf[a][t] = (a < rb && t < rb) ? (T)xinv(S, n, r0, a, t) : T(0);
+      if constexpr (sizeof(T) == 4) {
+        // X_r^T staged by rows: Xf[a][t] = X_r[t][a], zero for t < a
+        for (int e = tid; e < NB * NB; e += kThreads) {
+          const int a = e >> 5, t = e & 31;
+          Xf[a * LDA + t] = (a < rb && t < rb) ? (T)xinv(S, n, r0, t, a) : T(0);
+        }
+      } else {
+        for (int e = tid; e < NB * NB; e += kThreads) {
+          const int a = e >> 5, t = e & 31;
+          Xf[a * LDA + t] = (a < rb && t < rb) ? (T)xinv(S, n, r0, a, t) : T(0);
+        }
       }
       __syncthreads();
       if (act) {
+        if constexpr (sizeof(T) == 4) {
+          T o[NB];
 #pragma unroll
-        for (int a = 0; a < NB; ++a) {   // x = X_r^T acc (upper triangular: row a uses acc[a..])
-          T s = T(0);
+          for (int a = 0; a < NB; ++a) {   // x = X_r^T acc (row a of X_r^T is zero before a)
+            float s = 0.0f;
 #pragma unroll
-          for (int t = a; t < NB; ++t) s += Xf[t][a] * acc[t];
-          if (a < rb) X[(size_t)(r0 + a) * n + c] = s;
-          acc[a] = s;
+            for (int t = a & ~3; t < NB; t += 4) {
+              const float4 x4 = *reinterpret_cast<const float4*>(Xf + a * LDA + t);
+              s = fmaf(x4.x, acc[t], s);
+              s = fmaf(x4.y, acc[t + 1], s);
+              s = fmaf(x4.z, acc[t + 2], s);
+              s = fmaf(x4.w, acc[t + 3], s);
+            }
+            o[a] = s;
+          }
+#pragma unroll
+          for (int a = 0; a < NB; ++a)
+            if (a < rb) X[(size_t)(r0 + a) * n + c] = o[a];
+        } else {
+#pragma unroll
+          for (int a = 0; a < NB; ++a) {   // x = X_r^T acc (upper triangular: row a uses acc[a..])
+            T s = T(0);
+#pragma unroll
+            for (int t = a; t < NB; ++t) s += Xf[t * LDA + a] * acc[t];
+            if (a < rb) X[(size_t)(r0 + a) * n + c] = s;
+            acc[a] = s;
+          }
         }
       }
       __syncthreads();
@@ -287,35 +402,91 @@ __device__ void solve_Q(const double* __restrict__ S, int n, int c0, int b, doub
   }
 }
 
+// ------------------------------------------------------------------------------------ mixed-precision Q
+// W <- L^-T L^-1 W for the b columns of W (n x b row-major, FP32), with the FP32 factor.
+__device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
+                             float (*Acc)[kMaxB + 1], float (*Xd)[NB + 1]) {
+  const int tid = threadIdx.x;
+  const int nblk = (n + NB - 1) / NB;
+  for (int rbk = 0; rbk < nblk; ++rbk) {   // forward
+    const int r0 = rbk * NB, rb = min(NB, n - r0);
+    for (int e = tid; e < rb * b; e += kThreads) {
+      const int i = e / b, c = e - i * b;
+      float s = W[(size_t)(r0 + i) * b + c];
+      const float* Li = L + (size_t)(r0 + i) * n;
+      for (int q = 0; q < r0; ++q) s = fmaf(-Li[q], W[(size_t)q * b + c], s);
+      Acc[i][c] = s;
+    }
+    for (int e = tid; e < NB * NB; e += kThreads) {
+      const int a = e >> 5, t = e & 31;
+      Xd[a][t] = (a < rb && t < rb) ? xinv(L, n, r0, a, t) : 0.0f;
+    }
+    __syncthreads();
+    for (int e = tid; e < rb * b; e += kThreads) {
+      const int a = e / b, c = e - a * b;
+      float s = 0.0f;
+      for (int t = 0; t <= a; ++t) s = fmaf(Xd[a][t], Acc[t][c], s);
+      W[(size_t)(r0 + a) * b + c] = s;
+    }
+    __syncthreads();
+  }
+  for (int rbk = nblk - 1; rbk >= 0; --rbk) {   // backward
+    const int r0 = rbk * NB, rb = min(NB, n - r0);
+    for (int e = tid; e < rb * b; e += kThreads) {
+      const int i = e / b, c = e - i * b;
+      float s = W[(size_t)(r0 + i) * b + c];
+      for (int q = r0 + rb; q < n; ++q) s = fmaf(-L[(size_t)q * n + r0 + i], W[(size_t)q * b + c], s);
+      Acc[i][c] = s;
+    }
+    for (int e = tid; e < NB * NB; e += kThreads) {
+      const int a = e >> 5, t = e & 31;
+      Xd[a][t] = (a < rb && t < rb) ? xinv(L, n, r0, a, t) : 0.0f;
+    }
+    __syncthreads();
+    for (int e = tid; e < rb * b; e += kThreads) {
+      const int a = e / b, c = e - a * b;
+      float s = 0.0f;
+      for (int t = a; t < rb; ++t) s = fmaf(Xd[t][a], Acc[t][c], s);
+      W[(size_t)(r0 + a) * b + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// R = E_c - S q in FP64 (S the full symmetric T_J(S)); one warp per row, lanes along the row, up to 8
+// columns of q per sweep.
+__device__ void residual64(const double* __restrict__ S, int n, int c0, int b, const double* __restrict__ q,
+                           double* __restrict__ R) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < n; i += kThreads / 32) {
+    const double* Si = S + (size_t)i * n;
+    for (int cg = 0; cg < b; cg += 8) {
+      const int cn = min(8, b - cg);
+      double acc[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+      for (int k = lane; k < n; k += 32) {
+        const double s = Si[k];
+        const double* qk = q + (size_t)k * b + cg;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < cn) acc[c] = fma(s, qk[c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c < cn) {
+          double v = acc[c];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) R[(size_t)i * b + cg + c] = (i == c0 + cg + c ? 1.0 : 0.0) - v;
+        }
+      }
+    }
+  }
+}
+
+// Gershgorin interval of A (n x n, FP32 or FP64) widened by its rounding, into lam[2J], lam[2J+1].
 template <typename TA>
-__global__ void __launch_bounds__(kThreads, 2) k_prepare(PrepArgs g, TA* __restrict__ Acache) {
-  extern __shared__ double Ps[];   // factorisation panel: n x (NB+1) doubles
-  __shared__ double Xs[NB][NB + 1];
-  __shared__ __align__(16) unsigned char raw[sizeof(double) * NB * (kMaxB + 1)];
-  __shared__ double s_rinv[2];
-  __shared__ int s_bad;
-  __shared__ float rlo[kThreads], rhi[kThreads];
-  const int J = g.j0 + blockIdx.x;
-  const int n = g.sub_n[J];
-  const int bJ = g.nbf[J];
-  const int c0 = g.sub_c0[J];
-  double* S = g.ws + (g.a_off[J] - g.a_base);
-  const double* H = S + g.chunk_n2;
-  if (threadIdx.x == 0) s_bad = 0;
-  __syncthreads();
-  const bool ok = cholesky(S, n, Ps, Xs, s_rinv, &s_bad);
-  if (threadIdx.x == 0) g.prep_status[J] = ok ? kSubOk : kSubNotSpd;
-  if (!ok) return;   // uniform: every thread read the flag after the same barrier
-  // A_J in TA (shared memory reused: two T tiles)
-  TA* A = Acache + g.a_off[J];
-  TA (*Lp)[NB + 1] = reinterpret_cast<TA (*)[NB + 1]>(Ps);
-  TA (*Xf)[NB + 1] = reinterpret_cast<TA (*)[NB + 1]>(Ps + NB * (NB + 1));
-  solve_A<TA>(S, H, n, A, Lp, Xf);
-  __syncthreads();
-  // Q_J in FP64
-  solve_Q(S, n, c0, bJ, g.Q + g.c_off[J], reinterpret_cast<double (*)[kMaxB + 1]>(raw), Xs);
-  __syncthreads();
-  // Gershgorin interval of A_J (in the arithmetic of A, widened by its rounding)
+__device__ void gershgorin(const TA* __restrict__ A, int n, double* lam, float* rlo, float* rhi) {
   float lo = INFINITY, hi = -INFINITY;
   for (int i = threadIdx.x; i < n; i += kThreads) {
     float r = 0.0f;
@@ -337,19 +508,146 @@ __global__ void __launch_bounds__(kThreads, 2) k_prepare(PrepArgs g, TA* __restr
   }
   if (threadIdx.x == 0) {
     const double w = 1e-5 * fmax(fabs((double)rlo[0]), fabs((double)rhi[0]));
-    g.lam[2 * J] = (double)rlo[0] - w;
-    g.lam[2 * J + 1] = (double)rhi[0] + w;
+    lam[0] = (double)rlo[0] - w;
+    lam[1] = (double)rhi[0] + w;
   }
 }
 
+constexpr int kSubRefine = 64;   // internal prep status: prepare again with the FP64 factor
+
+// ------------------------------------------------------------------------------------ kernels
+template <typename TA>
+__global__ void __launch_bounds__(kThreads, 2) k_prepare(PrepArgs g, TA* __restrict__ Acache) {
+  extern __shared__ __align__(16) double Ps[];   // factorisation panel: n x (NB+1) doubles
+  __shared__ double Xs[NB][NB + 1];
+  __shared__ __align__(16) unsigned char raw[sizeof(double) * NB * (kMaxB + 1)];
+  __shared__ double s_rinv[2];
+  __shared__ int s_bad;
+  __shared__ float rlo[kThreads], rhi[kThreads];
+  const int J = g.j0 + blockIdx.x;
+  if (g.only_flagged && g.prep_status[J] != kSubRefine) return;
+  const int n = g.sub_n[J];
+  const int bJ = g.nbf[J];
+  const int c0 = g.sub_c0[J];
+  double* S = g.ws + (g.a_off[J] - g.a_base);
+  const double* H = S + g.chunk_n2;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const bool ok = cholesky<double>(S, n, Ps, Xs, s_rinv, &s_bad);
+  if (threadIdx.x == 0) g.prep_status[J] = ok ? kSubOk : kSubNotSpd;
+  if (!ok) return;   // uniform: every thread read the flag after the same barrier
+  // A_J in TA (shared memory reused: two T tiles)
+  TA* A = Acache + g.a_off[J];
+  TA* Lp = reinterpret_cast<TA*>(Ps);
+  solve_A<TA, double>(S, H, n, A, Lp, Lp + NB * Ld<TA>::v);
+  __syncthreads();
+  // Q_J in FP64
+  solve_Q(S, n, c0, bJ, g.Q + g.c_off[J], reinterpret_cast<double (*)[kMaxB + 1]>(raw), Xs);
+  __syncthreads();
+  gershgorin(A, n, g.lam + 2 * J, rlo, rhi);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float* __restrict__ Acache) {
+  extern __shared__ __align__(16) float Pf[];   // factorisation panel: n x (NB+4) floats
+  __shared__ float Xs[NB][NB + 1];
+  __shared__ float Acc[NB][kMaxB + 1];
+  __shared__ float s_rinv[2];
+  __shared__ int s_bad;
+  __shared__ float rlo[kThreads], rhi[kThreads];
+  __shared__ float red_d[kThreads / 32];
+  __shared__ double red_q[kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int J = g.j0 + blockIdx.x;
+  const int n = g.sub_n[J];
+  const int bJ = g.nbf[J];
+  const int c0 = g.sub_c0[J];
+  const double* S = g.ws + (g.a_off[J] - g.a_base);
+  const double* H = S + g.chunk_n2;
+  float* L = g.L32 + (g.a_off[J] - g.a_base);
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < n * n; e += kThreads) {
+    const int i = e / n, j = e - i * n;
+    if (j <= i) L[e] = (float)S[e];
+  }
+  __syncthreads();
+  bool ok = cholesky<float>(L, n, Pf, Xs, s_rinv, &s_bad);
+  if (ok) {
+    // A_J = L^-T L^-1 T_J(H0) in FP32
+    float* A = Acache + g.a_off[J];
+    solve_A<float, float>(L, H, n, A, Pf, Pf + NB * Ld<float>::v);
+    __syncthreads();
+    // Q_J: FP32 solve, then refinement with the FP64 residual
+    const int nbc = n * bJ;
+    float* w = g.W32 + (g.c_off[J] - g.c_base);
+    double* r = g.R64 + (g.c_off[J] - g.c_base);
+    double* q = g.Q + g.c_off[J];
+    for (int e = tid; e < nbc; e += kThreads) {
+      const int i = e / bJ, c = e - i * bJ;
+      w[e] = (i == c0 + c) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    solve_cols32(L, n, bJ, w, Acc, Xs);
+    for (int e = tid; e < nbc; e += kThreads) q[e] = (double)w[e];
+    __syncthreads();
+    bool conv = false;
+    for (int it = 0; it < kRefineMax && !conv; ++it) {
+      residual64(S, n, c0, bJ, q, r);
+      __syncthreads();
+      for (int e = tid; e < nbc; e += kThreads) w[e] = (float)r[e];
+      __syncthreads();
+      solve_cols32(L, n, bJ, w, Acc, Xs);
+      float dmax = 0.0f;
+      double qmax = 0.0;
+      bool finite = true;
+      for (int e = tid; e < nbc; e += kThreads) {
+        const float d = w[e];
+        const double qe = q[e] + (double)d;
+        q[e] = qe;
+        finite = finite && isfinite(d) && isfinite(qe);
+        dmax = fmaxf(dmax, fabsf(d));
+        qmax = fmax(qmax, fabs(qe));
+      }
+      if (!finite) dmax = INFINITY;
+      for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+      }
+      if (lane == 0) {
+        red_d[warp] = dmax;
+        red_q[warp] = qmax;
+      }
+      __syncthreads();
+      float dm = 0.0f;
+      double qm = 0.0;
+      for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+        dm = fmaxf(dm, red_d[w2]);
+        qm = fmax(qm, red_q[w2]);
+      }
+      conv = (double)dm <= kRefineTol * qm;   // the same shared values in every thread
+      __syncthreads();
+    }
+    ok = conv;
+    if (ok) gershgorin(A, n, g.lam + 2 * J, rlo, rhi);
+  }
+  // a failed FP32 factor or a refinement that did not contract: the FP64 preparation takes the
+  // submatrix again when its panel fits in shared memory; otherwise T_J(S) counts as not positive
+  // definite in working precision
+  if (tid == 0) g.prep_status[J] = ok ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
+}
+
+size_t smem_fp64(int max_n) { return sizeof(double) * (size_t)std::max(max_n, 2 * NB) * (NB + 1); }
+size_t smem_mixed(int max_n) { return sizeof(float) * (size_t)std::max(max_n, 2 * NB) * Ld<float>::v; }
+constexpr size_t kSmemLimit = 200 * 1024;
+
 }  // namespace
 
-size_t prepare_smem_bytes(int max_n) { return sizeof(double) * (size_t)max_n * (NB + 1); }
+int prepare_fp64_max_n() { return (int)(kSmemLimit / (sizeof(double) * (NB + 1))); }
 
 nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A, void* Acache, cudaStream_t st) {
-  const size_t smem = prepare_smem_bytes(std::max(max_n, 2 * NB));
-  if (smem > 200 * 1024) {
-    set_error("submatrix dimension %d exceeds the factorisation panel's shared memory", max_n);
+  const size_t smem = smem_fp64(max_n);
+  if (smem > kSmemLimit) {
+    set_error("submatrix dimension %d exceeds the FP64 factorisation panel's shared memory (n <= %d)", max_n,
+              prepare_fp64_max_n());
     return NOLSM_ERR_UNSUPPORTED;
   }
   if (fp64_A) {
@@ -360,6 +658,23 @@ nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A
     k_prepare<float><<<count, kThreads, smem, st>>>(g, static_cast<float*>(Acache));
   }
   NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
+
+nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float* Acache, cudaStream_t st) {
+  const size_t smem = smem_mixed(max_n);
+  if (smem > kSmemLimit) {
+    set_error("submatrix dimension %d exceeds the FP32 factorisation panel's shared memory (n <= %d)", max_n,
+              (int)(kSmemLimit / (sizeof(float) * Ld<float>::v)));
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_prepare_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_prepare_mixed<<<count, kThreads, smem, st>>>(g, Acache);
+  NOLSM_LAUNCH_CHECK();
+  // the FP64 preparation again for the flagged submatrices (every other CTA returns at once)
+  PrepArgs f = g;
+  f.only_flagged = 1;
+  NOLSM_TRY(launch_prepare(f, count, std::min(max_n, prepare_fp64_max_n()), false, Acache, st));
   return NOLSM_OK;
 }
 
