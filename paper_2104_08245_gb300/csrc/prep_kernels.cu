@@ -48,6 +48,11 @@ __device__ __forceinline__ T xinv(const T* S, int n, int r0, int a, int t) {
   return S[(size_t)(r0 + t) * n + r0 + a];  // stored transposed in the upper triangle
 }
 
+// The same for the FP32 factor, which stores X_r in the lower triangle of its diagonal blocks.
+__device__ __forceinline__ float xinv32(const float* L, int n, int r0, int a, int t) {
+  return t > a ? 0.0f : L[(size_t)(r0 + a) * n + r0 + t];
+}
+
 // ------------------------------------------------------------------------------------ Cholesky
 // In place: the lower triangle of S receives L; the strict upper triangle of every diagonal block
 // receives X_r^T. Returns false (uniformly) if a pivot is not positive or not finite.
@@ -120,11 +125,15 @@ __device__ bool cholesky(T* __restrict__ S, int n, T* __restrict__ Ps, T (*Xs)[N
       __syncthreads();
     }
     if (*s_bad) return false;
-    // write back L (panel) and X^T (upper triangle of the diagonal block)
+    // write back L (panel) and X^T (upper triangle of the diagonal block); the FP32 factor keeps X_r
+    // itself (diagonal 1/L_ii) in the lower triangle of the diagonal block, which no solve reads as L
     for (int e = tid; e < mt * kb; e += kThreads) {
       const int i = e / kb, t = e - i * kb;
-      if (i >= kb || t <= i) S[(size_t)(k0 + i) * n + k0 + t] = Ps[i * LDP + t];
-      else S[(size_t)(k0 + i) * n + k0 + t] = Xs[t][i];
+      T v;
+      if (i >= kb) v = Ps[i * LDP + t];
+      else if (t > i) v = Xs[t][i];
+      else v = sizeof(T) == 4 ? Xs[i][t] : Ps[i * LDP + t];
+      S[(size_t)(k0 + i) * n + k0 + t] = v;
     }
     // trailing update of the lower triangle, 32 x 32 tiles, 4 x 2 outputs per thread
     const int r0 = kb, m = mt - kb;   // panel-local first trailing row, trailing size
@@ -351,6 +360,148 @@ __device__ void solve_A(const LT* __restrict__ S, const double* __restrict__ H, 
   }
 }
 
+// FP32 form for the mixed preparation, as an outer product. Columns c < n are the columns of T_J(H0)
+// (result into X, n x n); columns n <= c < n + b are the centre columns of the identity (result into W,
+// n x b), the first solve of Q. For each 32-row block the whole block row of L needed by the step is
+// staged once, transposed (LT[t][i], so that every t broadcasts one right-hand-side value to 32
+// independent accumulators via 16-byte shared loads), together with X_r (XfT). Shared memory: sm holds
+// (n + 32) x (NB + 4) floats.
+__device__ void solve_A32(const float* __restrict__ L, const double* __restrict__ H, int n, int c0, int b,
+                          float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm) {
+  constexpr int LDA = Ld<float>::v;
+  const int tid = threadIdx.x;
+  const int nblk = (n + NB - 1) / NB;
+  const int ncol = n + b;
+  for (int cb = 0; cb < ncol; cb += kThreads) {
+    const int c = cb + tid;
+    const bool act = c < ncol;
+    const bool qcol = c >= n;
+    float* dst = qcol ? W + (c - n) : X + c;   // this thread's column of the result
+    const int ld = qcol ? b : n;
+    // forward: Y = L^-1 RHS
+    for (int rbk = 0; rbk < nblk; ++rbk) {
+      const int r0 = rbk * NB, rb = min(NB, n - r0);
+      float acc[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        float v = 0.0f;
+        if (act && i < rb) v = qcol ? (r0 + i == c0 + c - n ? 1.0f : 0.0f) : (float)H[(size_t)(r0 + i) * n + c];
+        acc[i] = v;
+      }
+      float* LT = sm;                   // [r0][LDA]: LT[t][i] = L[r0+i][t]
+      float* XfT = sm + r0 * LDA;       // [NB][LDA]: XfT[t][a] = X_r[a][t]
+      for (int e = tid; e < r0 * NB; e += kThreads) {
+        const int i = e / r0, t = e - i * r0;
+        LT[t * LDA + i] = i < rb ? L[(size_t)(r0 + i) * n + t] : 0.0f;
+      }
+      for (int e = tid; e < NB * NB; e += kThreads) {
+        const int a = e >> 5, t = e & 31;
+        XfT[t * LDA + a] = (a < rb && t < rb) ? xinv32(L, n, r0, a, t) : 0.0f;
+      }
+      __syncthreads();
+      if (act) {
+        for (int q0 = 0; q0 < r0; q0 += NB) {
+          float y[NB];
+#pragma unroll
+          for (int t = 0; t < NB; ++t) y[t] = dst[(size_t)(q0 + t) * ld];
+#pragma unroll
+          for (int t = 0; t < NB; ++t) {
+            const float yt = y[t];
+            const float* lrow = LT + (q0 + t) * LDA;
+#pragma unroll
+            for (int i = 0; i < NB; i += 4) {
+              const float4 l = *reinterpret_cast<const float4*>(lrow + i);
+              acc[i] = fmaf(-l.x, yt, acc[i]);
+              acc[i + 1] = fmaf(-l.y, yt, acc[i + 1]);
+              acc[i + 2] = fmaf(-l.z, yt, acc[i + 2]);
+              acc[i + 3] = fmaf(-l.w, yt, acc[i + 3]);
+            }
+          }
+        }
+        float o[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) o[a] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {   // y = X_r acc (XfT[t][a] zero for a < t)
+          const float at = acc[t];
+#pragma unroll
+          for (int a = t & ~3; a < NB; a += 4) {
+            const float4 x4 = *reinterpret_cast<const float4*>(XfT + t * LDA + a);
+            o[a] = fmaf(x4.x, at, o[a]);
+            o[a + 1] = fmaf(x4.y, at, o[a + 1]);
+            o[a + 2] = fmaf(x4.z, at, o[a + 2]);
+            o[a + 3] = fmaf(x4.w, at, o[a + 3]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+          if (a < rb) dst[(size_t)(r0 + a) * ld] = o[a];
+      }
+      __syncthreads();
+    }
+    // backward: result = L^-T Y
+    for (int rbk = nblk - 1; rbk >= 0; --rbk) {
+      const int r0 = rbk * NB, rb = min(NB, n - r0);
+      const int q0 = r0 + rb, m = n - q0;   // rows below the block
+      float acc[NB];
+#pragma unroll
+      for (int i = 0; i < NB; ++i) acc[i] = (act && i < rb) ? dst[(size_t)(r0 + i) * ld] : 0.0f;
+      float* LT = sm;                   // [m][LDA]: LT[t][i] = L[q0+t][r0+i]
+      float* XfT = sm + ((m + 3) & ~3) * LDA;   // [NB][LDA]: XfT[t][a] = X_r[t][a]
+      for (int e = tid; e < m * NB; e += kThreads) {
+        const int t = e >> 5, i = e & 31;
+        LT[t * LDA + i] = i < rb ? L[(size_t)(q0 + t) * n + r0 + i] : 0.0f;
+      }
+      for (int e = tid; e < NB * NB; e += kThreads) {
+        const int t = e >> 5, a = e & 31;
+        XfT[t * LDA + a] = (a < rb && t < rb) ? xinv32(L, n, r0, t, a) : 0.0f;
+      }
+      __syncthreads();
+      if (act) {
+        for (int t0 = 0; t0 < m; t0 += NB) {
+          float x[NB];
+#pragma unroll
+          for (int t = 0; t < NB; ++t) x[t] = t0 + t < m ? dst[(size_t)(q0 + t0 + t) * ld] : 0.0f;
+#pragma unroll
+          for (int t = 0; t < NB; ++t) {
+            if (t0 + t < m) {
+              const float xt = x[t];
+              const float* lrow = LT + (t0 + t) * LDA;
+#pragma unroll
+              for (int i = 0; i < NB; i += 4) {
+                const float4 l = *reinterpret_cast<const float4*>(lrow + i);
+                acc[i] = fmaf(-l.x, xt, acc[i]);
+                acc[i + 1] = fmaf(-l.y, xt, acc[i + 1]);
+                acc[i + 2] = fmaf(-l.z, xt, acc[i + 2]);
+                acc[i + 3] = fmaf(-l.w, xt, acc[i + 3]);
+              }
+            }
+          }
+        }
+        float o[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) o[a] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {   // x = X_r^T acc (XfT[t][a] zero for a > t)
+          const float at = acc[t];
+#pragma unroll
+          for (int a = 0; a <= (t | 3); a += 4) {
+            const float4 x4 = *reinterpret_cast<const float4*>(XfT + t * LDA + a);
+            o[a] = fmaf(x4.x, at, o[a]);
+            o[a + 1] = fmaf(x4.y, at, o[a + 1]);
+            o[a + 2] = fmaf(x4.z, at, o[a + 2]);
+            o[a + 3] = fmaf(x4.w, at, o[a + 3]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+          if (a < rb) dst[(size_t)(r0 + a) * ld] = o[a];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------ Q = L^-T L^-1 E_c (FP64)
 // Threads take (row, column) pairs so that every FP64 instruction is issued by full warps.
 __device__ void solve_Q(const double* __restrict__ S, int n, int c0, int b, double* __restrict__ Q,
@@ -419,7 +570,7 @@ __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* _
     }
     for (int e = tid; e < NB * NB; e += kThreads) {
       const int a = e >> 5, t = e & 31;
-      Xd[a][t] = (a < rb && t < rb) ? xinv(L, n, r0, a, t) : 0.0f;
+      Xd[a][t] = (a < rb && t < rb) ? xinv32(L, n, r0, a, t) : 0.0f;
     }
     __syncthreads();
     for (int e = tid; e < rb * b; e += kThreads) {
@@ -440,7 +591,7 @@ __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* _
     }
     for (int e = tid; e < NB * NB; e += kThreads) {
       const int a = e >> 5, t = e & 31;
-      Xd[a][t] = (a < rb && t < rb) ? xinv(L, n, r0, a, t) : 0.0f;
+      Xd[a][t] = (a < rb && t < rb) ? xinv32(L, n, r0, a, t) : 0.0f;
     }
     __syncthreads();
     for (int e = tid; e < rb * b; e += kThreads) {
@@ -548,9 +699,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_prepare(PrepArgs g, TA* __restr
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float* __restrict__ Acache) {
-  extern __shared__ __align__(16) float Pf[];   // factorisation panel: n x (NB+4) floats
+  extern __shared__ __align__(16) float Pf[];   // panel (n x (NB+4)), then solve tiles ((n+36) x (NB+4))
   __shared__ float Xs[NB][NB + 1];
-  __shared__ float Acc[NB][kMaxB + 1];
   __shared__ float s_rinv[2];
   __shared__ int s_bad;
   __shared__ float rlo[kThreads], rhi[kThreads];
@@ -564,6 +714,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   const double* S = g.ws + (g.a_off[J] - g.a_base);
   const double* H = S + g.chunk_n2;
   float* L = g.L32 + (g.a_off[J] - g.a_base);
+  float (*Acc)[kMaxB + 1] = reinterpret_cast<float (*)[kMaxB + 1]>(Pf);   // solve_cols32 (after the solves)
   if (tid == 0) s_bad = 0;
   for (int e = tid; e < n * n; e += kThreads) {
     const int i = e / n, j = e - i * n;
@@ -572,21 +723,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   __syncthreads();
   bool ok = cholesky<float>(L, n, Pf, Xs, s_rinv, &s_bad);
   if (ok) {
-    // A_J = L^-T L^-1 T_J(H0) in FP32
+    // A_J = L^-T L^-1 T_J(H0) in FP32, and the FP32 first solve of Q when its b columns fit in the
+    // last column batch
     float* A = Acache + g.a_off[J];
-    solve_A<float, float>(L, H, n, A, Pf, Pf + NB * Ld<float>::v);
-    __syncthreads();
-    // Q_J: FP32 solve, then refinement with the FP64 residual
     const int nbc = n * bJ;
     float* w = g.W32 + (g.c_off[J] - g.c_base);
     double* r = g.R64 + (g.c_off[J] - g.c_base);
     double* q = g.Q + g.c_off[J];
-    for (int e = tid; e < nbc; e += kThreads) {
-      const int i = e / bJ, c = e - i * bJ;
-      w[e] = (i == c0 + c) ? 1.0f : 0.0f;
+    const bool merge_q = (n + bJ + kThreads - 1) / kThreads == (n + kThreads - 1) / kThreads;
+    solve_A32(L, H, n, c0, merge_q ? bJ : 0, A, w, Pf);
+    if (!merge_q) {
+      for (int e = tid; e < nbc; e += kThreads) {
+        const int i = e / bJ, c = e - i * bJ;
+        w[e] = (i == c0 + c) ? 1.0f : 0.0f;
+      }
+      __syncthreads();
+      solve_cols32(L, n, bJ, w, Acc, Xs);
     }
-    __syncthreads();
-    solve_cols32(L, n, bJ, w, Acc, Xs);
+    // Q_J: refinement with the FP64 residual
     for (int e = tid; e < nbc; e += kThreads) q[e] = (double)w[e];
     __syncthreads();
     bool conv = false;
@@ -636,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
 }
 
 size_t smem_fp64(int max_n) { return sizeof(double) * (size_t)std::max(max_n, 2 * NB) * (NB + 1); }
-size_t smem_mixed(int max_n) { return sizeof(float) * (size_t)std::max(max_n, 2 * NB) * Ld<float>::v; }
+size_t smem_mixed(int max_n) { return sizeof(float) * (size_t)(std::max(max_n, 2 * NB) + 36) * Ld<float>::v; }
 constexpr size_t kSmemLimit = 200 * 1024;
 
 }  // namespace
