@@ -201,12 +201,87 @@ typedef struct {
   double flops_tensor_padded;  /* same on the padded tile shapes the kernel executes */
   double flops_fp64;           /* FP64 flops of the factorisation and solves (a2, a3) */
   int64_t launches;            /* kernels launched for this plan */
+  int64_t reruns;              /* submatrices solved again after failing the convergence test under
+                                  learned or power-iteration bounds */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);
 nolsm_status nolsm_plan_stats_reset(nolsm_plan* plan);
 
 void nolsm_plan_destroy(nolsm_plan* plan);
+
+/* ---------------------------------------------------------------------------------------------
+ * a4 bound sources and a10, the learned bound predictor. No counterpart in the paper, which only
+ * requires a rescaling before the sign iteration (Sec. "Linear-Scaling Electronic Structure
+ * Calculations", after Eq. NS2) and runs a fixed number of steps (Sec. "Efficient Iterative Matrix
+ * Function Solvers on GPU Tensor Cores").
+ *
+ * Bound sources (nolsm_options.bound_source) for the scale alpha_J(mu) = max(hi - mu, mu - lo):
+ *   NOLSM_BOUND_GERSHGORIN  the Gershgorin interval of A_J (always safe);
+ *   NOLSM_BOUND_POWER       [lo, hi] from 30 steps of two shifted power iterations on A_J (A_J - lo_G I
+ *                           and hi_G I - A_J), widened by 5 % of the width, clipped to Gershgorin;
+ *   NOLSM_BOUND_MLP         the plan's network (nolsm_plan_set_mlp) predicts (lo, hi, steps / 16) from the
+ *                           features below (trained on the power interval, which is already widened); the
+ *                           interval, widened by 1 % of its width and clipped to Gershgorin, sets alpha,
+ *                           and ceil(1.5 * steps) + 3 caps the submatrix's Newton-Schulz steps.
+ * In every source alpha is at least 1/1.7 of the Gershgorin alpha, so every eigenvalue of X_0 lies in
+ * [-1.7, 1.7], where the Newton-Schulz map keeps its sign.
+ * Every submatrix whose sign iteration fails the convergence test (or turns non-finite) under MLP
+ * bounds is solved again with power bounds, and under power bounds again with the Gershgorin interval,
+ * within the same nolsm_solve_batch call: no submatrix is accepted unconverged (stats.reruns counts).
+ *
+ * Features of submatrix J (float32, 7 per submatrix, in this order): n_J / 100, Gershgorin lo and hi
+ * of A_J, |N(J)| / 32, mean and standard deviation of diag T_J(H0), mu.
+ * Network: h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), y = h2 W3 + b3, width 128, FP32; parameters in
+ * one float32 array of nolsm_mlp_param_count() values: W1 [7][128], b1 [128], W2 [128][128], b2 [128],
+ * W3 [128][3], b3 [3] (weights [fan_in][fan_out] row-major). Loss 1/(2B) sum (y - t)^2; Adam.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct nolsm_mlp nolsm_mlp; /* opaque; owns its parameters, Adam state and workspaces */
+
+int32_t nolsm_mlp_param_count(void);
+
+/* Glorot-uniform weights from SplitMix64(seed, parameter index), zero biases, Adam state zero. */
+nolsm_status nolsm_mlp_create(uint64_t seed, nolsm_stream_t stream, nolsm_mlp** out);
+void nolsm_mlp_destroy(nolsm_mlp* mlp);
+
+/* Parameters to / from host memory (nolsm_mlp_param_count() floats); set also resets the Adam state. */
+nolsm_status nolsm_mlp_get_params(const nolsm_mlp* mlp, float* host_params);
+nolsm_status nolsm_mlp_set_params(nolsm_mlp* mlp, const float* host_params);
+
+/* y [B][3] = network(x [B][7]); x, y device float32. */
+nolsm_status nolsm_mlp_forward(nolsm_mlp* mlp, int32_t B, const float* x, float* y, nolsm_stream_t stream);
+
+/* Gradient of the loss over the batch (x [B][7], targets t [B][3], device) by the backward pass; kept for
+ * nolsm_mlp_adam_step and copied to grad_host (nullable, param_count floats); loss (nullable, host). */
+nolsm_status nolsm_mlp_gradient(nolsm_mlp* mlp, int32_t B, const float* x, const float* t, nolsm_stream_t stream,
+                                float* grad_host, double* loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradient. */
+nolsm_status nolsm_mlp_adam_step(nolsm_mlp* mlp, float lr, nolsm_stream_t stream);
+
+/* Minibatch Adam training on N samples (x [N][7], t [N][3], device): epochs passes of ceil(N / batch)
+ * steps, sample order (r * 7919 + epoch * 104729) mod N. epoch_loss (host, nullable, [epochs]) receives
+ * the mean minibatch loss of each epoch. */
+nolsm_status nolsm_mlp_train(nolsm_mlp* mlp, int32_t N, const float* x, const float* t, int32_t epochs,
+                             int32_t batch, float lr, nolsm_stream_t stream, double* epoch_loss);
+
+/* The network NOLSM_BOUND_MLP uses in this plan's solves (NULL: none); it must outlive that use. */
+nolsm_status nolsm_plan_set_mlp(nolsm_plan* plan, const nolsm_mlp* mlp);
+
+/* Features (device, float32 [n_mol][7]) of the submatrices in the options' range at mu (prepares a1-a3
+ * for the range first). Synchronises the stream. */
+nolsm_status nolsm_features(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                            float* feat);
+
+/* Power-iteration interval (device, float64 [2*n_mol], nullable) of the submatrices in the options' range
+ * (prepares a1-a3 first; cached in the plan). Synchronises the stream. */
+nolsm_status nolsm_power_bounds(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, double* lam);
+
+/* Training samples the method produces for the learned predictor, for the options' range at mu:
+ * x = features (device float32 [n_mol][7]); t = (power-iteration lo, hi, Newton-Schulz steps / 16 of a
+ * solve at mu with power bounds) (device float32 [n_mol][3]). Runs that solve. Synchronises the stream. */
+nolsm_status nolsm_training_data(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                                 float* x, float* t);
 
 /* Allocation-free sign iteration. No counterpart in the paper.
  *

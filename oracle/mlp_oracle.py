@@ -96,3 +96,24 @@ def features(A: np.ndarray, H_sub: np.ndarray, n_nb: int, mu: float) -> np.ndarr
     hd = np.diag(H_sub)
     return np.array([A.shape[0] / 100.0, float(np.min(d - R)), float(np.max(d + R)), n_nb / 32.0,
                      float(np.mean(hd)), float(np.std(hd)), mu])
+
+
+ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def pack(p: dict) -> np.ndarray:
+    """Flat parameter vector in the library's order W1, b1, W2, b2, W3, b3 (row-major)."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).ravel() for k in ORDER])
+
+
+def unpack(flat, n_in=N_FEATURES, width=WIDTH, n_out=N_OUT) -> dict:
+    shapes = {"W1": (n_in, width), "b1": (width,), "W2": (width, width), "b2": (width,),
+              "W3": (width, n_out), "b3": (n_out,)}
+    out, o = {}, 0
+    flat = np.asarray(flat, dtype=np.float64)
+    for k in ORDER:
+        m = int(np.prod(shapes[k]))
+        out[k] = flat[o:o + m].reshape(shapes[k]).copy()
+        o += m
+    assert o == flat.size
+    return out

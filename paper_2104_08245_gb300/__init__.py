@@ -17,7 +17,8 @@ from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4
 
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
-           "nolsm_spectral_bracket",
+           "nolsm_spectral_bracket", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
+           "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
            "options", "NolsmError", "Plan", "SolveResult", "MuResult"]
 
 
@@ -251,3 +252,125 @@ class Plan:
 
     def stats_reset(self):
         nolsm_plan_stats_reset(self)
+
+
+# ------------------------------------------------------------------------------------ a4 bounds, a10 network
+
+def nolsm_features(plan: "Plan", mu: float, opts: NolsmOptions, stream=None):
+    """float32 [n_mol, 7] device tensor of features (rows of the options' range written)."""
+    torch = _torch()
+    feat = torch.zeros(plan.dsys.n_mol, 7, dtype=torch.float32, device=plan.dsys.nbf.device)
+    rc = _abi.load().nolsm_features(plan.handle, float(mu), ctypes.byref(opts), _stream(stream), feat.data_ptr())
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_features")
+    return feat
+
+
+def nolsm_power_bounds(plan: "Plan", opts: NolsmOptions, stream=None):
+    """float64 [n_mol, 2] device tensor of power-iteration intervals (rows of the options' range written)."""
+    torch = _torch()
+    lam = torch.zeros(plan.dsys.n_mol, 2, dtype=torch.float64, device=plan.dsys.nbf.device)
+    rc = _abi.load().nolsm_power_bounds(plan.handle, ctypes.byref(opts), _stream(stream), lam.data_ptr())
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_power_bounds")
+    return lam
+
+
+def nolsm_training_data(plan: "Plan", mu: float, opts: NolsmOptions, stream=None):
+    """(x [n_mol, 7], t [n_mol, 3]) float32 device tensors: features and the method's own targets."""
+    torch = _torch()
+    dev = plan.dsys.nbf.device
+    x = torch.zeros(plan.dsys.n_mol, 7, dtype=torch.float32, device=dev)
+    t = torch.zeros(plan.dsys.n_mol, 3, dtype=torch.float32, device=dev)
+    rc = _abi.load().nolsm_training_data(plan.handle, float(mu), ctypes.byref(opts), _stream(stream), x.data_ptr(),
+                                         t.data_ptr())
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_training_data")
+    return x, t
+
+
+def nolsm_plan_set_mlp(plan: "Plan", mlp: Optional["Mlp"]) -> None:
+    rc = _abi.load().nolsm_plan_set_mlp(plan.handle, None if mlp is None else mlp.handle)
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_set_mlp")
+    plan.mlp = mlp   # keeps the network alive while the plan may use it
+
+
+MLP_PARAMS = 17923
+
+
+class Mlp:
+    """Owner of a nolsm_mlp handle: the learned bound predictor's network (FP32 on the device)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        lib = _abi.load()
+        h = ctypes.c_void_p()
+        rc = lib.nolsm_mlp_create(ctypes.c_uint64(seed), _stream(stream), ctypes.byref(h))
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_create")
+        self.handle = h
+        self.n_params = lib.nolsm_mlp_param_count()
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _abi.load().nolsm_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        out = np.zeros(self.n_params, dtype=np.float32)
+        rc = _abi.load().nolsm_mlp_get_params(self.handle, out.ctypes.data)
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_get_params")
+        return out
+
+    def set_params(self, params) -> None:
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.size}")
+        rc = _abi.load().nolsm_mlp_set_params(self.handle, p.ctypes.data)
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_set_params")
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        x = x.contiguous()
+        y = torch.zeros(x.shape[0], 3, dtype=torch.float32, device=x.device)
+        rc = _abi.load().nolsm_mlp_forward(self.handle, int(x.shape[0]), x.data_ptr(), y.data_ptr(), _stream(stream))
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_forward")
+        return y
+
+    def gradient(self, x, t, stream=None):
+        """(flat float32 gradient on the host, loss) of the batch."""
+        import numpy as np
+        x, t = x.contiguous(), t.contiguous()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        rc = _abi.load().nolsm_mlp_gradient(self.handle, int(x.shape[0]), x.data_ptr(), t.data_ptr(),
+                                            _stream(stream), g.ctypes.data, ctypes.byref(loss))
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_gradient")
+        return g, loss.value
+
+    def adam_step(self, lr: float, stream=None) -> None:
+        rc = _abi.load().nolsm_mlp_adam_step(self.handle, ctypes.c_float(lr), _stream(stream))
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_adam_step")
+
+    def train(self, x, t, epochs: int, batch: int, lr: float, stream=None):
+        """Per-epoch mean minibatch loss (list)."""
+        x, t = x.contiguous(), t.contiguous()
+        losses = (ctypes.c_double * epochs)()
+        rc = _abi.load().nolsm_mlp_train(self.handle, int(x.shape[0]), x.data_ptr(), t.data_ptr(), int(epochs),
+                                         int(batch), ctypes.c_float(lr), _stream(stream), losses)
+        if rc != 0:
+            raise NolsmError(rc, "nolsm_mlp_train")
+        return list(losses)

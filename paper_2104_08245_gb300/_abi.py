@@ -39,7 +39,7 @@ class NolsmStats(ctypes.Structure):
     _fields_ = [("ms_plan", c_double), ("ms_prepare", c_double), ("ms_sign", c_double), ("ms_reduce", c_double),
                 ("ms_scatter", c_double), ("solves", c_int64), ("sub_solves", c_int64), ("ns_steps", c_int64),
                 ("flops_paper", c_double), ("flops_tensor", c_double), ("flops_tensor_padded", c_double),
-                ("flops_fp64", c_double), ("launches", c_int64)]
+                ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,6 +66,22 @@ SIGNATURES = [
     ("nolsm_plan_destroy", None, [c_void_p]),
     ("nolsm_sign_noalloc", c_int32, [c_int32] + [c_void_p] * 9 + [c_double, ctypes.POINTER(NolsmOptions), c_void_p]
      + [c_void_p] * 5),
+    ("nolsm_mlp_param_count", c_int32, []),
+    ("nolsm_mlp_create", c_int32, [ctypes.c_uint64, c_void_p, ctypes.POINTER(c_void_p)]),
+    ("nolsm_mlp_destroy", None, [c_void_p]),
+    ("nolsm_mlp_get_params", c_int32, [c_void_p, c_void_p]),
+    ("nolsm_mlp_set_params", c_int32, [c_void_p, c_void_p]),
+    ("nolsm_mlp_forward", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    ("nolsm_mlp_gradient", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     ctypes.POINTER(c_double)]),
+    ("nolsm_mlp_adam_step", c_int32, [c_void_p, ctypes.c_float, c_void_p]),
+    ("nolsm_mlp_train", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_int32, ctypes.c_float,
+                                  c_void_p, c_void_p]),
+    ("nolsm_plan_set_mlp", c_int32, [c_void_p, c_void_p]),
+    ("nolsm_features", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p]),
+    ("nolsm_power_bounds", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p]),
+    ("nolsm_training_data", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p,
+                                      c_void_p]),
     ("nolsm_status_str", ctypes.c_char_p, [c_int32]),
     ("nolsm_last_error", ctypes.c_char_p, []),
 ]

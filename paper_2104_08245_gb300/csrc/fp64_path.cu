@@ -176,9 +176,13 @@ struct NsArgs {
   const int32_t* sub_n; const int32_t* nbf;
   const int64_t* a_off; const int64_t* c_off;
   const double* A; const double* Q; const double* Sc; const double* Hc; const double* lam;
+  const double* lam_g;         // Gershgorin interval (the scale never drops below its alpha / 1.7)
   const int32_t* prep_status;
   double mu, tol;
   int32_t max_iter;
+  const int32_t* budget;       // per-submatrix step cap (nullable)
+  const int32_t* list;         // work list (nullable: [j0, j1))
+  int32_t count;
   double* ws; int64_t slot_elems;
   int32_t* next;               // work counter
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
@@ -193,11 +197,14 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
   double* T = X + g.slot_elems;
   double* Xn = T + g.slot_elems;
   for (;;) {
-    if (threadIdx.x == 0) job = g.j0 + atomicAdd(g.next, 1);
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(g.next, 1);
+      job = g.list ? (k < g.count ? g.list[k] : -1) : (g.j0 + k < g.j1 ? g.j0 + k : -1);
+    }
     __syncthreads();
     const int J = job;
     __syncthreads();
-    if (J >= g.j1) break;
+    if (J < 0) break;
     if (g.prep_status[J] != kSubOk) {
       if (threadIdx.x == 0) {
         g.status[J] = g.prep_status[J];
@@ -211,8 +218,8 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
     const int n = g.sub_n[J];
     const int64_t nn = (int64_t)n * n;
     const double* A = g.A + g.a_off[J];
-    // a4: X_0 = (A - mu I) / alpha, alpha = max(hi - mu, mu - lo) from the Gershgorin interval
-    const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
+    // a4: X_0 = (A - mu I) / alpha, alpha = max(hi - mu, mu - lo) from the interval of the bound source
+    const double alpha = scale_alpha(g.lam, g.lam_g, J, g.mu);
     const double inv_alpha = 1.0 / alpha;
     for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
       const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
@@ -223,7 +230,8 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
     int it = 0, st = kSubNotConv;
     double* x = X;
     double* xn = Xn;
-    while (it < g.max_iter) {
+    const int cap = g.budget ? min(g.max_iter, g.budget[J]) : g.max_iter;
+    while (it < cap) {
       double part = 0.0;
       cta_dgemm(x, x, n, As, Bs, [&](int i, int j, double acc) {
         const double v = (i == j ? 1.0 : 0.0) - acc;   // (I - X^2)_ij
@@ -446,12 +454,13 @@ nolsm_status ensure_results(nolsm_plan* plan) {
 }
 
 nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1,
-                        cudaStream_t st) {
+                        const SolveSpec& spec, cudaStream_t st) {
   NOLSM_TRY(ensure_results(plan));
   int dev = 0, sms = 0;
   NOLSM_CUDA_TRY(cudaGetDevice(&dev));
   NOLSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int slots = (int)std::min<int64_t>(2 * sms, j1 - j0);
+  const int slots = (int)std::min<int64_t>(2 * sms, spec.list ? spec.count : j1 - j0);
+  if (slots <= 0) return NOLSM_OK;
   int32_t maxn = 0;
   for (int64_t J = j0; J < j1; ++J) maxn = std::max(maxn, plan->h_sub_n[J]);
   const int64_t slot_elems = (int64_t)maxn * maxn;
@@ -462,10 +471,12 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
   g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
   g.A = plan->prep64.A.as<double>(); g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>();
-  g.Hc = plan->Hc.as<double>(); g.lam = plan->lam.as<double>();
+  g.Hc = plan->Hc.as<double>(); g.lam = spec.lam ? spec.lam : plan->lam.as<double>();
+  g.lam_g = plan->lam.as<double>();
   g.prep_status = plan->prep_status.as<int32_t>();
   g.mu = mu; g.tol = o.tol_ns;
   g.max_iter = o.max_iter;
+  g.budget = spec.budget; g.list = spec.list; g.count = spec.count;
   g.ws = plan->ws_ns.as<double>(); g.slot_elems = slot_elems;
   g.next = plan->counter.as<int32_t>();
   g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();

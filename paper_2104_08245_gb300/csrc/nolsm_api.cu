@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "nolsm_internal.cuh"
+#include "bounds.cuh"
 #include "tc_path.cuh"
 
 namespace nolsm {
@@ -67,7 +68,8 @@ using namespace nolsm;
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &Dc,
-                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &ws_ns};
+                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &ws_ns,
+                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
   if (ev_ok)
@@ -187,6 +189,24 @@ static nolsm_status check_options(const nolsm_plan* plan, const nolsm_options* o
   return NOLSM_OK;
 }
 
+// Scale source of one solve: the Gershgorin interval, the power-iteration interval (cached per plan) or
+// the learned interval and step budget (features at mu, then the plan's network).
+static nolsm_status bound_spec(nolsm_plan* plan, int source, double mu, const nolsm_options& o, bool fp64, int64_t j0,
+                               int64_t j1, cudaStream_t st, SolveSpec* spec) {
+  *spec = SolveSpec{};
+  spec->lam = plan->lam.as<double>();
+  if (source == NOLSM_BOUND_POWER) {
+    NOLSM_TRY(power_bounds(plan, fp64, j0, j1, nullptr, 0, st));
+    spec->lam = plan->lam_p.as<double>();
+  } else if (source == NOLSM_BOUND_MLP) {
+    NOLSM_TRY(features(plan, mu, j0, j1, st));
+    NOLSM_TRY(mlp_bounds(plan, j0, j1, o.max_iter, st));
+    spec->lam = plan->lam_m.as<double>();
+    spec->budget = plan->budget.as<int32_t>();
+  }
+  return NOLSM_OK;
+}
+
 nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
                                double* trace_DS, double* trace_DH, double* sub_t_S, double* sub_t_H,
                                int32_t* iters, int32_t* status) {
@@ -199,11 +219,29 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   const bool fp64 = opts->precision == NOLSM_FP64;
   mark(plan, 0, st);
   NOLSM_TRY(prepare_fp64(plan, j0, j1, fp64, st));
+  int level = opts->bound_source;
+  SolveSpec spec;
+  NOLSM_TRY(bound_spec(plan, level, mu, *opts, fp64, j0, j1, st, &spec));
   mark(plan, 1, st);
-  if (fp64) {
-    NOLSM_TRY(solve_fp64(plan, mu, *opts, j0, j1, st));
-  } else {
-    NOLSM_TRY(solve_tc(plan, mu, *opts, j0, j1, st));
+  NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, spec, st) : solve_tc(plan, mu, *opts, j0, j1, spec, st));
+  // submatrices that failed the convergence test under learned bounds are solved again with power
+  // bounds, under power bounds with the Gershgorin interval
+  while (level > NOLSM_BOUND_GERSHGORIN) {
+    int32_t count = 0;
+    NOLSM_TRY(failed_list(plan, j0, j1, st, &count));
+    if (count == 0) break;
+    level -= 1;
+    SolveSpec rs;
+    rs.list = plan->rerun.as<int32_t>();
+    rs.count = count;
+    if (level == NOLSM_BOUND_POWER) {
+      NOLSM_TRY(power_bounds(plan, fp64, 0, 0, rs.list, count, st));
+      rs.lam = plan->lam_p.as<double>();
+    } else {
+      rs.lam = plan->lam.as<double>();
+    }
+    NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, rs, st) : solve_tc(plan, mu, *opts, j0, j1, rs, st));
+    plan->stats.reruns += count;
   }
   mark(plan, 2, st);
   double tS = 0, tH = 0;
@@ -308,6 +346,58 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
   if (result == NOLSM_ERR_NO_PLATEAU)
     set_error("nolsm_find_mu: stopped after %d evaluations at mu=%.12g with Tr(DS)=%.9f, target %.9f", step, mu, t, n_occ);
   return result;
+}
+
+nolsm_status nolsm_plan_set_mlp(nolsm_plan* plan, const nolsm_mlp* mlp) {
+  if (!plan) { set_error("nolsm_plan_set_mlp: NULL plan"); return NOLSM_ERR_ARG; }
+  plan->mlp = mlp;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_features(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream, float* feat) {
+  if (!plan || !feat || !std::isfinite(mu)) { set_error("nolsm_features: invalid argument"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  NOLSM_TRY(prepare_fp64(plan, j0, j1, opts->precision == NOLSM_FP64, st));
+  NOLSM_TRY(features(plan, mu, j0, j1, st));
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(feat + j0 * kFeatures, plan->feat.as<float>() + j0 * kFeatures,
+                                 sizeof(float) * kFeatures * (size_t)(j1 - j0), cudaMemcpyDeviceToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_power_bounds(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, double* lam) {
+  if (!plan) { set_error("nolsm_power_bounds: NULL plan"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  const bool fp64 = opts->precision == NOLSM_FP64;
+  NOLSM_TRY(prepare_fp64(plan, j0, j1, fp64, st));
+  NOLSM_TRY(power_bounds(plan, fp64, j0, j1, nullptr, 0, st));
+  if (lam)
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(lam + 2 * j0, plan->lam_p.as<double>() + 2 * j0, sizeof(double) * 2 * (size_t)(j1 - j0),
+                                   cudaMemcpyDeviceToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_training_data(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                                 float* x, float* t) {
+  if (!plan || !x || !t || !std::isfinite(mu)) { set_error("nolsm_training_data: invalid argument"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  nolsm_options o = *opts;
+  o.bound_source = NOLSM_BOUND_POWER;
+  NOLSM_TRY(nolsm_power_bounds(plan, &o, stream, nullptr));
+  NOLSM_TRY(nolsm_features(plan, mu, &o, stream, x));
+  NOLSM_TRY(nolsm_solve_batch(plan, mu, &o, stream, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(training_targets(plan, j0, j1, t, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NOLSM_OK;
 }
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats) {

@@ -10,6 +10,7 @@
 
 namespace nolsm {
 
+
 // Per-submatrix status codes written by kernels (values of nolsm_status).
 enum : int32_t { kSubOk = 0, kSubNotSpd = NOLSM_ERR_NOT_SPD, kSubNotConv = NOLSM_ERR_NOT_CONVERGED,
                  kSubNonFinite = NOLSM_ERR_NONFINITE, kSubTimeout = NOLSM_ERR_TIMEOUT };
@@ -77,6 +78,19 @@ struct nolsm_plan {
   nolsm::DevBuf prep_status;  // int32 [n_mol]: kSubOk or kSubNotSpd from the factorisation
   nolsm::Prepared prep64, prep32;
 
+  // bound sources other than Gershgorin (bounds.cu)
+  nolsm::DevBuf lam_p;              // float64 [2*n_mol]: power-iteration interval
+  std::vector<uint8_t> pow_done;    // host flag per submatrix: lam_p computed (for pow_fp64)
+  bool pow_fp64 = false;
+  nolsm::DevBuf onsite;             // float64 [2*n_mol]: sum and sum of squares of diag(H0_II)
+  bool onsite_done = false;
+  nolsm::DevBuf feat;               // float32 [n_mol*7]: features of the last features() call
+  nolsm::DevBuf mlp_y;              // float32 [n_mol*3]: network outputs
+  nolsm::DevBuf lam_m;              // float64 [2*n_mol]: learned interval
+  nolsm::DevBuf budget;             // int32 [n_mol]: learned step budget
+  nolsm::DevBuf rerun;              // int32 [n_mol + 1]: failed submatrices, then their count
+  const nolsm_mlp* mlp = nullptr;   // network used by NOLSM_BOUND_MLP (caller-owned)
+
   // per-mu results
   nolsm::DevBuf Dc;                 // centre columns of T_J(D), FP64, at c_off[J]
   nolsm::DevBuf t_S, t_H;           // float64 [n_mol]
@@ -112,8 +126,26 @@ nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st);
 
 // per-geometry preparation and per-mu solve of the FP64 path (fp64_path.cu)
 nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp64_A, cudaStream_t st);
+// a4 scale of submatrix J at mu: alpha = max(hi - mu, mu - lo) of the bound source's interval, but not
+// below 1/1.7 of the same from the Gershgorin interval [lg, hg], which contains the spectrum. Every
+// eigenvalue of X_0 then lies in [-1.7, 1.7] inside (-sqrt(3), sqrt(3)), where the Newton-Schulz map
+// keeps its sign and converges, whatever the learned or estimated interval says.
+__host__ __device__ inline double scale_alpha(const double* lam, const double* lam_g, int J, double mu) {
+  const double a = fmax(lam[2 * J + 1] - mu, mu - lam[2 * J]);
+  const double ag = fmax(lam_g[2 * J + 1] - mu, mu - lam_g[2 * J]);
+  return fmax(a, ag * (1.0 / 1.7));
+}
+
+// Scale source and work list of one solve: lam = interval per submatrix (Gershgorin, power or learned),
+// budget = per-submatrix step cap (nullable); list/count = solve only list[0, count) instead of [j0, j1).
+struct SolveSpec {
+  const double* lam = nullptr;
+  const int32_t* budget = nullptr;
+  const int32_t* list = nullptr;
+  int32_t count = 0;
+};
 nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1,
-                        cudaStream_t st);
+                        const SolveSpec& spec, cudaStream_t st);
 
 nolsm_status ensure_results(nolsm_plan* plan);
 

@@ -60,10 +60,12 @@ struct TcArgs {
   const int64_t* a_off; const int64_t* c_off;
   const float* A;             // FP32 A_J
   const double* Q; const double* Sc; const double* Hc; const double* lam;
+  const double* lam_g;        // Gershgorin interval (the scale never drops below its alpha / 1.7)
   const int32_t* prep_status;
   double mu;
   float tol_ns, tol_accept;
   int32_t max_iter, refine_steps;
+  const int32_t* budget;      // per-submatrix step cap (nullable)
   Fmt main_fmt, refine_fmt;
   uint16_t* planes;           // [slots*6][R][LD]
   float* xf;                  // [slots][R][LD]
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
         const float* A = g.A + g.a_off[J];
-        const double alpha = fmax(g.lam[2 * J + 1] - g.mu, g.mu - g.lam[2 * J]);
+        const double alpha = scale_alpha(g.lam, g.lam_g, J, g.mu);
         const float inv = (float)(1.0 / alpha), fmu = (float)g.mu;
         uint16_t* hi = g.planes + (size_t)(sub0 + s) * kPlanes * plane_elems;
         uint16_t* lo = hi + plane_elems;
@@ -557,7 +559,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               status = dd <= g.tol_accept ? kSubOk : kSubNotConv;
             }
           }
-          if (!last_ && steps >= g.max_iter) {
+          const int cap = g.budget ? min(g.max_iter, g.budget[st.job]) : g.max_iter;
+          if (!last_ && steps >= cap) {
             last_ = 1;
             status = kSubNotConv;
           }
@@ -653,7 +656,8 @@ static bool formats(int precision, Fmt* main_fmt, Fmt* refine_fmt) {
   }
 }
 
-nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1, cudaStream_t st) {
+nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1, const SolveSpec& spec,
+                      cudaStream_t st) {
   Fmt mf, rf;
   if (!formats(o.precision, &mf, &rf)) {
     set_error("precision %d is not available on the tensor-core path in this build", o.precision);
@@ -668,7 +672,9 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   for (int64_t J = j0; J < j1; ++J) maxn = std::max(maxn, plan->h_sub_n[J]);
   const int LD = (maxn + 63) & ~63, R = (maxn + 127) & ~127;
   // one CTA per SM at most, each with kSlots submatrices in flight (one scratch sub-slot each)
-  const int ctas = (int)std::min<int64_t>(sms, (j1 - j0 + kSlots - 1) / kSlots);
+  const int64_t work = spec.list ? spec.count : j1 - j0;
+  if (work <= 0) return NOLSM_OK;
+  const int ctas = (int)std::min<int64_t>(sms, (work + kSlots - 1) / kSlots);
   const int slots = ctas * kSlots;
   if (!S->planes.p || S->R < R || S->LD < LD || S->slots < slots) {
     const int nR = std::max(R, S->R), nLD = std::max(LD, S->LD), nS = std::max(slots, S->slots);
@@ -705,17 +711,24 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
   NOLSM_CUDA_TRY(cudaMemsetAsync(S->err.p, 0, sizeof(int32_t), st));
   TcArgs g;
-  g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
-  g.order = S->order.as<int32_t>();
+  if (spec.list) {   // an explicit work list (reruns): in list order
+    g.j0 = 0; g.j1 = spec.count;
+    g.order = spec.list;
+  } else {
+    g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
+    g.order = S->order.as<int32_t>();
+  }
   g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
   g.A = plan->prep32.A.as<float>();
   g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
-  g.lam = plan->lam.as<double>();
+  g.lam = spec.lam ? spec.lam : plan->lam.as<double>();
+  g.lam_g = plan->lam.as<double>();
   g.prep_status = plan->prep_status.as<int32_t>();
   g.mu = mu;
   g.tol_ns = (float)o.tol_ns; g.tol_accept = (float)o.tol_accept;
   g.max_iter = o.max_iter; g.refine_steps = o.refine_steps;
+  g.budget = spec.budget;
   g.main_fmt = mf; g.refine_fmt = rf;
   g.planes = S->planes.as<uint16_t>(); g.xf = S->xf.as<float>();
   g.R = S->R; g.LD = S->LD;
@@ -838,11 +851,12 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.j0 = 0; g.j1 = count;
   g.order = ints;
   g.sub_n = sub_n; g.nbf = nbf; g.a_off = a_off; g.c_off = c_off;
-  g.A = A; g.Q = Q; g.Sc = Sc; g.Hc = Hc; g.lam = lam;
+  g.A = A; g.Q = Q; g.Sc = Sc; g.Hc = Hc; g.lam = lam; g.lam_g = lam;
   g.prep_status = ints + kNaMaxSub;
   g.mu = mu;
   g.tol_ns = (float)opts->tol_ns; g.tol_accept = (float)opts->tol_accept;
   g.max_iter = opts->max_iter; g.refine_steps = opts->refine_steps;
+  g.budget = nullptr;
   g.main_fmt = mf; g.refine_fmt = rf;
   g.planes = reinterpret_cast<uint16_t*>(base);
   g.xf = reinterpret_cast<float*>(base + kNaPlanesBytes);
