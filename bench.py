@@ -47,6 +47,30 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
+# FP32 SIMT peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _src_sha(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def kernel_traffic(kernel, units_per_launch):
+    """DRAM bytes per launch of a kernel from the committed ncu summary (profiles/traffic.json), scaled
+    by the units (submatrices) one launch processes; None when the kernel's source changed since the
+    counters were taken or no capture exists."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f).get(kernel)
+    if not d or _src_sha(d["source"]) != d["source_sha1"]:
+        return None
+    return d["dram_bytes"] / d["units"] * units_per_launch
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -208,6 +232,60 @@ def reference_arm(args, spec_name, desc):
     return 0
 
 
+# ------------------------------------------------------------------------------------ bound sources
+
+def bound_sources_leg(nl, synth, spec_name, dsys, mu_star, precision, dev):
+    """a4/a10: the learned predictor trained on samples the method produces on this system (power
+    interval and step counts at three chemical potentials around mu*), then Gershgorin, power and
+    learned bounds compared on a fresh system of the same kind (another seed) at mu*."""
+    import dataclasses
+
+    import torch
+    o = nl.options(precision)
+    plan = nl.nolsm_build_submatrices(dsys)
+    t0 = time.perf_counter()
+    xs, ts = [], []
+    for dmu in (-0.05, 0.0, 0.05):
+        x, t = nl.nolsm_training_data(plan, mu_star + dmu, o)
+        xs.append(x)
+        ts.append(t)
+    x, t = torch.cat(xs), torch.cat(ts)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    plan.close()
+    mlp = nl.Mlp(seed=11)
+    t0 = time.perf_counter()
+    losses = mlp.train(x, t, epochs=30, batch=1024, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    spec = getattr(synth, spec_name)()
+    fresh = synth.make_system(dataclasses.replace(spec, seed=spec.seed + 1000))
+    p2 = nl.nolsm_build_submatrices(nl.DeviceSystem(fresh, dev))
+    nl.nolsm_plan_set_mlp(p2, mlp)
+    out = {"training_samples": int(x.shape[0]), "epochs": 30, "batch": 1024,
+           "loss_first_last": [losses[0], losses[-1]], "s_training_data": t_data, "s_training": t_train,
+           "evaluated_on": f"fresh system of the same workload (seed {spec.seed + 1000}), mu*"}
+    ref = None
+    for name, b in (("gershgorin", nl.BOUND_GERSHGORIN), ("power", nl.BOUND_POWER), ("mlp", nl.BOUND_MLP)):
+        ob = nl.options(precision, bound_source=b)
+        nl.nolsm_solve_batch(p2, mu_star, ob, check=False)          # geometry caches, power bounds
+        p2.stats_reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = nl.nolsm_solve_batch(p2, mu_star, ob, check=False)
+        dt = time.perf_counter() - t0
+        s2 = p2.stats()
+        D = p2.scatter()
+        if ref is None:
+            ref = D.clone()
+        out[name] = {"mean_ns_steps": float(r.iters.float().mean()), "ms_sign": s2["ms_sign"],
+                     "ms_solve_call": dt * 1e3, "submatrices_per_s_one_mu": fresh.n_mol / dt,
+                     "reruns": int(s2["reruns"]), "status": int(r.status),
+                     "not_converged": int((r.sub_status != 0).sum()),
+                     "max_abs_dD_vs_gershgorin": float((D - ref).abs().max())}
+    p2.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------ our arm
 
 def main():
@@ -342,6 +420,8 @@ def main():
     st = stats_all[-1]
     launches = int(np.mean([s["launches"] for s in stats_all]))
     ms_sign = statistics.mean(s["ms_sign"] for s in stats_all)
+    ms_factor = statistics.mean(s["ms_factor"] for s in stats_all)
+    fl_fp32 = statistics.mean(s["flops_fp32"] for s in stats_all)
     fl_tensor = statistics.mean(s["flops_tensor"] for s in stats_all)
     fl_paper = statistics.mean(s["flops_paper"] for s in stats_all)
     fl_padded = statistics.mean(s["flops_tensor_padded"] for s in stats_all)
@@ -349,10 +429,29 @@ def main():
     fp64_path = args.precision == "fp64"
     achieved = fl_tensor / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0
     peak = peaks["bf16_sustained"]
+    # launches of the factorisation kernel per step: one per preparation chunk
+    chunks = max(1, int(st["factor_launches"]))
+    roof_sign = {"bound": "tensor" if not fp64_path else "alu", "kernel": "k_ns_tc (sign iteration)",
+                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                 "traffic": kernel_traffic("k_ns_tc", n_mol),
+                 "peak_source": peaks["source"] + " bf16 sustained (kernel timed inside a long step)",
+                 "algorithmic": "tensor flops the products need: (1 or 3 terms) x 2 n^3 per product, "
+                                "2 products per Newton-Schulz step, unpadded n"}
+    if not fp64_path and ms_factor > ms_sign:
+        ach_f = fl_fp32 / (ms_factor / 1e3) / 1e12 if ms_factor > 0 else 0.0
+        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, FP64 refinement)",
+                    "achieved": ach_f, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
+                    "traffic": kernel_traffic("k_prepare_mixed", n_mol / chunks), "launches_per_step": chunks,
+                    "peak_source": "FP32 SIMT peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                    "algorithmic": "FP32 flops 2 (n^3/3 + 2 n^3 + 4 n^2 b) per submatrix"}
+    else:
+        roofline = roof_sign
 
     extra = {"mu": mu_star, "trace_DS": r.trace_DS, "n_occ": n_occ, "bisection_points": evals,
              "ms_phases": {k: statistics.mean(s[k] for s in stats_all)
-                           for k in ("ms_plan", "ms_prepare", "ms_sign", "ms_reduce", "ms_scatter")},
+                           for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_sign", "ms_reduce",
+                                     "ms_scatter")},
              "sign_tflops_paper_convention": fl_paper / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0,
              "sign_tflops_tensor_padded": fl_padded / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0,
              "ns_steps_per_submatrix": st["ns_steps"] / max(1, st["sub_solves"]),
@@ -381,6 +480,10 @@ def main():
                            "_Dc": {}}
             paths[prec]["_D"] = plan.scatter().cpu().numpy()
         plan.close()
+
+    bounds = {}
+    if not args.no_extra and not fp64_path:
+        bounds = bound_sources_leg(nl, synth, spec_name, dsys, mu_star, args.precision, dev)
 
     # oracle: accuracy on a sample at mu* and the CPU baseline
     workers = max(1, os.cpu_count() or 1)
@@ -436,16 +539,15 @@ def main():
         "e2e": {"value": n_mol / (ms_e2e / 1e3), "unit": "submatrices/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
-        "roofline": {"bound": "tensor" if not fp64_path else "alu", "kernel": "k_ns_tc (sign iteration)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "peak_source": peaks["source"] + " bf16 sustained (kernel timed inside a long step)"},
+        "roofline": roofline,
+        "roofline_sign": roof_sign,
         "cpu_baseline": {"value": cpu_subs_per_s, "unit": "submatrices/s", "cores": workers, "kind": "oracle",
                          "sample": f"{len(sample)} submatrices solved once at the final mu, divided by the "
                                    f"{evals} bisection points of a step"},
         "clocks": clk.summary(),
         "extra": extra,
         "paths_one_mu": paths,
+        "bound_sources": bounds,
     }
     print(json.dumps(line), flush=True)
     return 0

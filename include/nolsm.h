@@ -203,6 +203,10 @@ typedef struct {
   int64_t launches;            /* kernels launched for this plan */
   int64_t reruns;              /* submatrices solved again after failing the convergence test under
                                   learned or power-iteration bounds */
+  double ms_gather;            /* a1 alone (part of ms_prepare) */
+  double ms_factor;            /* a2-a3 factorisation and solve kernels alone (part of ms_prepare) */
+  double flops_fp32;           /* FP32 flops of the low-precision paths' factorisation and solves */
+  int64_t factor_launches;     /* preparation chunks (one factorisation kernel launch each) */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);

@@ -39,7 +39,8 @@ class NolsmStats(ctypes.Structure):
     _fields_ = [("ms_plan", c_double), ("ms_prepare", c_double), ("ms_sign", c_double), ("ms_reduce", c_double),
                 ("ms_scatter", c_double), ("solves", c_int64), ("sub_solves", c_int64), ("ns_steps", c_int64),
                 ("flops_paper", c_double), ("flops_tensor", c_double), ("flops_tensor_padded", c_double),
-                ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64)]
+                ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64), ("ms_gather", c_double),
+                ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

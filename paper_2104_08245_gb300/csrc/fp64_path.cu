@@ -401,8 +401,10 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     g.ws = plan->ws_dense.as<double>();
     g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
     const int64_t bands = plan->h_nb_ptr[e] - plan->h_nb_ptr[J];
+    pmark(plan, st);
     k_gather<<<(unsigned)bands, 256, sizeof(int32_t) * 3 * max_nq, st>>>(g);
     NOLSM_LAUNCH_CHECK();
+    pmark(plan, st);
     PrepArgs pa;
     pa.j0 = (int32_t)J;
     pa.sub_n = plan->sub_n.as<int32_t>(); pa.sub_c0 = plan->sub_c0.as<int32_t>(); pa.nbf = plan->sys.nbf;
@@ -427,8 +429,12 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
       NOLSM_TRY(launch_prepare_mixed(pa, (int)(e - J), chunk_max_n, P.A.as<float>(), st));
       plan->stats.launches += 3;
     }
+    pmark(plan, st);
+    plan->stats.factor_launches += 1;
     for (int64_t k = J; k < e; ++k) {
       const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
+      // FP32 flops of the mixed path: Cholesky m^3/3, A = L^-T L^-1 H 2 m^3, Q solves 4 m^2 b (2 FMA each)
+      if (!keep_fp64_A) plan->stats.flops_fp32 += 2.0 * (m * m * m / 3.0 + 2.0 * m * m * m + 4.0 * m * m * b);
       // FP64 flops: the factorisation and Q solves (FP64 path) or one FP64 residual of Q (mixed)
       plan->stats.flops_fp64 += keep_fp64_A ? m * m * m / 3.0 + 2.0 * m * m * b + 2.0 * m * m * m : 2.0 * m * m * b;
       P.done[k] = 1;

@@ -51,6 +51,33 @@ void mark(nolsm_plan* plan, int i, cudaStream_t st) {
   if (plan->ev_ok) cudaEventRecord(plan->ev[i], st);
 }
 
+void pmark(nolsm_plan* plan, cudaStream_t st) {
+  if (!plan->ev_ok) return;
+  if (plan->pev_used == plan->pev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    plan->pev.push_back(e);
+  }
+  cudaEventRecord(plan->pev[plan->pev_used++], st);
+}
+
+void prep_times(nolsm_plan* plan) {
+  for (size_t k = 0; k + 2 < plan->pev_used; k += 3) {
+    float a = 0.0f, b = 0.0f;
+    if (cudaEventElapsedTime(&a, plan->pev[k], plan->pev[k + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, plan->pev[k + 1], plan->pev[k + 2]) == cudaSuccess) {
+      plan->stats.ms_gather += a;
+      plan->stats.ms_factor += b;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  plan->pev_used = 0;
+}
+
 double elapsed(nolsm_plan* plan, int i, int j) {
   if (!plan->ev_ok) return 0.0;
   float ms = 0.0f;
@@ -74,6 +101,7 @@ nolsm_plan::~nolsm_plan() {
   tc_release(this);
   if (ev_ok)
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : pev) cudaEventDestroy(e);
 }
 
 extern "C" {
@@ -255,6 +283,7 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   if (status) NOLSM_CUDA_TRY(cudaMemcpyAsync(status + j0, plan->status.as<int32_t>() + j0, 4 * cnt, cudaMemcpyDeviceToDevice, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   plan->stats.ms_prepare += elapsed(plan, 0, 1);
+  prep_times(plan);
   plan->stats.ms_sign += elapsed(plan, 1, 2);
   plan->stats.ms_reduce += elapsed(plan, 2, 3);
   plan->stats.solves += 1;
@@ -297,6 +326,7 @@ nolsm_status nolsm_spectral_bracket(nolsm_plan* plan, const nolsm_options* opts,
                                  cudaMemcpyDeviceToHost, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   plan->stats.ms_prepare += elapsed(plan, 0, 1);
+  prep_times(plan);
   std::vector<int32_t> pst((size_t)(j1 - j0));
   NOLSM_CUDA_TRY(cudaMemcpy(pst.data(), plan->prep_status.as<int32_t>() + j0, sizeof(int32_t) * pst.size(),
                             cudaMemcpyDeviceToHost));

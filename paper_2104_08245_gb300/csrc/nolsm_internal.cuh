@@ -112,6 +112,8 @@ struct nolsm_plan {
   nolsm_stats stats{};
   cudaEvent_t ev[8] = {};
   bool ev_ok = false;
+  std::vector<cudaEvent_t> pev;     // preparation chunks: before gather, after gather, after factorisation
+  size_t pev_used = 0;
 
   ~nolsm_plan();
 };
@@ -153,6 +155,10 @@ nolsm_status ensure_results(nolsm_plan* plan);
 // synchronised, elapsed(i, j) is the device time between marks i and j in ms (0 if unavailable).
 void mark(nolsm_plan* plan, int i, cudaStream_t st);
 double elapsed(nolsm_plan* plan, int i, int j);
+// The same for the preparation's per-chunk events: pmark records the next one; after a synchronisation
+// prep_times adds the gather and factorisation times to the stats and starts over.
+void pmark(nolsm_plan* plan, cudaStream_t st);
+void prep_times(nolsm_plan* plan);
 
 // shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
 nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
