@@ -295,7 +295,7 @@ nolsm_status nolsm_training_data(nolsm_plan* plan, double mu, const nolsm_option
  * while it runs. It runs the same tensor-core kernel as nolsm_solve_batch (a4-a7: scale, Newton-Schulz
  * sign iteration with the defect test and refinement, centre columns of D and the partial traces) on
  * inputs the caller already holds, using scratch that lives in a static device array inside the
- * library (about 6.3 MB; every GPU that loads the library keeps it until the process exits).
+ * library (about 4.8 MB; every GPU that loads the library keeps it until the process exits).
  *
  * Inputs (device, caller-owned) for submatrix i in [0, count):
  *   sub_n[i] dimension n_i (1..192), nbf[i] number b_i of centre columns,

@@ -2,7 +2,7 @@
 //
 // Newton-Schulz sign iteration (Eq. NS1): X_{k+1} = 1/2 X_k (3I - X_k^2), two products per step:
 //   GEMM0: Y = X X      -> epilogue writes T = 3I - Y and sums the defect ||I - X^2||_F^2
-//   GEMM1: Z = X T      -> epilogue writes X_{k+1} = Z / 2 (FP32 after the last step)
+//   GEMM1: Z = X T      -> epilogue writes X_{k+1} = Z / 2 (the last one feeds the centre columns)
 // Each product is either one tensor-core product of the rounded operands (BF16 or FP16) or the
 // three-term split hi*hi + hi*lo + lo*hi with x = hi + lo (hi = round(x), lo = round(x - hi)),
 // accumulated in FP32 in tensor memory.
@@ -68,7 +68,6 @@ struct TcArgs {
   const int32_t* budget;      // per-submatrix step cap (nullable)
   Fmt main_fmt, refine_fmt;
   uint16_t* planes;           // [slots*6][R][LD]
-  float* xf;                  // [slots][R][LD]
   int32_t R, LD;
   int32_t* next;              // work counter
   int32_t* err;               // global error flag (timeouts)
@@ -134,6 +133,12 @@ __device__ __forceinline__ void split2(float a, float b, int fmt, uint32_t& hi, 
     hi = *reinterpret_cast<const uint32_t*>(&h);
     lo = *reinterpret_cast<const uint32_t*>(&l);
   }
+}
+
+// Element k of a row held as hi (and lo) 2-byte planes.
+__device__ __forceinline__ float xval(const uint16_t* hi, const uint16_t* lo, int k, Fmt f) {
+  const float h = from_bits(hi[k], f.fmt);
+  return f.terms > 1 ? h + from_bits(lo[k], f.fmt) : h;
 }
 
 // 32 consecutive values of one row as packed hi (and lo) pairs.
@@ -229,7 +234,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int zb = (sub0 + pick) * kPlanes;
         d.za = zb + 2 * st.cur;
         d.zb = st.kind == 0 ? d.za : zb + 4;
-        d.zo = st.kind == 0 ? zb + 4 : zb + 2 * (st.cur ^ 1);
+        // X_{k+1} overwrites X_k when one column tile covers the matrix: row block mb of X_k is read
+        // (as the A operand) only by tile (mb, 0), whose loads have completed before its epilogue writes
+        d.zo = st.kind == 0 ? zb + 4 : (st.ncb == 1 ? d.za : zb + 2 * (st.cur ^ 1));
       }
       sh.ring[i % kRing] = d;
       tc::mbar_arrive(&sh.desc_full[i % kRing]);
@@ -371,32 +378,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     // a7 for the finished submatrix of slot s: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the
     // FP64 partial traces
     auto finish_slot = [&](int s) {
+      epi_bar();   // the slot state written by thread 128 and the final X of both groups are visible
       SlotState& st = sh.slot[s];
       const int J = st.job, n = st.n, b = g.nbf[J];
-      const float* xf = g.xf + (size_t)(sub0 + s) * plane_elems;
+      // the final X_k, hi (+ lo) in the last product's output format
+      const uint16_t* xh = g.planes + ((size_t)(sub0 + s) * kPlanes + 2 * st.cur) * plane_elems;
+      const uint16_t* xl = xh + plane_elems;
+      const Fmt xfmt = st.fcur;
       const double* Q = g.Q + g.c_off[J];
       const double* Sc = g.Sc + g.c_off[J];
       const double* Hc = g.Hc + g.c_off[J];
       double* Dc = g.Dc + g.c_off[J];
       float* Qs = reinterpret_cast<float*>(stg);   // staging is idle between products
       const bool staged = (size_t)n * b * sizeof(float) <= 4 * kStgBytes;
-      epi_bar();   // the final X (written by both groups) is visible
       if (staged)
         for (int e = etid; e < n * b; e += 256) Qs[e] = (float)Q[e];
       epi_bar();
       double ps = 0.0, ph = 0.0;
       for (int e = etid; e < n * b; e += 256) {
         const int i = e / b, c = e - i * b;
-        const float* xi = xf + (size_t)i * g.LD;
+        const uint16_t* xhi = xh + (size_t)i * g.LD;
+        const uint16_t* xli = xl + (size_t)i * g.LD;
         // FP32 partial sums of 16 products, combined with Kahan compensation
         float sum = 0.0f, comp = 0.0f;
         for (int k0 = 0; k0 < n; k0 += 16) {
           float p = 0.0f;
           const int k1 = min(n, k0 + 16);
           if (staged) {
-            for (int k = k0; k < k1; ++k) p = fmaf(xi[k], Qs[k * b + c], p);
+            for (int k = k0; k < k1; ++k) p = fmaf(xval(xhi, xli, k, xfmt), Qs[k * b + c], p);
           } else {
-            for (int k = k0; k < k1; ++k) p = fmaf(xi[k], (float)Q[(size_t)k * b + c], p);
+            for (int k = k0; k < k1; ++k) p = fmaf(xval(xhi, xli, k, xfmt), (float)Q[(size_t)k * b + c], p);
           }
           const float y = p - comp;
           const float t = sum + y;
@@ -449,7 +460,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int n = d.n, n64 = d.n64;
       float part = 0.0f;
       bool bad = false;   // a wait of this warp ran out: keep the barrier schedule, skip the work
-      float* xf = g.xf + (size_t)(sub0 + d.slot) * plane_elems;
       for (int mb = 0; mb < d.nrb; ++mb)
         for (int cb = 0; cb < d.ncb; ++cb) {
           const int nt = min(256, n64 - 256 * cb);
@@ -482,13 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
-            if (d.last) {
-              if (live) {
-                float4* dst = reinterpret_cast<float4*>(xf + (size_t)row * g.LD + col0);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-              }
-            } else {
+            {
               // stage the chunk in shared memory (64-byte swizzle: 16-byte unit c of row r sits at
               // unit c ^ ((r >> 1) & 3)) and write it with TMA tensor stores
               uint8_t* shi = stg + grp * 2 * kStgBytes;
@@ -569,9 +573,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           st.status = status;
           st.fnxt = nxt;
           st.kind = 1;
-        } else if (!d.last) {
-          // after X T: swap the ping-pong X and adopt the next format
-          st.cur ^= 1;
+        } else {
+          // after X T: X_{k+1} is the current X (ping-pong unless written in place), in the next format
+          if (d.ncb != 1) st.cur ^= 1;
           st.fcur = st.fnxt;
           st.kind = 0;
         }
@@ -621,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ==================================================================================== host side
 
 struct TcState {
-  DevBuf planes, xf, order, err;
+  DevBuf planes, order, err;
   int R = 0, LD = 0, slots = 0;
   int64_t ord_j0 = -1, ord_j1 = -1;
 };
@@ -635,7 +639,6 @@ void tc_release(nolsm_plan* plan) {
   if (!plan->tc) return;
   TcState* s = static_cast<TcState*>(plan->tc);
   dev_free(plan, s->planes);
-  dev_free(plan, s->xf);
   dev_free(plan, s->order);
   dev_free(plan, s->err);
   delete s;
@@ -679,9 +682,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   if (!S->planes.p || S->R < R || S->LD < LD || S->slots < slots) {
     const int nR = std::max(R, S->R), nLD = std::max(LD, S->LD), nS = std::max(slots, S->slots);
     dev_free(plan, S->planes);
-    dev_free(plan, S->xf);
     NOLSM_TRY(dev_alloc(plan, S->planes, sizeof(uint16_t) * (size_t)kPlanes * nS * nR * nLD));
-    NOLSM_TRY(dev_alloc(plan, S->xf, sizeof(float) * (size_t)nS * nR * nLD));
     S->R = nR;
     S->LD = nLD;
     S->slots = nS;
@@ -730,7 +731,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.max_iter = o.max_iter; g.refine_steps = o.refine_steps;
   g.budget = spec.budget;
   g.main_fmt = mf; g.refine_fmt = rf;
-  g.planes = S->planes.as<uint16_t>(); g.xf = S->xf.as<float>();
+  g.planes = S->planes.as<uint16_t>();
   g.R = S->R; g.LD = S->LD;
   g.next = plan->counter.as<int32_t>();
   g.err = S->err.as<int32_t>();
@@ -759,15 +760,14 @@ constexpr int kNaSlots = 8;                   // scratch sub-slots: 4 CTAs with 
 constexpr int kNaMaxSub = 4096;               // submatrices per call
 constexpr size_t kNaPlaneElems = (size_t)kNaR * kNaLD;
 constexpr size_t kNaPlanesBytes = sizeof(uint16_t) * kPlanes * kNaSlots * kNaPlaneElems;
-constexpr size_t kNaXfBytes = sizeof(float) * kNaSlots * kNaPlaneElems;
 constexpr size_t kNaIntBytes = sizeof(int32_t) * (3 * (size_t)kNaMaxSub + 64);
-constexpr size_t kNaBytes = kNaPlanesBytes + kNaXfBytes + kNaIntBytes;   // about 6.3 MB
+constexpr size_t kNaBytes = kNaPlanesBytes + kNaIntBytes;   // about 4.8 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 // Identity work order, zero factorisation status, zero counters: what the kernel expects to find.
 __global__ void k_noalloc_reset(unsigned char* base, int count) {
-  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes + kNaXfBytes);
+  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
   int32_t* order = ints;
   int32_t* prep = ints + kNaMaxSub;
   int32_t* rst = ints + 2 * kNaMaxSub;
@@ -836,7 +836,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
     g_na_addr[dev] = p;
   }
   unsigned char* base = static_cast<unsigned char*>(g_na_addr[dev]);
-  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes + kNaXfBytes);
+  int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
 
   CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
@@ -859,7 +859,6 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.budget = nullptr;
   g.main_fmt = mf; g.refine_fmt = rf;
   g.planes = reinterpret_cast<uint16_t*>(base);
-  g.xf = reinterpret_cast<float*>(base + kNaPlanesBytes);
   g.R = kNaR; g.LD = kNaLD;
   g.next = ints + 3 * kNaMaxSub;
   g.err = ints + 3 * kNaMaxSub + 32;
