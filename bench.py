@@ -34,6 +34,11 @@ WORKLOADS = {
                     "field, 6 A cutoff (profiling size)"),
     "streamed_bf16": ("spec_streamed_bf16",
                       "water-like lattice, 262144 molecules (64x64x64), 6 functions each, 6 A cutoff"),
+    "split_valence": ("spec_split_valence",
+                      "water-like lattice, 16384 molecules (32x32x16), 23 functions each (split-valence-like), "
+                      "6 A cutoff"),
+    "mixed": ("spec_mixed",
+              "water-like lattice, 65536 molecules (64x32x32), 6 or 23 functions per molecule (50/50), 6 A cutoff"),
 }
 
 
