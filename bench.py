@@ -466,7 +466,7 @@ def main():
     paths = {}
     if not args.no_extra:
         plan = nl.nolsm_build_submatrices(dsys)
-        for prec in ["fp32", "bf16x3", "bf16", "fp64"]:
+        for prec in ["fp32", "bf16x3", "fp16", "bf16", "fp64"]:
             o = nl.options(prec)
             if prec == "fp64":
                 o.sub_begin, o.sub_end = 0, min(n_mol, 2 * 152 * 4)
@@ -535,7 +535,7 @@ def main():
         "metric": "submatrices/s (NOLSM step: plan, mu bisection, write-back) and sign-iteration TFLOP/s",
         "value": value, "unit": "submatrices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "fp16x3", "bf16x3": "bf16x3", "bf16": "bf16"}.get(args.precision,
+        "dtype": {"fp64": "f64", "fp32": "fp16x3", "bf16x3": "bf16x3", "bf16": "bf16", "fp16": "fp16"}.get(args.precision,
                                                                                            args.precision),
         "data": "synthetic",
         "config": {"workload": desc, "precision": args.precision, "molecules": n_mol,

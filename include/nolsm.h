@@ -59,13 +59,18 @@ typedef enum {
  *   NOLSM_BF16X3     three-term split BF16 products throughout (about 16 significant bits), then
  *                    refine_steps steps in the NOLSM_FP32 arithmetic.
  *   NOLSM_FP8E4M3    single E4M3 products with a per-submatrix power-of-two scale (FP32
- *                    accumulation) until tol_ns, then refine_steps steps in NOLSM_FP32 arithmetic. */
+ *                    accumulation) until tol_ns, then refine_steps steps in NOLSM_FP32 arithmetic
+ *                    (not available in this build: NOLSM_ERR_UNSUPPORTED).
+ *   NOLSM_FP16       single FP16 tensor-core products (11 significant bits, FP32 accumulation) until
+ *                    tol_ns, then refine_steps steps in the NOLSM_FP32 arithmetic: the cost of NOLSM_BF16
+ *                    with three more bits per product. */
 typedef enum {
   NOLSM_FP64 = 0,
   NOLSM_FP32 = 1,
   NOLSM_BF16 = 2,
   NOLSM_BF16X3 = 3,
-  NOLSM_FP8E4M3 = 4
+  NOLSM_FP8E4M3 = 4,
+  NOLSM_FP16 = 5
 } nolsm_precision;
 
 /* Source of the spectral scale alpha_J(mu) >= rho(A_J - mu I) applied before the sign iteration. */

@@ -12,7 +12,7 @@ import dataclasses
 from typing import Optional
 
 from . import _abi
-from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP32, FP64,  # noqa: F401
+from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP16, FP32, FP64,  # noqa: F401
                    PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmStats, NolsmSystem)
 
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",

@@ -12,8 +12,8 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_NO_PLATEAU, \
     ERR_UNSUPPORTED, ERR_NO_SOLUTION, ERR_TIMEOUT = range(11)
 # nolsm_precision
-FP64, FP32, BF16, BF16X3, FP8E4M3 = range(5)
-PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8e4m3": FP8E4M3}
+FP64, FP32, BF16, BF16X3, FP8E4M3, FP16 = range(6)
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8e4m3": FP8E4M3, "fp16": FP16}
 # nolsm_bound_source
 BOUND_GERSHGORIN, BOUND_POWER, BOUND_MLP = range(3)
 

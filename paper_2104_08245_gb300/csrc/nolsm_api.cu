@@ -201,7 +201,7 @@ nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_
 
 static nolsm_status check_options(const nolsm_plan* plan, const nolsm_options* o, int64_t* j0, int64_t* j1) {
   if (!o) { set_error("options are NULL"); return NOLSM_ERR_ARG; }
-  if (o->precision < NOLSM_FP64 || o->precision > NOLSM_FP8E4M3 || o->max_iter < 1 || o->max_iter > 10000 ||
+  if (o->precision < NOLSM_FP64 || o->precision > NOLSM_FP16 || o->max_iter < 1 || o->max_iter > 10000 ||
       o->refine_steps < 0 || o->refine_steps > 100 || !(o->tol_ns > 0) || !(o->tol_accept > 0) ||
       o->bound_source < 0 || o->bound_source > NOLSM_BOUND_MLP) {
     set_error("invalid options (precision %d, max_iter %d, refine %d, tol_ns %g, tol_accept %g, bound %d)",

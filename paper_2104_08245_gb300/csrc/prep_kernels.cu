@@ -360,144 +360,148 @@ __device__ void solve_A(const LT* __restrict__ S, const double* __restrict__ H, 
   }
 }
 
-// FP32 form for the mixed preparation, as an outer product. Columns c < n are the columns of T_J(H0)
-// (result into X, n x n); columns n <= c < n + b are the centre columns of the identity (result into W,
-// n x b), the first solve of Q. For each 32-row block the whole block row of L needed by the step is
-// staged once, transposed (LT[t][i], so that every t broadcasts one right-hand-side value to 32
-// independent accumulators via 16-byte shared loads), together with X_r (XfT). Shared memory: sm holds
-// (n + 32) x (NB + 4) floats.
-__device__ void solve_A32(const float* __restrict__ L, const double* __restrict__ H, int n, int c0, int b,
-                          float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm) {
-  constexpr int LDA = Ld<float>::v;
+// Register-tiled form of the same solves for the mixed preparation. Right-hand sides: columns c < n of
+// T_J(H0) (result into X, n x n) and, when bq > 0, the centre columns of the identity (result into W,
+// n x bq). Columns go in batches of 64; thread (tr, tc) = (tid / 16, tid % 16) owns rows 4tr..4tr+3 of the
+// current 32-row block and columns 4tc..4tc+3 of the batch, so every step of the inner loop is two
+// 16-byte shared loads and 16 FMAs. Chunks of 32 columns of L and 32 rows of the solution are staged
+// through registers, the next chunk's global loads in flight while the current one is used.
+// Shared memory: sm holds kRtSmem floats.
+constexpr int kRtLd = NB + 4;                  // LT, XT rows (16-byte aligned)
+constexpr int kRtCb = 64;                      // columns per batch
+constexpr int kRtYd = kRtCb + 4;               // YC / AC rows
+constexpr int kRtSmem = 2 * NB * kRtLd + NB * kRtYd;
+
+__device__ __forceinline__ float rt_rhs(const double* __restrict__ H, int n, int c0, int row, int col) {
+  return col < n ? (float)H[(size_t)row * n + col] : (row == c0 + col - n ? 1.0f : 0.0f);
+}
+
+__device__ void solve_A_rt(const float* __restrict__ L, const double* __restrict__ H, int n, int c0, int bq,
+                           float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm) {
   const int tid = threadIdx.x;
+  const int tr = tid >> 4, tc = tid & 15;
   const int nblk = (n + NB - 1) / NB;
-  const int ncol = n + b;
-  for (int cb = 0; cb < ncol; cb += kThreads) {
-    const int c = cb + tid;
-    const bool act = c < ncol;
-    const bool qcol = c >= n;
-    float* dst = qcol ? W + (c - n) : X + c;   // this thread's column of the result
-    const int ld = qcol ? b : n;
-    // forward: Y = L^-1 RHS
-    for (int rbk = 0; rbk < nblk; ++rbk) {
-      const int r0 = rbk * NB, rb = min(NB, n - r0);
-      float acc[NB];
+  const int ncol = n + bq;
+  float* LT = sm;                       // [32][kRtLd]
+  float* XT = sm + NB * kRtLd;          // [32][kRtLd]
+  float* YC = sm + 2 * NB * kRtLd;      // [32][kRtYd], also the accumulator exchange
+  // element (row, col) of the result / right-hand-side array of global column col
+  auto addr = [&](int row, int col) -> float* {
+    return col < n ? X + (size_t)row * n + col : W + (size_t)row * bq + (col - n);
+  };
+  for (int cb = 0; cb < ncol; cb += kRtCb) {
+    for (int pass = 0; pass < 2; ++pass) {   // 0: forward Y = L^-1 B; 1: backward L^-T Y
+      for (int s = 0; s < nblk; ++s) {
+        const int rbk = pass == 0 ? s : nblk - 1 - s;
+        const int r0 = rbk * NB, rb = min(NB, n - r0);
+        float acc[4][4];
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        float v = 0.0f;
-        if (act && i < rb) v = qcol ? (r0 + i == c0 + c - n ? 1.0f : 0.0f) : (float)H[(size_t)(r0 + i) * n + c];
-        acc[i] = v;
-      }
-      float* LT = sm;                   // [r0][LDA]: LT[t][i] = L[r0+i][t]
-      float* XfT = sm + r0 * LDA;       // [NB][LDA]: XfT[t][a] = X_r[a][t]
-      for (int e = tid; e < r0 * NB; e += kThreads) {
-        const int i = e / r0, t = e - i * r0;
-        LT[t * LDA + i] = i < rb ? L[(size_t)(r0 + i) * n + t] : 0.0f;
-      }
-      for (int e = tid; e < NB * NB; e += kThreads) {
-        const int a = e >> 5, t = e & 31;
-        XfT[t * LDA + a] = (a < rb && t < rb) ? xinv32(L, n, r0, a, t) : 0.0f;
-      }
-      __syncthreads();
-      if (act) {
-        for (int q0 = 0; q0 < r0; q0 += NB) {
-          float y[NB];
+        for (int a = 0; a < 4; ++a) {
+          const int row = r0 + 4 * tr + a;
 #pragma unroll
-          for (int t = 0; t < NB; ++t) y[t] = dst[(size_t)(q0 + t) * ld];
+          for (int c = 0; c < 4; ++c) {
+            const int col = cb + 4 * tc + c;
+            float v = 0.0f;
+            if (row < n && col < ncol) v = pass == 0 ? rt_rhs(H, n, c0, row, col) : *addr(row, col);
+            acc[a][c] = v;
+          }
+        }
+        // chunks of the coupling: forward q0 in [0, r0), backward q0 in [r0 + rb, n)
+        const int q_begin = pass == 0 ? 0 : r0 + rb;
+        const int q_end = pass == 0 ? r0 : n;
+        float lreg[8], yreg[16];
+        auto load_chunk = [&](int q0) {
 #pragma unroll
-          for (int t = 0; t < NB; ++t) {
-            const float yt = y[t];
-            const float* lrow = LT + (q0 + t) * LDA;
-#pragma unroll
-            for (int i = 0; i < NB; i += 4) {
-              const float4 l = *reinterpret_cast<const float4*>(lrow + i);
-              acc[i] = fmaf(-l.x, yt, acc[i]);
-              acc[i + 1] = fmaf(-l.y, yt, acc[i + 1]);
-              acc[i + 2] = fmaf(-l.z, yt, acc[i + 2]);
-              acc[i + 3] = fmaf(-l.w, yt, acc[i + 3]);
+          for (int u = 0; u < 8; ++u) {
+            const int e = tid + 128 * u;
+            if (pass == 0) {   // LT[t][i] = L[r0+i][q0+t]
+              const int i = e >> 5, t = e & 31;
+              lreg[u] = (i < rb && q0 + t < q_end) ? L[(size_t)(r0 + i) * n + q0 + t] : 0.0f;
+            } else {           // LT[t][i] = L[q0+t][r0+i]
+              const int t = e >> 5, i = e & 31;
+              lreg[u] = (i < rb && q0 + t < q_end) ? L[(size_t)(q0 + t) * n + r0 + i] : 0.0f;
             }
           }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {   // YC[k][j] = result[q0+k][cb+j]
+            const int e = tid + 128 * u;
+            const int k = e >> 6, j = e & 63;
+            const int row = q0 + k, col = cb + j;
+            yreg[u] = (row < q_end && col < ncol) ? *addr(row, col) : 0.0f;
+          }
+        };
+        auto store_chunk = [&]() {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = tid + 128 * u;
+            if (pass == 0) LT[(e & 31) * kRtLd + (e >> 5)] = lreg[u];
+            else LT[(e >> 5) * kRtLd + (e & 31)] = lreg[u];
+          }
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int e = tid + 128 * u;
+            YC[(e >> 6) * kRtYd + (e & 63)] = yreg[u];
+          }
+        };
+        if (q_begin < q_end) load_chunk(q_begin);
+        for (int q0 = q_begin; q0 < q_end; q0 += NB) {
+          store_chunk();
+          __syncthreads();
+          if (q0 + NB < q_end) load_chunk(q0 + NB);   // in flight during the FMAs below
+#pragma unroll 8
+          for (int k = 0; k < NB; ++k) {
+            const float4 l4 = *reinterpret_cast<const float4*>(LT + k * kRtLd + 4 * tr);
+            const float4 y4 = *reinterpret_cast<const float4*>(YC + k * kRtYd + 4 * tc);
+            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(-lv[a], yv[c], acc[a][c]);
+          }
+          __syncthreads();
         }
-        float o[NB];
+        // the diagonal block: forward y = X_r acc (XT[t][a] = X_r[a][t]); backward x = X_r^T acc
+        // (XT[t][a] = X_r[t][a]); the accumulators of the block go through YC
 #pragma unroll
-        for (int a = 0; a < NB; ++a) o[a] = 0.0f;
+        for (int u = 0; u < 8; ++u) {
+          const int e = tid + 128 * u;
+          const int p = e >> 5, q = e & 31;   // coalesced along q
+          if (pass == 0) XT[q * kRtLd + p] = (p < rb && q < rb) ? xinv32(L, n, r0, p, q) : 0.0f;
+          else XT[p * kRtLd + q] = (p < rb && q < rb) ? xinv32(L, n, r0, p, q) : 0.0f;
+        }
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {   // y = X_r acc (XfT[t][a] zero for a < t)
-          const float at = acc[t];
+        for (int a = 0; a < 4; ++a)
+          *reinterpret_cast<float4*>(YC + (4 * tr + a) * kRtYd + 4 * tc) =
+              make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        __syncthreads();
+        float o[4][4];
 #pragma unroll
-          for (int a = t & ~3; a < NB; a += 4) {
-            const float4 x4 = *reinterpret_cast<const float4*>(XfT + t * LDA + a);
-            o[a] = fmaf(x4.x, at, o[a]);
-            o[a + 1] = fmaf(x4.y, at, o[a + 1]);
-            o[a + 2] = fmaf(x4.z, at, o[a + 2]);
-            o[a + 3] = fmaf(x4.w, at, o[a + 3]);
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) o[a][c] = 0.0f;
+#pragma unroll 8
+        for (int t = 0; t < NB; ++t) {
+          const float4 x4 = *reinterpret_cast<const float4*>(XT + t * kRtLd + 4 * tr);
+          const float4 y4 = *reinterpret_cast<const float4*>(YC + t * kRtYd + 4 * tc);
+          const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+          const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) o[a][c] = fmaf(xv[a], yv[c], o[a][c]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int row = r0 + 4 * tr + a;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int col = cb + 4 * tc + c;
+            if (4 * tr + a < rb && col < ncol) *addr(row, col) = o[a][c];
           }
         }
-#pragma unroll
-        for (int a = 0; a < NB; ++a)
-          if (a < rb) dst[(size_t)(r0 + a) * ld] = o[a];
+        __syncthreads();
       }
-      __syncthreads();
-    }
-    // backward: result = L^-T Y
-    for (int rbk = nblk - 1; rbk >= 0; --rbk) {
-      const int r0 = rbk * NB, rb = min(NB, n - r0);
-      const int q0 = r0 + rb, m = n - q0;   // rows below the block
-      float acc[NB];
-#pragma unroll
-      for (int i = 0; i < NB; ++i) acc[i] = (act && i < rb) ? dst[(size_t)(r0 + i) * ld] : 0.0f;
-      float* LT = sm;                   // [m][LDA]: LT[t][i] = L[q0+t][r0+i]
-      float* XfT = sm + ((m + 3) & ~3) * LDA;   // [NB][LDA]: XfT[t][a] = X_r[t][a]
-      for (int e = tid; e < m * NB; e += kThreads) {
-        const int t = e >> 5, i = e & 31;
-        LT[t * LDA + i] = i < rb ? L[(size_t)(q0 + t) * n + r0 + i] : 0.0f;
-      }
-      for (int e = tid; e < NB * NB; e += kThreads) {
-        const int t = e >> 5, a = e & 31;
-        XfT[t * LDA + a] = (a < rb && t < rb) ? xinv32(L, n, r0, t, a) : 0.0f;
-      }
-      __syncthreads();
-      if (act) {
-        for (int t0 = 0; t0 < m; t0 += NB) {
-          float x[NB];
-#pragma unroll
-          for (int t = 0; t < NB; ++t) x[t] = t0 + t < m ? dst[(size_t)(q0 + t0 + t) * ld] : 0.0f;
-#pragma unroll
-          for (int t = 0; t < NB; ++t) {
-            if (t0 + t < m) {
-              const float xt = x[t];
-              const float* lrow = LT + (t0 + t) * LDA;
-#pragma unroll
-              for (int i = 0; i < NB; i += 4) {
-                const float4 l = *reinterpret_cast<const float4*>(lrow + i);
-                acc[i] = fmaf(-l.x, xt, acc[i]);
-                acc[i + 1] = fmaf(-l.y, xt, acc[i + 1]);
-                acc[i + 2] = fmaf(-l.z, xt, acc[i + 2]);
-                acc[i + 3] = fmaf(-l.w, xt, acc[i + 3]);
-              }
-            }
-          }
-        }
-        float o[NB];
-#pragma unroll
-        for (int a = 0; a < NB; ++a) o[a] = 0.0f;
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {   // x = X_r^T acc (XfT[t][a] zero for a > t)
-          const float at = acc[t];
-#pragma unroll
-          for (int a = 0; a <= (t | 3); a += 4) {
-            const float4 x4 = *reinterpret_cast<const float4*>(XfT + t * LDA + a);
-            o[a] = fmaf(x4.x, at, o[a]);
-            o[a + 1] = fmaf(x4.y, at, o[a + 1]);
-            o[a + 2] = fmaf(x4.z, at, o[a + 2]);
-            o[a + 3] = fmaf(x4.w, at, o[a + 3]);
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < NB; ++a)
-          if (a < rb) dst[(size_t)(r0 + a) * ld] = o[a];
-      }
-      __syncthreads();
     }
   }
 }
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
     double* r = g.R64 + (g.c_off[J] - g.c_base);
     double* q = g.Q + g.c_off[J];
     const bool merge_q = (n + bJ + kThreads - 1) / kThreads == (n + kThreads - 1) / kThreads;
-    solve_A32(L, H, n, c0, merge_q ? bJ : 0, A, w, Pf);
+    solve_A_rt(L, H, n, c0, merge_q ? bJ : 0, A, w, Pf);
     if (!merge_q) {
       for (int e = tid; e < nbc; e += kThreads) {
         const int i = e / bJ, c = e - i * bJ;
@@ -790,7 +794,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
 }
 
 size_t smem_fp64(int max_n) { return sizeof(double) * (size_t)std::max(max_n, 2 * NB) * (NB + 1); }
-size_t smem_mixed(int max_n) { return sizeof(float) * (size_t)(std::max(max_n, 2 * NB) + 36) * Ld<float>::v; }
+size_t smem_mixed(int max_n) {
+  return sizeof(float) * std::max((size_t)(std::max(max_n, 2 * NB) + 36) * Ld<float>::v, (size_t)kRtSmem);
+}
 constexpr size_t kSmemLimit = 200 * 1024;
 
 }  // namespace

@@ -655,6 +655,7 @@ static bool formats(int precision, Fmt* main_fmt, Fmt* refine_fmt) {
     case NOLSM_FP32: *main_fmt = Fmt{FMT_F16, 3}; return true;
     case NOLSM_BF16X3: *main_fmt = Fmt{FMT_BF16, 3}; return true;
     case NOLSM_BF16: *main_fmt = Fmt{FMT_BF16, 1}; return true;
+    case NOLSM_FP16: *main_fmt = Fmt{FMT_F16, 1}; return true;
     default: return false;
   }
 }
