@@ -200,6 +200,165 @@ __device__ bool cholesky(T* __restrict__ S, int n, T* __restrict__ Ps, T (*Xs)[N
   return true;
 }
 
+// FP32 form for the mixed preparation with four block-wide barriers per 32-column panel instead of two
+// per column: warp 0 factors the panel's 32 x 32 diagonal block in registers (lane i holds row i, the
+// pivot column travels by shuffles) and inverts it (X_r = L_11^-1, row by row, each finished row
+// broadcast); then every thread forms rows of L_21 = A_21 X_r^T; the trailing update is the tiled one above.
+// Xs is [NB][NB + 4] (16-byte rows). Same results up to rounding order as cholesky<float>.
+__device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps, float (*Xs)[NB + 4],
+                           int* s_bad) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int LDP = Ld<float>::v;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = min(NB, n - k0), mt = n - k0;
+    // panel rows by warp, lanes along the row, zero beyond kb
+#pragma unroll 4
+    for (int i = warp; i < mt; i += kThreads / 32)
+      Ps[i * LDP + lane] = lane < kb ? S[(size_t)(k0 + i) * n + k0 + lane] : 0.0f;
+    __syncthreads();
+    if (warp == 0) {
+      // factor the diagonal block in the panel itself: lane i owns row i (rows beyond kb idle)
+      const bool live = lane < kb;
+      bool bad = false;
+      float myr = 1.0f;   // 1 / L_ii of this lane's row
+      for (int j = 0; j < kb; ++j) {
+        const float piv = Ps[j * LDP + j];
+        bad = bad || !(piv > 0.0f) || !isfinite(piv);
+        const float d = fmaxf(piv, 1e-30f);
+        float r = rsqrtf(d);
+        r = r * fmaf(-0.5f * d * r, r, 1.5f);
+        __syncwarp();
+        if (lane == j) {
+          Ps[j * LDP + j] = d * r;
+          myr = r;
+        }
+        if (live && lane > j) Ps[lane * LDP + j] *= r;
+        __syncwarp();
+        if (live && lane > j) {
+          const float lij = Ps[lane * LDP + j];
+          for (int k = j + 1; k <= lane; ++k) Ps[lane * LDP + k] = fmaf(-lij, Ps[k * LDP + j], Ps[lane * LDP + k]);
+        }
+        __syncwarp();
+      }
+      // X_r = L_11^-1: rows in order; lane i accumulates -sum_{k<i} L_ik X[k][j], then scales by 1/L_ii
+      float x[NB];
+#pragma unroll
+      for (int k = 0; k < NB; ++k) x[k] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (lane == i) {
+#pragma unroll
+          for (int j = 0; j <= i; ++j) x[j] = ((j == i) ? 1.0f + x[j] : x[j]) * myr;
+        }
+        const float lli = (live && lane > i) ? Ps[lane * LDP + i] : 0.0f;   // L[lane][i]
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          const float xij = __shfl_sync(0xffffffffu, x[j], i);
+          if (lane > i) x[j] = fmaf(-lli, xij, x[j]);
+        }
+      }
+      // Xs holds X_r transposed: Xs[k][i] = X_r[i][k] (zero above the diagonal of X_r)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) Xs[k][lane] = (live && k <= lane) ? x[k] : 0.0f;
+      if (__any_sync(0xffffffffu, bad && lane < kb)) {
+        if (lane == 0) *s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (*s_bad) return false;
+    // L_21 = A_21 X_r^T: row i of the panel below the diagonal block, one thread per row, eight outputs
+    // at a time: out[j] = sum_{t <= j} A_21[i][t] X_r[j][t], X_r^T rows read as 16-byte vectors
+    for (int i = kb + tid; i < mt; i += kThreads) {
+      asm volatile("" ::: "memory");   // keeps the X_r loads in the loop (hoisting them all would spill)
+      float* pi = Ps + i * LDP;
+      float out[4][8];
+#pragma unroll
+      for (int jb = 0; jb < 4; ++jb) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) out[jb][q] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 8 * jb + 8; ++t) {
+          const float rt = pi[t];
+          const float4 x0 = *reinterpret_cast<const float4*>(&Xs[t][8 * jb]);
+          const float4 x1 = *reinterpret_cast<const float4*>(&Xs[t][8 * jb + 4]);
+          out[jb][0] = fmaf(rt, x0.x, out[jb][0]);
+          out[jb][1] = fmaf(rt, x0.y, out[jb][1]);
+          out[jb][2] = fmaf(rt, x0.z, out[jb][2]);
+          out[jb][3] = fmaf(rt, x0.w, out[jb][3]);
+          out[jb][4] = fmaf(rt, x1.x, out[jb][4]);
+          out[jb][5] = fmaf(rt, x1.y, out[jb][5]);
+          out[jb][6] = fmaf(rt, x1.z, out[jb][6]);
+          out[jb][7] = fmaf(rt, x1.w, out[jb][7]);
+        }
+      }
+#pragma unroll
+      for (int jb = 0; jb < 4; ++jb) {
+        *reinterpret_cast<float4*>(pi + 8 * jb) = make_float4(out[jb][0], out[jb][1], out[jb][2], out[jb][3]);
+        *reinterpret_cast<float4*>(pi + 8 * jb + 4) = make_float4(out[jb][4], out[jb][5], out[jb][6], out[jb][7]);
+      }
+    }
+    __syncthreads();
+    // write back L (panel), X_r^T in the upper and X_r in the lower triangle of the diagonal block
+    if (lane < kb) {
+#pragma unroll 4
+      for (int i = warp; i < mt; i += kThreads / 32) {
+        float v;
+        if (i >= kb) v = Ps[i * LDP + lane];
+        else if (lane > i) v = Xs[i][lane];   // X_r^T[i][lane] = X_r[lane][i]
+        else v = Xs[lane][i];                 // X_r[i][lane]
+        S[(size_t)(k0 + i) * n + k0 + lane] = v;
+      }
+    }
+    // trailing update of the lower triangle, 32 x 32 tiles, 4 x 2 outputs per thread
+    const int r0 = kb, m = mt - kb;
+    if (m > 0) {
+      const int TT = (m + 31) / 32;
+      const int tx = tid & 15, ty = tid >> 4;
+      for (int tile = 0; tile < TT * (TT + 1) / 2; ++tile) {
+        int ti = 0;
+        while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+        const int tj = tile - ti * (ti + 1) / 2;
+        const int bi = r0 + 32 * ti, bj = r0 + 32 * tj;
+        float acc[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0f;
+        int ii[4], jj[2];
+        bool vi[4], vj[2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { ii[a] = bi + ty + 8 * a; vi[a] = ii[a] < mt; }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) { jj[b] = bj + tx + 16 * b; vj[b] = jj[b] < mt; }
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = 0; t < kb; t += 4) {
+          float4 av[4], bv[2];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = vi[a] ? *reinterpret_cast<const float4*>(&Ps[ii[a] * LDP + t]) : z4;
+#pragma unroll
+          for (int b = 0; b < 2; ++b) bv[b] = vj[b] ? *reinterpret_cast<const float4*>(&Ps[jj[b] * LDP + t]) : z4;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+              float s2 = acc[a][b];
+              s2 = fmaf(av[a].x, bv[b].x, s2);
+              s2 = fmaf(av[a].y, bv[b].y, s2);
+              s2 = fmaf(av[a].z, bv[b].z, s2);
+              s2 = fmaf(av[a].w, bv[b].w, s2);
+              acc[a][b] = s2;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            if (vi[a] && vj[b] && jj[b] <= ii[a]) S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]] -= acc[a][b];
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------------------------ A = L^-T L^-1 H
 // s - sum_t row[t] y[t] over one 32-wide block (row in shared memory; FP32 rows are 16-byte aligned)
 template <typename T>
@@ -560,7 +719,7 @@ __device__ void solve_Q(const double* __restrict__ S, int n, int c0, int b, doub
 // ------------------------------------------------------------------------------------ mixed-precision Q
 // W <- L^-T L^-1 W for the b columns of W (n x b row-major, FP32), with the FP32 factor.
 __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
-                             float (*Acc)[kMaxB + 1], float (*Xd)[NB + 1]) {
+                             float (*Acc)[kMaxB + 1], float (*Xd)[NB + 4]) {
   const int tid = threadIdx.x;
   const int nblk = (n + NB - 1) / NB;
   for (int rbk = 0; rbk < nblk; ++rbk) {   // forward
@@ -704,8 +863,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_prepare(PrepArgs g, TA* __restr
 
 __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float* __restrict__ Acache) {
   extern __shared__ __align__(16) float Pf[];   // panel (n x (NB+4)), then solve tiles ((n+36) x (NB+4))
-  __shared__ float Xs[NB][NB + 1];
-  __shared__ float s_rinv[2];
+  __shared__ __align__(16) float Xs[NB][NB + 4];
   __shared__ int s_bad;
   __shared__ float rlo[kThreads], rhi[kThreads];
   __shared__ float red_d[kThreads / 32];
@@ -725,7 +883,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
     if (j <= i) L[e] = (float)S[e];
   }
   __syncthreads();
-  bool ok = cholesky<float>(L, n, Pf, Xs, s_rinv, &s_bad);
+  __syncthreads();
+  bool ok = cholesky32(L, n, Pf, Xs, &s_bad);
   if (ok) {
     // A_J = L^-T L^-1 T_J(H0) in FP32, and the FP32 first solve of Q when its b columns fit in the
     // last column batch
