@@ -112,6 +112,10 @@ typedef struct {
   int32_t bound_source;  /* nolsm_bound_source */
   int64_t sub_begin;     /* solve only submatrices [sub_begin, sub_end) (streaming); */
   int64_t sub_end;       /* sub_end <= 0 means n_mol */
+  int32_t symmetric_form;/* tensor-core modes: iterate on M = L^-1 T_J(H0) L^-T (T_J(S) = L L^T), which has
+                            the spectrum of A_J and symmetric iterates, and finish with T_J(D) =
+                            L^-T 1/2 (I - sign(M - mu I)) L^-1 (Eq. purification_submatrix); always used by
+                            NOLSM_FP8E4M3 (every operand is then loaded in the K-major layout) */
 } nolsm_options;
 
 /* Defaults for a precision: FP64 tol_ns 1e-9, tol_accept 1e-7, max_iter 100; low-precision modes

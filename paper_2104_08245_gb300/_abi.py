@@ -27,7 +27,8 @@ class NolsmSystem(ctypes.Structure):
 class NolsmOptions(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_steps", c_int32), ("max_iter", c_int32),
                 ("tol_ns", c_double), ("tol_accept", c_double), ("tol_n", c_double), ("tol_mu", c_double),
-                ("max_bisect", c_int32), ("bound_source", c_int32), ("sub_begin", c_int64), ("sub_end", c_int64)]
+                ("max_bisect", c_int32), ("bound_source", c_int32), ("sub_begin", c_int64), ("sub_end", c_int64),
+                ("symmetric_form", c_int32)]
 
 
 class NolsmPlanInfo(ctypes.Structure):

@@ -611,13 +611,13 @@ nolsm_status ensure_buf(nolsm_plan* plan, DevBuf& b, size_t bytes) {
 
 }  // namespace
 
-nolsm_status power_bounds(nolsm_plan* plan, bool fp64_A, int64_t j0, int64_t j1, const int32_t* list, int32_t count,
+nolsm_status power_bounds(nolsm_plan* plan, int cls, int64_t j0, int64_t j1, const int32_t* list, int32_t count,
                           cudaStream_t st) {
   const size_t n = (size_t)plan->n_mol;
   NOLSM_TRY(ensure_buf(plan, plan->lam_p, sizeof(double) * 2 * n));
-  if (plan->pow_done.size() != n || plan->pow_fp64 != fp64_A) {
+  if (plan->pow_done.size() != n || plan->pow_cls != cls) {
     plan->pow_done.assign(n, 0);
-    plan->pow_fp64 = fp64_A;
+    plan->pow_cls = cls;
   }
   int64_t a = j0, b = j1;
   if (!list) {   // skip what is cached
@@ -635,12 +635,12 @@ nolsm_status power_bounds(nolsm_plan* plan, bool fp64_A, int64_t j0, int64_t j1,
   const int blocks = list ? count : (int)(b - a);
   if (blocks <= 0) return NOLSM_OK;
   const size_t smem = sizeof(float) * 4 * (size_t)std::max(plan->max_n, 1);
-  if (fp64_A) {
+  if (cls == kPrepFP64) {
     NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_power_bounds<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_power_bounds<double><<<blocks, kPowThreads, smem, st>>>(g, plan->prep64.A.as<double>());
   } else {
     NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_power_bounds<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_power_bounds<float><<<blocks, kPowThreads, smem, st>>>(g, plan->prep32.A.as<float>());
+    k_power_bounds<float><<<blocks, kPowThreads, smem, st>>>(g, prepared(plan, cls).A.as<float>());
   }
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;

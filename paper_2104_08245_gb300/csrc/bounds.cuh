@@ -30,8 +30,8 @@ struct FeatArgs {
   float* feat;                // [n_mol][kFeatures]
 };
 
-// Power-iteration bounds for [j0, j1) (list == nullptr) or for list[0, count); A in FP32 or FP64.
-nolsm_status power_bounds(nolsm_plan* plan, bool fp64_A, int64_t j0, int64_t j1, const int32_t* list, int32_t count,
+// Power-iteration bounds for [j0, j1) (list == nullptr) or for list[0, count) on the A of a preparation class.
+nolsm_status power_bounds(nolsm_plan* plan, int cls, int64_t j0, int64_t j1, const int32_t* list, int32_t count,
                           cudaStream_t st);
 // Features of [j0, j1) at mu into plan->feat.
 nolsm_status features(nolsm_plan* plan, double mu, int64_t j0, int64_t j1, cudaStream_t st);

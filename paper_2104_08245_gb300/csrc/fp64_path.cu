@@ -354,8 +354,10 @@ static nolsm_status ensure(nolsm_plan* plan, DevBuf& b, size_t bytes) {
   return dev_alloc(plan, b, bytes);
 }
 
-nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp64_A, cudaStream_t st) {
-  Prepared& P = keep_fp64_A ? plan->prep64 : plan->prep32;
+nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStream_t st) {
+  const bool keep_fp64_A = cls == kPrepFP64;
+  const bool sym = cls == kPrepSym;
+  Prepared& P = prepared(plan, cls);
   const int32_t n_mol = plan->n_mol;
   const size_t esz = keep_fp64_A ? sizeof(double) : sizeof(float);
   if (!P.A.p) {
@@ -371,6 +373,10 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     NOLSM_TRY(dev_alloc(plan, plan->lam, sizeof(double) * 2 * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->prep_status, sizeof(int32_t) * n_mol));
     NOLSM_CUDA_TRY(cudaMemsetAsync(plan->prep_status.p, 0, sizeof(int32_t) * n_mol, st));
+  }
+  if (sym && !plan->Lsym.p) {
+    NOLSM_TRY(dev_alloc(plan, plan->Lsym, sizeof(float) * (size_t)std::max<int64_t>(plan->h_a_off[n_mol], 1)));
+    NOLSM_TRY(dev_alloc(plan, plan->Wc, sizeof(double) * nc));
   }
   int max_nq = 1;
   for (int64_t J = j0; J < j1; ++J) max_nq = std::max(max_nq, plan->h_nb_ptr[J + 1] - plan->h_nb_ptr[J]);
@@ -419,13 +425,21 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     } else {
       // FP32 factor, A in FP32, Q refined to FP64 accuracy; the FP64 factorisation only where flagged
       const int64_t nbc = plan->h_c_off[e] - plan->h_c_off[J];
-      NOLSM_TRY(ensure(plan, plan->ws_l32, sizeof(float) * (size_t)n2));
       NOLSM_TRY(ensure(plan, plan->ws_refine, (sizeof(double) + sizeof(float)) * (size_t)std::max<int64_t>(nbc, 1)));
-      pa.L32 = plan->ws_l32.as<float>();
+      if (sym) {   // the factors stay for the finishing step D_c = L^-T U
+        NOLSM_TRY(ensure(plan, plan->ws_ysym, sizeof(float) * (size_t)n2));
+        pa.L32 = plan->Lsym.as<float>() + plan->h_a_off[J];
+        pa.sym = 1;
+        pa.Ysym = plan->ws_ysym.as<float>();
+        pa.Wc = plan->Wc.as<double>();
+      } else {
+        NOLSM_TRY(ensure(plan, plan->ws_l32, sizeof(float) * (size_t)n2));
+        pa.L32 = plan->ws_l32.as<float>();
+      }
       pa.c_base = plan->h_c_off[J];
       pa.R64 = plan->ws_refine.as<double>();
       pa.W32 = reinterpret_cast<float*>(pa.R64 + std::max<int64_t>(nbc, 1));
-      pa.fallback_max_n = prepare_fp64_max_n();
+      pa.fallback_max_n = sym ? 0 : prepare_fp64_max_n();   // no FP64 fallback for the symmetric form
       NOLSM_TRY(launch_prepare_mixed(pa, (int)(e - J), chunk_max_n, P.A.as<float>(), st));
       plan->stats.launches += 3;
     }
@@ -433,10 +447,17 @@ nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp
     plan->stats.factor_launches += 1;
     for (int64_t k = J; k < e; ++k) {
       const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
-      // FP32 flops of the mixed path: Cholesky m^3/3, A = L^-T L^-1 H 2 m^3, Q solves 4 m^2 b (2 FMA each)
-      if (!keep_fp64_A) plan->stats.flops_fp32 += 2.0 * (m * m * m / 3.0 + 2.0 * m * m * m + 4.0 * m * m * b);
-      // FP64 flops: the factorisation and Q solves (FP64 path) or one FP64 residual of Q (mixed)
-      plan->stats.flops_fp64 += keep_fp64_A ? m * m * m / 3.0 + 2.0 * m * m * b + 2.0 * m * m * m : 2.0 * m * m * b;
+      // algorithmic flops (2 per FMA): Cholesky m^3/3 FMAs; two triangular solves with m right-hand sides
+      // m^3 FMAs (A = L^-T L^-1 H, or M = L^-1 (L^-1 H)^T); the Q solves m^2 b FMAs each (FP64 path: one;
+      // mixed: the first solve and one correction, plus m^2 b / 2 for W_c in the symmetric form); the FP64
+      // residual of the refinement m^2 b FMAs
+      const double fma_fact = m * m * m / 3.0 + m * m * m;
+      if (keep_fp64_A) {
+        plan->stats.flops_fp64 += 2.0 * (fma_fact + m * m * b);
+      } else {
+        plan->stats.flops_fp32 += 2.0 * (fma_fact + (sym ? 2.5 : 2.0) * m * m * b);
+        plan->stats.flops_fp64 += 2.0 * m * m * b;
+      }
       P.done[k] = 1;
     }
     J = e;

@@ -94,9 +94,9 @@ using namespace nolsm;
 
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
-                   &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &Dc,
+                   &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &Lsym, &Wc, &Dc,
                    &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &ws_ns,
-                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun};
+                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
   if (ev_ok)
@@ -219,12 +219,12 @@ static nolsm_status check_options(const nolsm_plan* plan, const nolsm_options* o
 
 // Scale source of one solve: the Gershgorin interval, the power-iteration interval (cached per plan) or
 // the learned interval and step budget (features at mu, then the plan's network).
-static nolsm_status bound_spec(nolsm_plan* plan, int source, double mu, const nolsm_options& o, bool fp64, int64_t j0,
+static nolsm_status bound_spec(nolsm_plan* plan, int source, double mu, const nolsm_options& o, int cls, int64_t j0,
                                int64_t j1, cudaStream_t st, SolveSpec* spec) {
   *spec = SolveSpec{};
   spec->lam = plan->lam.as<double>();
   if (source == NOLSM_BOUND_POWER) {
-    NOLSM_TRY(power_bounds(plan, fp64, j0, j1, nullptr, 0, st));
+    NOLSM_TRY(power_bounds(plan, cls, j0, j1, nullptr, 0, st));
     spec->lam = plan->lam_p.as<double>();
   } else if (source == NOLSM_BOUND_MLP) {
     NOLSM_TRY(features(plan, mu, j0, j1, st));
@@ -245,11 +245,12 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
   const bool fp64 = opts->precision == NOLSM_FP64;
+  const int cls = prep_class(*opts);
   mark(plan, 0, st);
-  NOLSM_TRY(prepare_fp64(plan, j0, j1, fp64, st));
+  NOLSM_TRY(prepare(plan, j0, j1, cls, st));
   int level = opts->bound_source;
   SolveSpec spec;
-  NOLSM_TRY(bound_spec(plan, level, mu, *opts, fp64, j0, j1, st, &spec));
+  NOLSM_TRY(bound_spec(plan, level, mu, *opts, cls, j0, j1, st, &spec));
   mark(plan, 1, st);
   NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, spec, st) : solve_tc(plan, mu, *opts, j0, j1, spec, st));
   // submatrices that failed the convergence test under learned bounds are solved again with power
@@ -263,7 +264,7 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
     rs.list = plan->rerun.as<int32_t>();
     rs.count = count;
     if (level == NOLSM_BOUND_POWER) {
-      NOLSM_TRY(power_bounds(plan, fp64, 0, 0, rs.list, count, st));
+      NOLSM_TRY(power_bounds(plan, cls, 0, 0, rs.list, count, st));
       rs.lam = plan->lam_p.as<double>();
     } else {
       rs.lam = plan->lam.as<double>();
@@ -319,7 +320,7 @@ nolsm_status nolsm_spectral_bracket(nolsm_plan* plan, const nolsm_options* opts,
   cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
   mark(plan, 0, st);
-  NOLSM_TRY(prepare_fp64(plan, j0, j1, opts->precision == NOLSM_FP64, st));
+  NOLSM_TRY(prepare(plan, j0, j1, prep_class(*opts), st));
   mark(plan, 1, st);
   std::vector<double> lam((size_t)(2 * (j1 - j0)));
   NOLSM_CUDA_TRY(cudaMemcpyAsync(lam.data(), plan->lam.as<double>() + 2 * j0, sizeof(double) * lam.size(),
@@ -390,7 +391,7 @@ nolsm_status nolsm_features(nolsm_plan* plan, double mu, const nolsm_options* op
   NOLSM_TRY(check_options(plan, opts, &j0, &j1));
   cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
-  NOLSM_TRY(prepare_fp64(plan, j0, j1, opts->precision == NOLSM_FP64, st));
+  NOLSM_TRY(prepare(plan, j0, j1, prep_class(*opts), st));
   NOLSM_TRY(features(plan, mu, j0, j1, st));
   NOLSM_CUDA_TRY(cudaMemcpyAsync(feat + j0 * kFeatures, plan->feat.as<float>() + j0 * kFeatures,
                                  sizeof(float) * kFeatures * (size_t)(j1 - j0), cudaMemcpyDeviceToDevice, st));
@@ -404,9 +405,9 @@ nolsm_status nolsm_power_bounds(nolsm_plan* plan, const nolsm_options* opts, nol
   NOLSM_TRY(check_options(plan, opts, &j0, &j1));
   cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
-  const bool fp64 = opts->precision == NOLSM_FP64;
-  NOLSM_TRY(prepare_fp64(plan, j0, j1, fp64, st));
-  NOLSM_TRY(power_bounds(plan, fp64, j0, j1, nullptr, 0, st));
+  const int cls = prep_class(*opts);
+  NOLSM_TRY(prepare(plan, j0, j1, cls, st));
+  NOLSM_TRY(power_bounds(plan, cls, j0, j1, nullptr, 0, st));
   if (lam)
     NOLSM_CUDA_TRY(cudaMemcpyAsync(lam + 2 * j0, plan->lam_p.as<double>() + 2 * j0, sizeof(double) * 2 * (size_t)(j1 - j0),
                                    cudaMemcpyDeviceToDevice, st));

@@ -76,12 +76,14 @@ struct nolsm_plan {
   nolsm::DevBuf Sc, Hc;   // centre columns of T_J(S), T_J(H0) (FP64)
   nolsm::DevBuf lam;      // float64 [2*n_mol]: Gershgorin interval of A_J
   nolsm::DevBuf prep_status;  // int32 [n_mol]: kSubOk or kSubNotSpd from the factorisation
-  nolsm::Prepared prep64, prep32;
+  nolsm::Prepared prep64, prep32, prep_sym;
+  nolsm::DevBuf Lsym;               // float32, FP32 factors of every submatrix at a_off (symmetric form)
+  nolsm::DevBuf Wc;                 // float64, W_c = L^-1 E_c at c_off (symmetric form)
 
   // bound sources other than Gershgorin (bounds.cu)
   nolsm::DevBuf lam_p;              // float64 [2*n_mol]: power-iteration interval
-  std::vector<uint8_t> pow_done;    // host flag per submatrix: lam_p computed (for pow_fp64)
-  bool pow_fp64 = false;
+  std::vector<uint8_t> pow_done;    // host flag per submatrix: lam_p computed (for pow_cls)
+  int pow_cls = -1;
   nolsm::DevBuf onsite;             // float64 [2*n_mol]: sum and sum of squares of diag(H0_II)
   bool onsite_done = false;
   nolsm::DevBuf feat;               // float32 [n_mol*7]: features of the last features() call
@@ -105,6 +107,7 @@ struct nolsm_plan {
   nolsm::DevBuf ws_dense;           // gathered T_J(S), T_J(H0) of one preparation chunk (FP64)
   nolsm::DevBuf ws_l32;             // FP32 factors of one preparation chunk (low-precision paths)
   nolsm::DevBuf ws_refine;          // FP64 residuals and FP32 corrections of Q for one chunk
+  nolsm::DevBuf ws_ysym;            // L^-1 T_J(H0) of one preparation chunk (symmetric form)
   nolsm::DevBuf ws_ns;              // per-CTA Newton-Schulz buffers (FP64 path)
   void* tc = nullptr;               // tensor-core path state (tc_path.cu)
 
@@ -127,7 +130,15 @@ void dev_free(nolsm_plan* plan, DevBuf& b);
 nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st);
 
 // per-geometry preparation and per-mu solve of the FP64 path (fp64_path.cu)
-nolsm_status prepare_fp64(nolsm_plan* plan, int64_t j0, int64_t j1, bool keep_fp64_A, cudaStream_t st);
+// Preparation classes: FP64 A (plain FP64 path), FP32 A = T_J(S)^-1 T_J(H0) (tensor-core paths), FP32
+// symmetric form M = L^-1 T_J(H0) L^-T (E4M3, or any tensor-core mode on request).
+enum : int { kPrepFP64 = 0, kPrepMixed = 1, kPrepSym = 2 };
+inline int prep_class(const nolsm_options& o) {
+  if (o.precision == NOLSM_FP64) return kPrepFP64;
+  return (o.precision == NOLSM_FP8E4M3 || o.symmetric_form) ? kPrepSym : kPrepMixed;
+}
+inline Prepared& prepared(nolsm_plan* plan, int cls);
+nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStream_t st);
 // a4 scale of submatrix J at mu: alpha = max(hi - mu, mu - lo) of the bound source's interval, but not
 // below 1/1.7 of the same from the Gershgorin interval [lg, hg], which contains the spectrum. Every
 // eigenvalue of X_0 then lies in [-1.7, 1.7] inside (-sqrt(3), sqrt(3)), where the Newton-Schulz map
@@ -166,3 +177,7 @@ nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_m
 nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st);
 
 }  // namespace nolsm
+
+inline nolsm::Prepared& nolsm::prepared(nolsm_plan* plan, int cls) {
+  return cls == kPrepFP64 ? plan->prep64 : (cls == kPrepSym ? plan->prep_sym : plan->prep32);
+}

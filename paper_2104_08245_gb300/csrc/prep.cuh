@@ -21,6 +21,21 @@ struct PrepArgs {
   double* R64 = nullptr;      // FP64 residuals of Q, n x b at c_off - c_base
   float* W32 = nullptr;       // FP32 corrections of Q, n x b at c_off - c_base
   int32_t fallback_max_n = 0; // largest n the FP64 preparation takes (shared-memory panel)
+  // symmetric form M = L^-1 T_J(H0) L^-T (mixed preparation only)
+  int32_t sym = 0;
+  float* Ysym = nullptr;      // L^-1 T_J(H0), same offsets as ws
+  double* Wc = nullptr;       // W_c = L^-1 E_c, n x b at c_off (plan-wide)
+};
+
+// The symmetric form's finishing step: D_c = L^-T U (U left in Dc by the sign kernel), traces.
+struct SymArgs {
+  int32_t j0;
+  const int32_t* list;        // or: submatrices by CTA
+  const int32_t* sub_n; const int32_t* nbf; const int64_t* a_off; const int64_t* c_off;
+  const int32_t* prep_status;
+  const float* L;             // FP32 factors of every submatrix, at a_off
+  const double* Sc; const double* Hc;
+  double* Dc; double* tS; double* tH; int32_t* status;
 };
 
 // a2-a3 for `count` submatrices starting at g.j0 (largest dimension max_n); A in FP64 (fp64_A) or FP32.
@@ -30,5 +45,6 @@ nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A
 nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float* Acache, cudaStream_t st);
 // Largest submatrix dimension the FP64 preparation takes.
 int prepare_fp64_max_n();
+nolsm_status launch_sym_finish(const SymArgs& g, int count, int max_n, int max_b, cudaStream_t st);
 
 }  // namespace nolsm

@@ -535,8 +535,12 @@ __device__ __forceinline__ float rt_rhs(const double* __restrict__ H, int n, int
   return col < n ? (float)H[(size_t)row * n + col] : (row == c0 + col - n ? 1.0f : 0.0f);
 }
 
+// kMode 0: X = L^-T L^-1 T_J(H0) (and W = L^-T L^-1 E_c); kMode 1: forward only, X = L^-1 T_J(H0) (and
+// W = L^-1 E_c); kMode 2: forward only with the transposed right-hand side Yt^T, X = L^-1 Yt^T (Yt n x n).
+template <int kMode>
 __device__ void solve_A_rt(const float* __restrict__ L, const double* __restrict__ H, int n, int c0, int bq,
-                           float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm) {
+                           float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm,
+                           const float* __restrict__ Yt = nullptr) {
   const int tid = threadIdx.x;
   const int tr = tid >> 4, tc = tid & 15;
   const int nblk = (n + NB - 1) / NB;
@@ -549,7 +553,7 @@ __device__ void solve_A_rt(const float* __restrict__ L, const double* __restrict
     return col < n ? X + (size_t)row * n + col : W + (size_t)row * bq + (col - n);
   };
   for (int cb = 0; cb < ncol; cb += kRtCb) {
-    for (int pass = 0; pass < 2; ++pass) {   // 0: forward Y = L^-1 B; 1: backward L^-T Y
+    for (int pass = 0; pass < (kMode == 0 ? 2 : 1); ++pass) {   // 0: forward Y = L^-1 B; 1: backward L^-T Y
       for (int s = 0; s < nblk; ++s) {
         const int rbk = pass == 0 ? s : nblk - 1 - s;
         const int r0 = rbk * NB, rb = min(NB, n - r0);
@@ -561,7 +565,11 @@ __device__ void solve_A_rt(const float* __restrict__ L, const double* __restrict
           for (int c = 0; c < 4; ++c) {
             const int col = cb + 4 * tc + c;
             float v = 0.0f;
-            if (row < n && col < ncol) v = pass == 0 ? rt_rhs(H, n, c0, row, col) : *addr(row, col);
+            if (row < n && col < ncol) {
+              if (pass == 1) v = *addr(row, col);
+              else if (kMode == 2) v = Yt[(size_t)col * n + row];
+              else v = rt_rhs(H, n, c0, row, col);
+            }
             acc[a][c] = v;
           }
         }
@@ -717,8 +725,8 @@ __device__ void solve_Q(const double* __restrict__ S, int n, int c0, int b, doub
 }
 
 // ------------------------------------------------------------------------------------ mixed-precision Q
-// W <- L^-T L^-1 W for the b columns of W (n x b row-major, FP32), with the FP32 factor.
-__device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
+// W <- L^-1 W for the b columns of W (n x b row-major, FP32), with the FP32 factor.
+__device__ void forward_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
                              float (*Acc)[kMaxB + 1], float (*Xd)[NB + 4]) {
   const int tid = threadIdx.x;
   const int nblk = (n + NB - 1) / NB;
@@ -744,6 +752,13 @@ __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* _
     }
     __syncthreads();
   }
+}
+
+// W <- L^-T W.
+__device__ void backward_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
+                             float (*Acc)[kMaxB + 1], float (*Xd)[NB + 4]) {
+  const int tid = threadIdx.x;
+  const int nblk = (n + NB - 1) / NB;
   for (int rbk = nblk - 1; rbk >= 0; --rbk) {   // backward
     const int r0 = rbk * NB, rb = min(NB, n - r0);
     for (int e = tid; e < rb * b; e += kThreads) {
@@ -765,6 +780,13 @@ __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* _
     }
     __syncthreads();
   }
+}
+
+// W <- L^-T L^-1 W for the b columns of W (n x b row-major, FP32), with the FP32 factor.
+__device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* __restrict__ W,
+                             float (*Acc)[kMaxB + 1], float (*Xd)[NB + 4]) {
+  forward_cols32(L, n, b, W, Acc, Xd);
+  backward_cols32(L, n, b, W, Acc, Xd);
 }
 
 // R = E_c - S q in FP64 (S the full symmetric T_J(S)); one warp per row, lanes along the row, up to 8
@@ -893,8 +915,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
     float* w = g.W32 + (g.c_off[J] - g.c_base);
     double* r = g.R64 + (g.c_off[J] - g.c_base);
     double* q = g.Q + g.c_off[J];
-    const bool merge_q = (n + bJ + kThreads - 1) / kThreads == (n + kThreads - 1) / kThreads;
-    solve_A_rt(L, H, n, c0, merge_q ? bJ : 0, A, w, Pf);
+    const bool merge_q = !g.sym && (n + bJ + kRtCb - 1) / kRtCb == (n + kRtCb - 1) / kRtCb;
+    if (g.sym) {
+      // the symmetric form M = L^-1 T_J(H0) L^-T = L^-1 (L^-1 T_J(H0))^T and W_c = L^-1 E_c
+      float* Y = g.Ysym + (g.a_off[J] - g.a_base);
+      solve_A_rt<1>(L, H, n, c0, bJ, Y, w, Pf);
+      for (int e = tid; e < nbc; e += kThreads) g.Wc[g.c_off[J] + e] = (double)w[e];
+      __syncthreads();
+      solve_A_rt<2>(L, H, n, c0, 0, A, nullptr, Pf, Y);
+    } else {
+      solve_A_rt<0>(L, H, n, c0, merge_q ? bJ : 0, A, w, Pf);
+    }
     if (!merge_q) {
       for (int e = tid; e < nbc; e += kThreads) {
         const int i = e / bJ, c = e - i * bJ;
@@ -952,6 +983,53 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   if (tid == 0) g.prep_status[J] = ok ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
 }
 
+// The symmetric form's last step, after the sign kernel: its centre-column phase leaves
+// U = 1/2 (I - X~) W_c in Dc (W_c = L^-1 E_c, X~ = sign of M - mu I); here D_c = L^-T U with the FP32 factor
+// (Eq. purification_submatrix: T_J(D) = L^-T 1/2 (I - X~) L^-1), and the partial traces in FP64.
+__global__ void __launch_bounds__(kThreads) k_sym_finish(SymArgs g) {
+  extern __shared__ __align__(16) float Wsh[];   // n x b
+  __shared__ float Acc[NB][kMaxB + 1];
+  __shared__ __align__(16) float Xd[NB][NB + 4];
+  __shared__ double red[2][kThreads / 32];
+  const int tid = threadIdx.x;
+  const int J = g.list ? g.list[blockIdx.x] : g.j0 + (int)blockIdx.x;
+  if (J < 0 || g.prep_status[J] != kSubOk) return;
+  const int n = g.sub_n[J], b = g.nbf[J], nb = n * b;
+  const float* L = g.L + g.a_off[J];
+  double* Dc = g.Dc + g.c_off[J];
+  for (int e = tid; e < nb; e += kThreads) Wsh[e] = (float)Dc[e];
+  __syncthreads();
+  backward_cols32(L, n, b, Wsh, Acc, Xd);
+  double ps = 0.0, ph = 0.0;
+  const double* Sc = g.Sc + g.c_off[J];
+  const double* Hc = g.Hc + g.c_off[J];
+  for (int e = tid; e < nb; e += kThreads) {
+    const double d = (double)Wsh[e];
+    Dc[e] = d;
+    ps += d * Sc[e];
+    ph += d * Hc[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ps += __shfl_xor_sync(0xffffffffu, ps, o);
+    ph += __shfl_xor_sync(0xffffffffu, ph, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = ps;
+    red[1][tid >> 5] = ph;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double ts = 0.0, th = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      ts += red[0][w];
+      th += red[1][w];
+    }
+    g.tS[J] = ts;
+    g.tH[J] = th;
+    if (g.status[J] == kSubOk && !(isfinite(ts) && isfinite(th))) g.status[J] = kSubNonFinite;
+  }
+}
+
 size_t smem_fp64(int max_n) { return sizeof(double) * (size_t)std::max(max_n, 2 * NB) * (NB + 1); }
 size_t smem_mixed(int max_n) {
   return sizeof(float) * std::max((size_t)(std::max(max_n, 2 * NB) + 36) * Ld<float>::v, (size_t)kRtSmem);
@@ -980,6 +1058,15 @@ nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A
   return NOLSM_OK;
 }
 
+nolsm_status launch_sym_finish(const SymArgs& g, int count, int max_n, int max_b, cudaStream_t st) {
+  if (count <= 0) return NOLSM_OK;
+  const size_t smem = sizeof(float) * (size_t)max_n * max_b;
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_sym_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_sym_finish<<<count, kThreads, smem, st>>>(g);
+  NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
+
 nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float* Acache, cudaStream_t st) {
   const size_t smem = smem_mixed(max_n);
   if (smem > kSmemLimit) {
@@ -990,7 +1077,9 @@ nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_prepare_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_prepare_mixed<<<count, kThreads, smem, st>>>(g, Acache);
   NOLSM_LAUNCH_CHECK();
-  // the FP64 preparation again for the flagged submatrices (every other CTA returns at once)
+  // the FP64 preparation again for the flagged submatrices (every other CTA returns at once); the
+  // symmetric form flags none (it has no FP64 fallback)
+  if (g.sym) return NOLSM_OK;
   PrepArgs f = g;
   f.only_flagged = 1;
   NOLSM_TRY(launch_prepare(f, count, std::min(max_n, prepare_fp64_max_n()), false, Acache, st));

@@ -28,6 +28,7 @@
 #include <cmath>
 
 #include "nolsm_internal.cuh"
+#include "prep.cuh"
 #include "tc_path.cuh"
 #include "tcgen05.cuh"
 #include "tmap.cuh"
@@ -722,8 +723,11 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   }
   g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
-  g.A = plan->prep32.A.as<float>();
-  g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
+  // the symmetric form iterates on M and its centre-column phase uses W_c = L^-1 E_c in place of Q
+  const bool sym = prep_class(o) == kPrepSym;
+  g.A = prepared(plan, prep_class(o)).A.as<float>();
+  g.Q = sym ? plan->Wc.as<double>() : plan->Q.as<double>();
+  g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
   g.lam = spec.lam ? spec.lam : plan->lam.as<double>();
   g.lam_g = plan->lam.as<double>();
   g.prep_status = plan->prep_status.as<int32_t>();
@@ -743,6 +747,20 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;
+  if (sym) {   // D_c = L^-T U and the traces
+    SymArgs a;
+    a.j0 = (int32_t)j0;
+    a.list = spec.list;
+    a.sub_n = plan->sub_n.as<int32_t>(); a.nbf = plan->sys.nbf;
+    a.a_off = plan->a_off.as<int64_t>(); a.c_off = plan->c_off.as<int64_t>();
+    a.prep_status = plan->prep_status.as<int32_t>();
+    a.L = plan->Lsym.as<float>();
+    a.Sc = plan->Sc.as<double>(); a.Hc = plan->Hc.as<double>();
+    a.Dc = plan->Dc.as<double>(); a.tS = plan->t_S.as<double>(); a.tH = plan->t_H.as<double>();
+    a.status = plan->status.as<int32_t>();
+    NOLSM_TRY(launch_sym_finish(a, (int)work, maxn, plan->max_b, st));
+    plan->stats.launches += 1;
+  }
   return NOLSM_OK;
 }
 

@@ -168,3 +168,36 @@ def test_not_spd_reported_on_tensor_path(nl):
     r = nl.nolsm_solve_batch(plan, -0.1, nl.options("bf16x3"), check=False)
     assert r.status == nl._abi.ERR_NOT_SPD
     assert np.sum(r.sub_status.cpu().numpy() == nl._abi.ERR_NOT_SPD) > 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_symmetric_form_matches_oracle(nl, small_ref, prec):
+    """The symmetric form M = L^-1 T_J(H0) L^-T (same spectrum, symmetric iterates, D_c = L^-T U) gives
+    the same densities as the standard form within the mode's tolerance."""
+    sysm, ref = small_ref
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    r = nl.nolsm_solve_batch(plan, -0.1, nl.options(prec, symmetric_form=1))
+    D = plan.scatter().cpu().numpy()
+    err = d_error(None, ref, D)
+    print(f"{prec} symmetric form: max|dD| = {err:.3e}")
+    assert err <= TOL[prec]
+    assert abs(r.trace_DH - ref.trace_DH) / abs(ref.trace_DH) <= TOL_TR_DH
+    assert abs(r.trace_DS - ref.trace_DS) / abs(ref.trace_DS) <= TOL_TR_DH
+    assert np.all(r.sub_status.cpu().numpy() == 0)
+
+
+def test_symmetric_form_full_size_sampled(nl):
+    from synth import spec_batched_uneven_4096
+    sysm = make_system(spec_batched_uneven_4096())
+    mu = -0.35
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    rng = np.random.default_rng(8)
+    subs = sorted(int(j) for j in rng.choice(sysm.n_mol, size=24, replace=False))
+    ref = orc.solve(sysm, mu, subs=subs, plan=po)
+    r = nl.nolsm_solve_batch(plan, mu, nl.options("fp32", symmetric_form=1))
+    D = plan.scatter().cpu().numpy()
+    err = d_error(po, ref, D, subs)
+    print(f"symmetric form, 4096 molecules: sampled max|dD| = {err:.3e}")
+    assert err <= TOL["fp32"]
+    assert np.all(r.sub_status.cpu().numpy() == 0)
