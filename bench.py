@@ -466,7 +466,7 @@ def main():
     paths = {}
     if not args.no_extra:
         plan = nl.nolsm_build_submatrices(dsys)
-        for prec in ["fp32", "bf16x3", "fp16", "bf16", "fp64"]:
+        for prec in ["fp32", "bf16x3", "fp16", "bf16", "fp8e4m3", "fp64"]:
             o = nl.options(prec)
             if prec == "fp64":
                 o.sub_begin, o.sub_end = 0, min(n_mol, 2 * 152 * 4)

@@ -23,6 +23,7 @@
 // submatrices in flight as timed out.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -47,12 +48,21 @@ constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + 
 constexpr int kPlanes = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
 
-enum : int { FMT_F16 = 0, FMT_BF16 = 1 };
+enum : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
 
 struct Fmt {
-  int fmt;    // FMT_F16 / FMT_BF16
-  int terms;  // 1 or 3
+  int fmt;    // FMT_F16 / FMT_BF16 / FMT_E4M3
+  int terms;  // 1 or 3 (E4M3: 1)
 };
+
+// E4M3 operands carry a fixed power-of-two scale: the symmetric iterates have |x_ij| <= rho <= 1.7 (the
+// scale guard), so x * 2^7 stays below 218 of E4M3's 448 and values down to 2^-16 keep a subnormal; a
+// product of two scaled operands is scaled back by 2^-14.
+constexpr float kF8Up = 128.0f;
+constexpr float kF8Down = 1.0f / 16384.0f;
+constexpr float kF8Switch = 0.1f;   // defect at which the E4M3 phase hands over to the refinement format
+// K extent of an E4M3 operand row: whole 128-byte slices
+__host__ __device__ inline int k8_extent(int n64) { return (n64 + 127) & ~127; }
 
 struct TcArgs {
   int32_t j0, j1;
@@ -86,6 +96,7 @@ struct SlotState {
   int kind;                      // next product: 0 (X X) or 1 (X T)
   int cur;                       // which X plane pair holds the current iterate
   int phase, refine_left, steps, rsteps, status, last;
+  float dprev;                   // defect of the previous step (E4M3 stagnation test)
   Fmt fcur, fnxt;
 };
 
@@ -164,7 +175,8 @@ __device__ __forceinline__ bool epi_bar_or(bool p) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-            const __grid_constant__ CUtensorMap mapS, TcArgs g) {
+            const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapA8,
+            const __grid_constant__ CUtensorMap mapB8, TcArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Shared sh;
@@ -187,6 +199,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::prefetch_tmap(&mapA);
     tc::prefetch_tmap(&mapB);
     tc::prefetch_tmap(&mapS);
+    tc::prefetch_tmap(&mapA8);
+    tc::prefetch_tmap(&mapB8);
   }
   if (warp == 0) {
     tc::tmem_alloc(&sh.tmem, 512);
@@ -243,11 +257,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_arrive(&sh.desc_full[i % kRing]);
       if (d.term) break;
       const int two = d.f.terms > 1 ? 2 : 1;
+      const bool f8 = d.f.fmt == FMT_E4M3;
+      const int nks = f8 ? k8_extent(d.n64) / 128 : d.nks;   // E4M3: 128-byte K slices
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
           const int nt = min(256, d.n64 - 256 * cb);
-          const uint32_t bytes = (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
-          for (int ks = 0; ks < d.nks; ++ks) {
+          // E4M3: both operands K-major (the symmetric iterate is its own transpose); the B box is always
+          // 256 rows (rows past R are zero-filled by the copy)
+          const uint32_t bytes = f8 ? kABytes + 256u * 128u : (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
+          for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
             if (!tc::mbar_wait(&sh.empty[st], ph ^ 1, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
@@ -255,11 +273,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::mbar_arrive_expect_tx(&sh.full[st], bytes);
             armed[st] = true;
             arm_phase[st] = ph;
-            for (int z = 0; z < two; ++z) {
-              tc::tma_load_3d(sm + z * kABytes, &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
-              uint8_t* bdst = sm + 2 * kABytes + z * kBBytes;
-              for (int c = 0; c < nt / 64; ++c)
-                tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], 256 * cb + 64 * c, 64 * ks, d.zb + z);
+            if (f8) {
+              tc::tma_load_3d(sm, &mapA8, &sh.full[st], 128 * ks, 128 * mb, d.za);
+              tc::tma_load_3d(sm + 2 * kABytes, &mapB8, &sh.full[st], 128 * ks, 256 * cb, d.zb);
+            } else {
+              for (int z = 0; z < two; ++z) {
+                tc::tma_load_3d(sm + z * kABytes, &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
+                uint8_t* bdst = sm + 2 * kABytes + z * kBBytes;
+                for (int c = 0; c < nt / 64; ++c)
+                  tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], 256 * cb + 64 * c, 64 * ks, d.zb + z);
+              }
             }
             ++kcount;
           }
@@ -276,10 +299,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const Desc d = sh.ring[i % kRing];
       if (d.term) break;
+      const bool f8 = d.f.fmt == FMT_E4M3;
+      const int nks = f8 ? k8_extent(d.n64) / 128 : d.nks;
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
           const int nt = min(256, d.n64 - 256 * cb);
-          const uint32_t id = tc::idesc(d.f.fmt, d.f.fmt, 0, 1, 128, nt);
+          // kind::f16: A K-major, B MN-major; kind::f8f6f4 (E4M3 = 0): both K-major
+          const uint32_t id = f8 ? tc::idesc(0, 0, 0, 0, 128, nt) : tc::idesc(d.f.fmt, d.f.fmt, 0, 1, 128, nt);
           const int buf = tcount & 1;
           if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + kWaitNs)) {
             sh.err = 1;
@@ -287,13 +313,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc::tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)buf * 256;
-          for (int ks = 0; ks < d.nks; ++ks) {
+          for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
             if (!tc::mbar_wait(&sh.full[st], ph, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_u32(stage_mem + st * kStageBytes);
             const uint32_t b0 = a0 + 2 * kABytes;
+            if (f8) {   // four K = 32 steps of 32 bytes through the 128-byte slice
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                tc::mma_f8(dt, tc::sdesc_sw128(a0 + kk * 32, 16, 1024), tc::sdesc_sw128(b0 + kk * 32, 16, 1024), id,
+                           (ks > 0 || kk > 0) ? 1u : 0u);
+              tc::mma_commit(&sh.empty[st]);
+              ++kcount;
+              continue;
+            }
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t ah = tc::sdesc_sw128(a0 + kk * 32, 16, 1024);
@@ -353,13 +388,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint16_t* hi = g.planes + (size_t)(sub0 + s) * kPlanes * plane_elems;
         uint16_t* lo = hi + plane_elems;
         const Fmt f = g.main_fmt;
-        for (int e = etid; e < R * n64; e += 256) {
-          const int i = e / n64, j = e - i * n64;
-          float x = 0.0f;
-          if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
-          const uint16_t h = to_bits(x, f.fmt);
-          hi[(size_t)i * g.LD + j] = h;
-          if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+        if (f.fmt == FMT_E4M3) {
+          // one-byte view: X_0 * 2^7 in E4M3 over whole 128-byte K slices, and zeros in the K padding of
+          // the other X plane and of T (their products write only the first n64 columns)
+          const int k8 = k8_extent(n64);
+          uint8_t* p8 = reinterpret_cast<uint8_t*>(hi);
+          for (int e = etid; e < R * k8; e += 256) {
+            const int i = e / k8, j = e - i * k8;
+            float x = 0.0f;
+            if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
+            p8[(size_t)i * 2 * g.LD + j] = (uint8_t)__nv_cvt_float_to_fp8(kF8Up * x, __NV_SATFINITE, __NV_E4M3);
+            if (j >= n64) {
+              p8[2 * 2 * plane_elems + (size_t)i * 2 * g.LD + j] = 0;   // X_1
+              p8[4 * 2 * plane_elems + (size_t)i * 2 * g.LD + j] = 0;   // T
+            }
+          }
+        } else {
+          for (int e = etid; e < R * n64; e += 256) {
+            const int i = e / n64, j = e - i * n64;
+            float x = 0.0f;
+            if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
+            const uint16_t h = to_bits(x, f.fmt);
+            hi[(size_t)i * g.LD + j] = h;
+            if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+          }
         }
         if (tid == 128) {
           st.job = J;
@@ -368,6 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           st.kind = 0; st.cur = 0;
           st.phase = 0; st.refine_left = g.refine_steps; st.steps = 0; st.rsteps = 0;
           st.status = kSubNotConv; st.last = 0;
+          st.dprev = INFINITY;
           st.fcur = g.main_fmt; st.fnxt = g.main_fmt;
         }
         break;
@@ -474,6 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
           uint32_t r[32];
           if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
+          const float sc = d.f.fmt == FMT_E4M3 ? kF8Down : 1.0f;   // E4M3 operand scales
           for (int c0 = grp; c0 < nch; c0 += 2) {
             const int col0 = 256 * cb + 32 * c0;
             float v[32];
@@ -483,17 +537,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   const int col = col0 + j;
-                  const float e = (row == col ? 1.0f : 0.0f) - __uint_as_float(r[j]);  // (I - X^2)_ij
+                  const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - X^2)_ij
                   if (row < n && col < n) part += e * e;
                   v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
                 }
               } else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.5f * __uint_as_float(r[j]);
+                for (int j = 0; j < 32; ++j) v[j] = 0.5f * sc * __uint_as_float(r[j]);
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
-            {
+            if (d.fo.fmt == FMT_E4M3) {
+              // E4M3 output (scaled by 2^7): this thread's 32 bytes of the row, two 16-byte stores into the
+              // one-byte view of the plane (rows of 2 LD bytes)
+              if (live) {
+                uint32_t w8[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const uint32_t p0 = __nv_cvt_float2_to_fp8x2(make_float2(kF8Up * v[4 * j], kF8Up * v[4 * j + 1]),
+                                                               __NV_SATFINITE, __NV_E4M3);
+                  const uint32_t p1 = __nv_cvt_float2_to_fp8x2(make_float2(kF8Up * v[4 * j + 2], kF8Up * v[4 * j + 3]),
+                                                               __NV_SATFINITE, __NV_E4M3);
+                  w8[j] = p0 | (p1 << 16);
+                }
+                uint8_t* dst = reinterpret_cast<uint8_t*>(g.planes) + (size_t)d.zo * plane_elems * 2 +
+                               (size_t)row * (2 * g.LD) + col0;
+                reinterpret_cast<uint4*>(dst)[0] = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+                reinterpret_cast<uint4*>(dst)[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
+              }
+            } else {
               // stage the chunk in shared memory (64-byte swizzle: 16-byte unit c of row r sits at
               // unit c ^ ((r >> 1) & 3)) and write it with TMA tensor stores
               uint8_t* shi = stg + grp * 2 * kStgBytes;
@@ -548,7 +620,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             last_ = 1;
             status = kSubNonFinite;
           } else if (st.phase == 0) {
-            if (dd <= g.tol_ns) {
+            // E4M3 iterates carry a rounding error of up to 2^-4 relative, which holds the defect at a floor
+            // near 0.05, well above tol_ns: their phase ends at twice that floor, or when the defect has
+            // stopped falling (below 0.25, where the exact iteration would at least halve it every step)
+            const bool f8_end = st.fcur.fmt == FMT_E4M3 && (dd <= kF8Switch || (dd < 0.25f && dd > 0.5f * st.dprev));
+            if (dd <= g.tol_ns || f8_end) {
               if (g.refine_steps == 0) {
                 last_ = 1;
                 status = dd <= g.tol_accept ? kSubOk : kSubNotConv;
@@ -558,10 +634,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 nxt = g.refine_fmt;
               }
             }
-          } else {
-            if (--st.refine_left == 0) {
+          } else if (--st.refine_left <= 0) {
+            if (dd <= g.tol_accept) {
               last_ = 1;
-              status = dd <= g.tol_accept ? kSubOk : kSubNotConv;
+              status = kSubOk;
+            } else if (dd < st.dprev) {
+              st.refine_left = 1;   // still converging: one more step (bounded by the step cap below)
+            } else {
+              last_ = 1;
+              status = kSubNotConv;
             }
           }
           const int cap = g.budget ? min(g.max_iter, g.budget[st.job]) : g.max_iter;
@@ -569,6 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             last_ = 1;
             status = kSubNotConv;
           }
+          st.dprev = dd;
           st.steps = steps;
           st.last = last_;
           st.status = status;
@@ -656,6 +738,7 @@ static bool formats(int precision, Fmt* main_fmt, Fmt* refine_fmt) {
     case NOLSM_FP32: *main_fmt = Fmt{FMT_F16, 3}; return true;
     case NOLSM_BF16X3: *main_fmt = Fmt{FMT_BF16, 3}; return true;
     case NOLSM_BF16: *main_fmt = Fmt{FMT_BF16, 1}; return true;
+    case NOLSM_FP8E4M3: *main_fmt = Fmt{FMT_E4M3, 1}; return true;
     case NOLSM_FP16: *main_fmt = Fmt{FMT_F16, 1}; return true;
     default: return false;
   }
@@ -666,6 +749,10 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   Fmt mf, rf;
   if (!formats(o.precision, &mf, &rf)) {
     set_error("precision %d is not available on the tensor-core path in this build", o.precision);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  if (mf.fmt == FMT_E4M3 && o.refine_steps < 1) {
+    set_error("E4M3 needs at least one refinement step (the centre-column phase reads a 2-byte X)");
     return NOLSM_ERR_UNSUPPORTED;
   }
   NOLSM_TRY(ensure_results(plan));
@@ -744,7 +831,14 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, g);
+  // one-byte views of the same planes (rows of 2 LD bytes) for E4M3 operands, both loaded K-major
+  CUtensorMap mA8, mB8;
+  if (!tmap::make_3d(&mA8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, 128) ||
+      !tmap::make_3d(&mB8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, 256)) {
+    set_error("cuTensorMapEncodeTiled rejected the one-byte scratch layout");
+    return NOLSM_ERR_CUDA;
+  }
+  k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;
   if (sym) {   // D_c = L^-T U and the traces
@@ -823,8 +917,9 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
     return NOLSM_ERR_UNSUPPORTED;
   }
   Fmt mf, rf;
-  if (!formats(opts->precision, &mf, &rf)) {
-    set_error("nolsm_sign_noalloc: precision %d is not a tensor-core mode", opts->precision);
+  if (!formats(opts->precision, &mf, &rf) || mf.fmt == FMT_E4M3) {
+    set_error("nolsm_sign_noalloc: precision %d is not available here (E4M3 needs the symmetric form)",
+              opts->precision);
     return NOLSM_ERR_UNSUPPORTED;
   }
   if (opts->max_iter < 1 || opts->refine_steps < 0 || !(opts->tol_ns > 0) || !(opts->tol_accept > 0)) {
@@ -884,7 +979,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
   g.rsteps = ints + 2 * kNaMaxSub;
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, g);
+  k_ns_tc<<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
   NOLSM_LAUNCH_CHECK();
   return NOLSM_OK;
 }

@@ -79,6 +79,69 @@ def test_plain_bf16_is_reported_not_hidden(nl, small_ref):
     assert np.all(r.sub_status.cpu().numpy() == 0)
 
 
+def fp8_report(nl, sysm, ref, mu, po=None, subs=None):
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    r = nl.nolsm_solve_batch(plan, mu, nl.options("fp8e4m3"))
+    D = plan.scatter().cpu().numpy()
+    err = d_error(po, ref, D, subs)
+    it = r.iters.cpu().numpy()
+    assert np.all(r.sub_status.cpu().numpy() == 0)
+    return r, err, it
+
+
+def test_fp8_mode_is_reported_not_hidden(nl, small_ref):
+    """E4M3 products (symmetric form, 2^7 operand scale) until the defect reaches 0.1, then three
+    FP32-mode steps. The E4M3 rounding of the iterates persists like the BF16 one, 5 bits coarser
+    (measured on GB300: max|dD| 4.9e-3, relative Tr(DH) 1.7e-5, 8 steps like the FP64 oracle)."""
+    sysm, ref = small_ref
+    r, err, it = fp8_report(nl, sysm, ref, -0.1)
+    rel = abs(r.trace_DH - ref.trace_DH) / abs(ref.trace_DH)
+    print(f"fp8e4m3 + 3 refinement steps: max|dD| = {err:.3e}, rel Tr(DH) = {rel:.3e}, "
+          f"steps {it.min()}..{it.max()}")
+    assert 1e-6 < err < 2e-2
+    assert rel < 1e-3
+    steps = np.array([ref.subs[J].steps for J in range(sysm.n_mol)])
+    assert np.all(it <= steps + 3)
+
+
+def test_fp8_mode_larger_than_one_tile(nl):
+    """n about 430: four 128-byte K slices, column blocks of 256 + 192, the ping-pong X planes."""
+    sysm = make_system(SystemSpec(6, 6, 6, cutoff=8.0, seed=17))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    subs = [0, 37, 101, 215]
+    ref = orc.solve(sysm, -0.1, subs=subs, plan=po)
+    _, err, it = fp8_report(nl, sysm, ref, -0.1, po, subs)
+    print(f"n~430 fp8e4m3: max|dD| = {err:.3e}, steps {it.min()}..{it.max()}")
+    assert err < 2e-2
+
+
+def test_fp8_mode_full_size_sampled(nl):
+    """4,096 molecules of the uneven workload (n = 138..240: K padding from n64 up to whole 128-byte
+    slices), 24 sampled submatrices against the oracle."""
+    from synth import spec_batched_uneven_4096
+    sysm = make_system(spec_batched_uneven_4096())
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    rng = np.random.default_rng(9)
+    subs = sorted(int(j) for j in rng.choice(sysm.n_mol, size=24, replace=False))
+    ref = orc.solve(sysm, -0.35, subs=subs, plan=po)
+    r, err, it = fp8_report(nl, sysm, ref, -0.35, po, subs)
+    tH = r.sub_t_H.cpu().numpy()
+    rel = max(abs(tH[J] - ref.subs[J].t_H) / abs(ref.subs[J].t_H) for J in subs)
+    print(f"full size fp8e4m3: sampled max|dD| = {err:.3e}, max rel t_H = {rel:.3e}, "
+          f"mean steps {it.mean():.2f}")
+    # measured on GB300: 2.9e-2 and 3.4e-3 (the E4M3 floor, amplified by the overlap's conditioning)
+    assert err < 1e-1
+    assert rel < 2e-2
+
+
+def test_fp8_needs_refinement_and_symmetric_form(nl, small_ref):
+    sysm, _ = small_ref
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    with pytest.raises(nl.NolsmError) as e:
+        nl.nolsm_solve_batch(plan, -0.1, nl.options("fp8e4m3", refine_steps=0))
+    assert e.value.status == nl._abi.ERR_UNSUPPORTED
+
+
 VARIANTS = {
     "aniso_cutoffs": spec_small_fp64(aniso=0.3, cutoff_h=5.0, seed=11),
     "mixed_nbf": SystemSpec(3, 3, 3, nbf="mixed", cutoff=4.5, seed=13),

@@ -118,3 +118,9 @@ def test_noalloc_rejects_oversized_submatrices():
                                 d.data_ptr(), d.data_ptr(), d.data_ptr(), d.data_ptr(), 0.0, ctypes.byref(opts), s,
                                 d.data_ptr(), d.data_ptr(), d.data_ptr(), i.data_ptr(), i.data_ptr())
     assert rc == nl._abi.ERR_UNSUPPORTED
+    # E4M3 products need the symmetric form, which the no-alloc entry does not prepare
+    opts8 = nl.options("fp8e4m3")
+    rc = lib.nolsm_sign_noalloc(1, one.data_ptr(), one.data_ptr(), z64.data_ptr(), z64.data_ptr(), f.data_ptr(),
+                                d.data_ptr(), d.data_ptr(), d.data_ptr(), d.data_ptr(), 0.0, ctypes.byref(opts8), s,
+                                d.data_ptr(), d.data_ptr(), d.data_ptr(), i.data_ptr(), i.data_ptr())
+    assert rc == nl._abi.ERR_UNSUPPORTED
