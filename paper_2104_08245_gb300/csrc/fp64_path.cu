@@ -437,8 +437,8 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
         pa.L32 = plan->ws_l32.as<float>();
       }
       pa.c_base = plan->h_c_off[J];
-      pa.R64 = plan->ws_refine.as<double>();
-      pa.W32 = reinterpret_cast<float*>(pa.R64 + std::max<int64_t>(nbc, 1));
+      pa.Qp = plan->ws_refine.as<float2>();
+      pa.W32 = reinterpret_cast<float*>(pa.Qp + std::max<int64_t>(nbc, 1));
       pa.fallback_max_n = sym ? 0 : prepare_fp64_max_n();   // no FP64 fallback for the symmetric form
       NOLSM_TRY(launch_prepare_mixed(pa, (int)(e - J), chunk_max_n, P.A.as<float>(), st));
       plan->stats.launches += 3;

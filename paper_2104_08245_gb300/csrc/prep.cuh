@@ -18,7 +18,7 @@ struct PrepArgs {
   // mixed preparation (low-precision paths)
   float* L32 = nullptr;       // FP32 factors, same offsets as ws (a_off - a_base)
   int64_t c_base = 0;         // c_off of the chunk's first submatrix
-  double* R64 = nullptr;      // FP64 residuals of Q, n x b at c_off - c_base
+  float2* Qp = nullptr;       // q as hi + lo FP32 pairs for the residual, n x b at c_off - c_base
   float* W32 = nullptr;       // FP32 corrections of Q, n x b at c_off - c_base
   int32_t fallback_max_n = 0; // largest n the FP64 preparation takes (shared-memory panel)
   // symmetric form M = L^-1 T_J(H0) L^-T (mixed preparation only)

@@ -10,8 +10,9 @@
 //    FP64 work is a dependent chain.
 //  - k_prepare_mixed (low-precision paths): L in FP32 (the FP32 pipe is ~60x the FP64 one), A by FP32
 //    solves as before, and Q by mixed-precision iterative refinement: q <- q + L^-T L^-1 (E_c - T_J(S) q)
-//    with the residual in FP64 and the correction solves in FP32, until the correction is below 1e-6 of
-//    q (the error then contracts by the same factor per step, so the result is FP64-accurate). A
+//    with the residual in double-FP32 arithmetic (T_J(S) and q split into two FP32 words each, about 48
+//    bits) and the correction solves in FP32, until the correction is below 1e-6 of q (the error then
+//    contracts by the same factor per step, down to the residual's accuracy, about 1e-12 relative). A
 //    submatrix whose FP32 factor fails or whose refinement does not contract is flagged and prepared
 //    again by k_prepare (FP64 factor).
 // The Cholesky factors a 32-column panel held in shared memory one column at a time in parallel over its
@@ -789,31 +790,70 @@ __device__ void solve_cols32(const float* __restrict__ L, int n, int b, float* _
   backward_cols32(L, n, b, W, Acc, Xd);
 }
 
-// R = E_c - S q in FP64 (S the full symmetric T_J(S)); one warp per row, lanes along the row, up to 8
-// columns of q per sweep.
-__device__ void residual64(const double* __restrict__ S, int n, int c0, int b, const double* __restrict__ q,
-                           double* __restrict__ R) {
+// s = hi + lo: hi the leading 24 significant bits of s (truncated), lo the next 24 (rounded), so 48 of
+// the 53 bits, by integer operations and conversions only (no FP64 arithmetic: the FP64 pipe is ~1/60
+// of the FP32 one here). For |s| < 2^-74 only hi is kept.
+__device__ __forceinline__ float2 split_f64(double s) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(s);
+  const float hi = __double2float_rz(__longlong_as_double((long long)(u & ~0x1FFFFFFFull)));
+  const int e = (int)((u >> 52) & 0x7FF);
+  float lo = 0.0f;
+  if (e >= 949 && e <= 1150) {
+    // the low 29 significand bits are an integer in units of 2^(e - 1075)
+    lo = __uint2float_rn((unsigned)(u & 0x1FFFFFFFull)) * __int_as_float((e - 948) << 23);
+    if (u >> 63) lo = -lo;
+  }
+  return make_float2(hi, lo);
+}
+
+// s + c <- s + c + p with s = fl(s + p) and the rounding error of that sum added to c (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float& s, float& c, float p) {
+  const float t = s + p;
+  const float z = t - s;
+  c += (s - (t - z)) + (p - z);
+  s = t;
+}
+
+// R = E_c - S q (S the full symmetric T_J(S) in FP64, q given as hi + lo FP32 pairs), written to R in
+// FP32, in double-FP32 arithmetic (the compensated dot product of Ogita, Rump and Oishi): the hi*hi
+// products are split exactly (fmaf) and summed with TwoSum, the hi*lo and lo*hi products summed plainly.
+// The sums are accurate to about n 2^-48 of |S||q|, which is what the refinement of q needs from its
+// residual. One warp per row, lanes along the row, up to 8 columns of q per sweep.
+__device__ void residual_df(const double* __restrict__ S, int n, int c0, int b, const float2* __restrict__ qp,
+                            float* __restrict__ R) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < n; i += kThreads / 32) {
     const double* Si = S + (size_t)i * n;
     for (int cg = 0; cg < b; cg += 8) {
       const int cn = min(8, b - cg);
-      double acc[8];
+      float sh[8], sl[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+      for (int c = 0; c < 8; ++c) sh[c] = sl[c] = 0.0f;
       for (int k = lane; k < n; k += 32) {
-        const double s = Si[k];
-        const double* qk = q + (size_t)k * b + cg;
+        const float2 a = split_f64(Si[k]);
+        const float2* qk = qp + (size_t)k * b + cg;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < cn) acc[c] = fma(s, qk[c], acc[c]);
+        for (int c = 0; c < 8; ++c) {
+          if (c < cn) {
+            const float2 v = qk[c];
+            const float p = a.x * v.x;
+            sl[c] += fmaf(a.x, v.x, -p);
+            two_sum(sh[c], sl[c], p);
+            sl[c] = fmaf(a.x, v.y, fmaf(a.y, v.x, sl[c]));
+          }
+        }
       }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         if (c < cn) {
-          double v = acc[c];
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) R[(size_t)i * b + cg + c] = (i == c0 + cg + c ? 1.0 : 0.0) - v;
+          float h = sh[c], l = sl[c];
+          for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+            two_sum(h, l, oh);
+            l += ol;
+          }
+          // 1 - h is exact when h is within a factor 2 of 1 (Sterbenz), as it is near the solution
+          if (lane == 0) R[(size_t)i * b + cg + c] = ((i == c0 + cg + c ? 1.0f : 0.0f) - h) - l;
         }
       }
     }
@@ -823,14 +863,16 @@ __device__ void residual64(const double* __restrict__ S, int n, int c0, int b, c
 // Gershgorin interval of A (n x n, FP32 or FP64) widened by its rounding, into lam[2J], lam[2J+1].
 template <typename TA>
 __device__ void gershgorin(const TA* __restrict__ A, int n, double* lam, float* rlo, float* rhi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float lo = INFINITY, hi = -INFINITY;
-  for (int i = threadIdx.x; i < n; i += kThreads) {
-    float r = 0.0f;
+  for (int i = warp; i < n; i += kThreads / 32) {   // one warp per row, lanes along it
     const TA* Ai = A + (size_t)i * n;
-    for (int j = 0; j < n; ++j)
-      if (j != i) r += fabsf((float)Ai[j]);
-    lo = fminf(lo, (float)Ai[i] - r);
-    hi = fmaxf(hi, (float)Ai[i] + r);
+    float r = 0.0f;
+    for (int j = lane; j < n; j += 32) r += j != i ? fabsf((float)Ai[j]) : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    const float d = (float)Ai[i];
+    lo = fminf(lo, d - r);
+    hi = fmaxf(hi, d + r);
   }
   rlo[threadIdx.x] = lo;
   rhi[threadIdx.x] = hi;
@@ -900,11 +942,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   float* L = g.L32 + (g.a_off[J] - g.a_base);
   float (*Acc)[kMaxB + 1] = reinterpret_cast<float (*)[kMaxB + 1]>(Pf);   // solve_cols32 (after the solves)
   if (tid == 0) s_bad = 0;
-  for (int e = tid; e < n * n; e += kThreads) {
-    const int i = e / n, j = e - i * n;
-    if (j <= i) L[e] = (float)S[e];
-  }
-  __syncthreads();
+  for (int i = warp; i < n; i += kThreads / 32)
+    for (int j = lane; j <= i; j += 32) L[(size_t)i * n + j] = (float)S[(size_t)i * n + j];
   __syncthreads();
   bool ok = cholesky32(L, n, Pf, Xs, &s_bad);
   if (ok) {
@@ -913,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
     float* A = Acache + g.a_off[J];
     const int nbc = n * bJ;
     float* w = g.W32 + (g.c_off[J] - g.c_base);
-    double* r = g.R64 + (g.c_off[J] - g.c_base);
+    float2* qp = g.Qp + (g.c_off[J] - g.c_base);
     double* q = g.Q + g.c_off[J];
     const bool merge_q = !g.sym && (n + bJ + kRtCb - 1) / kRtCb == (n + kRtCb - 1) / kRtCb;
     if (g.sym) {
@@ -934,14 +973,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
       __syncthreads();
       solve_cols32(L, n, bJ, w, Acc, Xs);
     }
-    // Q_J: refinement with the FP64 residual
+    // Q_J: refinement with the double-FP32 residual
     for (int e = tid; e < nbc; e += kThreads) q[e] = (double)w[e];
     __syncthreads();
     bool conv = false;
     for (int it = 0; it < kRefineMax && !conv; ++it) {
-      residual64(S, n, c0, bJ, q, r);
+      for (int e = tid; e < nbc; e += kThreads) qp[e] = split_f64(q[e]);
       __syncthreads();
-      for (int e = tid; e < nbc; e += kThreads) w[e] = (float)r[e];
+      residual_df(S, n, c0, bJ, qp, w);
       __syncthreads();
       solve_cols32(L, n, bJ, w, Acc, Xs);
       float dmax = 0.0f;
