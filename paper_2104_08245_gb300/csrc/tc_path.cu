@@ -121,10 +121,6 @@ struct Shared {
   double dred[2][8];
 };
 
-__device__ __forceinline__ uint16_t to_bits(float x, int fmt) {
-  if (fmt == FMT_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-  return __half_as_ushort(__float2half_rn(x));
-}
 __device__ __forceinline__ float from_bits(uint16_t b, int fmt) {
   if (fmt == FMT_BF16) return __bfloat162float(__ushort_as_bfloat16(b));
   return __half2float(__ushort_as_half(b));
@@ -147,16 +143,59 @@ __device__ __forceinline__ void split2(float a, float b, int fmt, uint32_t& hi, 
   }
 }
 
-// Element k of a row held as hi (and lo) 2-byte planes.
-__device__ __forceinline__ float xval(const uint16_t* hi, const uint16_t* lo, int k, Fmt f) {
-  const float h = from_bits(hi[k], f.fmt);
-  return f.terms > 1 ? h + from_bits(lo[k], f.fmt) : h;
+// s + c <- s + c + p with s = fl(s + p) and the rounding error of that sum added to c (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float& s, float& c, float p) {
+  const float t = s + p;
+  const float z = t - s;
+  c += (s - (t - z)) + (p - z);
+  s = t;
 }
 
 // 32 consecutive values of one row as packed hi (and lo) pairs.
 __device__ __forceinline__ void split_pack(const float (&v)[32], Fmt f, uint32_t (&h)[16], uint32_t (&l)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) split2(v[2 * j], v[2 * j + 1], f.fmt, h[j], l[j]);
+}
+
+// One row of X (2-byte hi and, with kLo, lo planes; n64 columns, zero padded) times 8 columns of Q in
+// FP32 (rows of stride bp, zero padded to n64 rows): FP32 partial sums of 16 products, each added to
+// sh + sl with TwoSum. The row is read in 32-column pieces, eight 16-byte loads in flight.
+template <int kFmt, bool kLo>
+__device__ __forceinline__ void xq_row(const uint16_t* __restrict__ xh, const uint16_t* __restrict__ xl, int n64,
+                                       const float* __restrict__ Qs, int bp, float (&sh)[8], float (&sl)[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) sh[c] = sl[c] = 0.0f;
+  for (int k0 = 0; k0 < n64; k0 += 32) {
+    uint4 hv[4], lv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      hv[t] = *reinterpret_cast<const uint4*>(xh + k0 + 8 * t);
+      lv[t] = kLo ? *reinterpret_cast<const uint4*>(xl + k0 + 8 * t) : make_uint4(0, 0, 0, 0);
+    }
+    float p[8];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      if ((u & 15) == 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) p[c] = 0.0f;
+      }
+      const uint4 h4 = hv[u >> 3], l4 = lv[u >> 3];
+      const int w = (u & 7) >> 1, sft = 16 * (u & 1);
+      const uint32_t hw = w == 0 ? h4.x : w == 1 ? h4.y : w == 2 ? h4.z : h4.w;
+      const uint32_t lw = w == 0 ? l4.x : w == 1 ? l4.y : w == 2 ? l4.z : l4.w;
+      float x = from_bits((uint16_t)(hw >> sft), kFmt);
+      if (kLo) x += from_bits((uint16_t)(lw >> sft), kFmt);
+      const float4 qa = *reinterpret_cast<const float4*>(Qs + (size_t)(k0 + u) * bp);
+      const float4 qb = *reinterpret_cast<const float4*>(Qs + (size_t)(k0 + u) * bp + 4);
+      const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) p[c] = fmaf(x, qv[c], p[c]);
+      if ((u & 15) == 15) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) two_sum(sh[c], sl[c], p[c]);
+      }
+    }
+  }
 }
 
 // named barriers: 1 + group for one epilogue group (128 threads), 3 for both groups (256 threads)
@@ -404,13 +443,33 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          for (int e = etid; e < R * n64; e += 256) {
-            const int i = e / n64, j = e - i * n64;
-            float x = 0.0f;
-            if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
-            const uint16_t h = to_bits(x, f.fmt);
-            hi[(size_t)i * g.LD + j] = h;
-            if (f.terms > 1) lo[(size_t)i * g.LD + j] = to_bits(x - from_bits(h, f.fmt), f.fmt);
+          // four rows per warp pass, 8 consecutive columns per lane (all 32 loads in flight together, then
+          // 16-byte stores of hi and lo); rows and columns n..n64 are the zero padding; rows from n64 on
+          // only feed product rows that are never read back
+          for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+            for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
+              float v[4][8];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const int i = i0 + r;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const int j = j0 + u;
+                  v[r][u] = (i < n && j < n) ? (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv : 0.0f;
+                }
+              }
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const int i = i0 + r;
+                if (i >= n64) break;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) split2(v[r][2 * u], v[r][2 * u + 1], f.fmt, h[u], l[u]);
+                *reinterpret_cast<uint4*>(hi + (size_t)i * g.LD + j0) = make_uint4(h[0], h[1], h[2], h[3]);
+                if (f.terms > 1)
+                  *reinterpret_cast<uint4*>(lo + (size_t)i * g.LD + j0) = make_uint4(l[0], l[1], l[2], l[3]);
+              }
+            }
           }
         }
         if (tid == 128) {
@@ -443,35 +502,66 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double* Sc = g.Sc + g.c_off[J];
       const double* Hc = g.Hc + g.c_off[J];
       double* Dc = g.Dc + g.c_off[J];
-      float* Qs = reinterpret_cast<float*>(stg);   // staging is idle between products
-      const bool staged = (size_t)n * b * sizeof(float) <= 4 * kStgBytes;
-      if (staged)
-        for (int e = etid; e < n * b; e += 256) Qs[e] = (float)Q[e];
-      epi_bar();
+      // X Q with one row of X per lane (32 consecutive rows per warp), Q in FP32 in the staging buffers (idle
+      // between products), zero padded to bp = 8 ceil(b / 8) columns and n64 rows so that the inner loop has
+      // no conditions; the sums (hi, lo) then go through shared memory to the FP64 step, which runs
+      // element by element. Larger cases take the same sums with Q read from global memory.
+      const int n64 = st.n64, bp = (b + 7) & ~7;
+      float* Qs = reinterpret_cast<float*>(stg);
+      const size_t qs_bytes = (size_t)n64 * bp * sizeof(float);
+      const bool fast = qs_bytes + (size_t)n * b * sizeof(float2) <= 4 * kStgBytes;
+      float2* Ps = reinterpret_cast<float2*>(stg + qs_bytes);
       double ps = 0.0, ph = 0.0;
-      for (int e = etid; e < n * b; e += 256) {
-        const int i = e / b, c = e - i * b;
-        const uint16_t* xhi = xh + (size_t)i * g.LD;
-        const uint16_t* xli = xl + (size_t)i * g.LD;
-        // FP32 partial sums of 16 products, combined with Kahan compensation
-        float sum = 0.0f, comp = 0.0f;
-        for (int k0 = 0; k0 < n; k0 += 16) {
-          float p = 0.0f;
-          const int k1 = min(n, k0 + 16);
-          if (staged) {
-            for (int k = k0; k < k1; ++k) p = fmaf(xval(xhi, xli, k, xfmt), Qs[k * b + c], p);
-          } else {
-            for (int k = k0; k < k1; ++k) p = fmaf(xval(xhi, xli, k, xfmt), (float)Q[(size_t)k * b + c], p);
-          }
-          const float y = p - comp;
-          const float t = sum + y;
-          comp = (t - sum) - y;
-          sum = t;
+      if (fast) {
+        for (int e = etid; e < n64 * bp; e += 256) {
+          const int k = e / bp, c = e - k * bp;
+          Qs[e] = (k < n && c < b) ? (float)Q[(size_t)k * b + c] : 0.0f;
         }
-        const double dv = 0.5 * (Q[e] - ((double)sum - (double)comp));
-        Dc[e] = dv;
-        ps += dv * Sc[e];
-        ph += dv * Hc[e];
+        epi_bar();
+        for (int i0 = 32 * (warp - 4); i0 < n; i0 += 256) {
+          const int i = i0 + lane;
+          const size_t ro = (size_t)(i < n ? i : 0) * g.LD;
+          for (int cg = 0; cg < b; cg += 8) {
+            float sh_[8], sl_[8];
+            if (xfmt.fmt == FMT_BF16) {
+              if (xfmt.terms > 1) xq_row<FMT_BF16, true>(xh + ro, xl + ro, n64, Qs + cg, bp, sh_, sl_);
+              else xq_row<FMT_BF16, false>(xh + ro, xl + ro, n64, Qs + cg, bp, sh_, sl_);
+            } else {
+              if (xfmt.terms > 1) xq_row<FMT_F16, true>(xh + ro, xl + ro, n64, Qs + cg, bp, sh_, sl_);
+              else xq_row<FMT_F16, false>(xh + ro, xl + ro, n64, Qs + cg, bp, sh_, sl_);
+            }
+            if (i < n) {
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                if (cg + c < b) Ps[(size_t)i * b + cg + c] = make_float2(sh_[c], sl_[c]);
+            }
+          }
+        }
+        epi_bar();
+        for (int e = etid; e < n * b; e += 256) {
+          const float2 p = Ps[e];
+          const double dv = 0.5 * (Q[e] - ((double)p.x + (double)p.y));
+          Dc[e] = dv;
+          ps += dv * Sc[e];
+          ph += dv * Hc[e];
+        }
+      } else {
+        for (int e = etid; e < n * b; e += 256) {
+          const int i = e / b, c = e - i * b;
+          float sum = 0.0f, cmp = 0.0f;
+          for (int k = 0; k < n; ++k) {
+            const float x = from_bits(xh[(size_t)i * g.LD + k], xfmt.fmt) +
+                            (xfmt.terms > 1 ? from_bits(xl[(size_t)i * g.LD + k], xfmt.fmt) : 0.0f);
+            const float qv = (float)Q[(size_t)k * b + c];
+            const float p = x * qv;
+            cmp += fmaf(x, qv, -p);
+            two_sum(sum, cmp, p);
+          }
+          const double dv = 0.5 * (Q[e] - ((double)sum + (double)cmp));
+          Dc[e] = dv;
+          ps += dv * Sc[e];
+          ph += dv * Hc[e];
+        }
       }
       for (int o = 16; o > 0; o >>= 1) {
         ps += __shfl_xor_sync(0xffffffffu, ps, o);
