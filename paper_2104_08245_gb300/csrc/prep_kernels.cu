@@ -49,6 +49,15 @@ __device__ __forceinline__ T xinv(const T* S, int n, int r0, int a, int t) {
   return S[(size_t)(r0 + t) * n + r0 + a];  // stored transposed in the upper triangle
 }
 
+// Asynchronous 4-byte copy from global to shared memory; cp_async_wait_all waits for this thread's copies.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // The same for the FP32 factor, which stores X_r in the lower triangle of its diagonal blocks.
 __device__ __forceinline__ float xinv32(const float* L, int n, int r0, int a, int t) {
   return t > a ? 0.0f : L[(size_t)(r0 + a) * n + r0 + t];
@@ -212,10 +221,13 @@ __device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps,
   constexpr int LDP = Ld<float>::v;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0), mt = n - k0;
-    // panel rows by warp, lanes along the row, zero beyond kb
-#pragma unroll 4
-    for (int i = warp; i < mt; i += kThreads / 32)
-      Ps[i * LDP + lane] = lane < kb ? S[(size_t)(k0 + i) * n + k0 + lane] : 0.0f;
+    // panel rows by warp, lanes along the row, zero beyond kb; the copies are asynchronous, all in flight
+    for (int i = warp; i < mt; i += kThreads / 32) {
+      float* dst = Ps + i * LDP + lane;
+      if (lane < kb) cp_async4(dst, S + (size_t)(k0 + i) * n + k0 + lane);
+      else *dst = 0.0f;
+    }
+    cp_async_wait_all();
     __syncthreads();
     if (warp == 0) {
       // factor the diagonal block in the panel itself: lane i owns row i (rows beyond kb idle)
@@ -329,6 +341,13 @@ __device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps,
         for (int a = 0; a < 4; ++a) { ii[a] = bi + ty + 8 * a; vi[a] = ii[a] < mt; }
 #pragma unroll
         for (int b = 0; b < 2; ++b) { jj[b] = bj + tx + 16 * b; vj[b] = jj[b] < mt; }
+        // the elements to update, loaded before the products so that their latency overlaps them
+        float sv[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+            sv[a][b] = (vi[a] && vj[b] && jj[b] <= ii[a]) ? S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]] : 0.0f;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int t = 0; t < kb; t += 4) {
           float4 av[4], bv[2];
@@ -352,7 +371,7 @@ __device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 2; ++b)
-            if (vi[a] && vj[b] && jj[b] <= ii[a]) S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]] -= acc[a][b];
+            if (vi[a] && vj[b] && jj[b] <= ii[a]) S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]] = sv[a][b] - acc[a][b];
       }
     }
     __syncthreads();
@@ -818,18 +837,39 @@ __device__ __forceinline__ void two_sum(float& s, float& c, float p) {
 // FP32, in double-FP32 arithmetic (the compensated dot product of Ogita, Rump and Oishi): the hi*hi
 // products are split exactly (fmaf) and summed with TwoSum, the hi*lo and lo*hi products summed plainly.
 // The sums are accurate to about n 2^-48 of |S||q|, which is what the refinement of q needs from its
-// residual. One warp per row, lanes along the row, up to 8 columns of q per sweep.
+// residual. One thread per row (no cross-lane sums), the row read four elements at a time, q broadcast;
+// up to 8 columns of q per sweep.
 __device__ void residual_df(const double* __restrict__ S, int n, int c0, int b, const float2* __restrict__ qp,
                             float* __restrict__ R) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < n; i += kThreads / 32) {
+  for (int i = threadIdx.x; i < n; i += kThreads) {
     const double* Si = S + (size_t)i * n;
     for (int cg = 0; cg < b; cg += 8) {
       const int cn = min(8, b - cg);
       float sh[8], sl[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) sh[c] = sl[c] = 0.0f;
-      for (int k = lane; k < n; k += 32) {
+      int k = 0;
+      for (; k + 4 <= n; k += 4) {
+        double sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sv[u] = Si[k + u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 a = split_f64(sv[u]);
+          const float2* qk = qp + (size_t)(k + u) * b + cg;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c < cn) {
+              const float2 v = qk[c];
+              const float p = a.x * v.x;
+              sl[c] += fmaf(a.x, v.x, -p);
+              two_sum(sh[c], sl[c], p);
+              sl[c] = fmaf(a.x, v.y, fmaf(a.y, v.x, sl[c]));
+            }
+          }
+        }
+      }
+      for (; k < n; ++k) {
         const float2 a = split_f64(Si[k]);
         const float2* qk = qp + (size_t)k * b + cg;
 #pragma unroll
@@ -843,19 +883,10 @@ __device__ void residual_df(const double* __restrict__ S, int n, int c0, int b, 
           }
         }
       }
+      // 1 - sh is exact when sh is within a factor 2 of 1 (Sterbenz), as it is near the solution
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c < cn) {
-          float h = sh[c], l = sl[c];
-          for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
-            two_sum(h, l, oh);
-            l += ol;
-          }
-          // 1 - h is exact when h is within a factor 2 of 1 (Sterbenz), as it is near the solution
-          if (lane == 0) R[(size_t)i * b + cg + c] = ((i == c0 + cg + c ? 1.0f : 0.0f) - h) - l;
-        }
-      }
+      for (int c = 0; c < 8; ++c)
+        if (c < cn) R[(size_t)i * b + cg + c] = ((i == c0 + cg + c ? 1.0f : 0.0f) - sh[c]) - sl[c];
     }
   }
 }
