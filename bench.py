@@ -444,7 +444,7 @@ def main():
                                 "2 products per Newton-Schulz step, unpadded n"}
     if not fp64_path and ms_factor > ms_sign:
         ach_f = fl_fp32 / (ms_factor / 1e3) / 1e12 if ms_factor > 0 else 0.0
-        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, FP64 refinement)",
+        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, double-FP32 refinement of Q)",
                     "achieved": ach_f, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
                     "traffic": kernel_traffic("k_prepare_mixed", n_mol / chunks), "launches_per_step": chunks,
