@@ -541,7 +541,7 @@ __device__ void solve_A(const LT* __restrict__ S, const double* __restrict__ H, 
 
 // Register-tiled form of the same solves for the mixed preparation. Right-hand sides: columns c < n of
 // T_J(H0) (result into X, n x n) and, when bq > 0, the centre columns of the identity (result into W,
-// n x bq). Columns go in batches of 64; thread (tr, tc) = (tid / 16, tid % 16) owns rows 4tr..4tr+3 of the
+// n x bq). Columns go in batches of 64; thread (tr, tc) (tr < 8, tc < 16) owns rows 4tr..4tr+3 of the
 // current 32-row block and columns 4tc..4tc+3 of the batch, so every step of the inner loop is two
 // 16-byte shared loads and 16 FMAs. Chunks of 32 columns of L and 32 rows of the solution are staged
 // through registers, the next chunk's global loads in flight while the current one is used.
@@ -562,7 +562,10 @@ __device__ void solve_A_rt(const float* __restrict__ L, const double* __restrict
                            float* __restrict__ X, float* __restrict__ W, float* __restrict__ sm,
                            const float* __restrict__ Yt = nullptr) {
   const int tid = threadIdx.x;
-  const int tr = tid >> 4, tc = tid & 15;
+  // a warp covers 4 values of tr and 8 of tc, so each step of the inner loop reads 64 B of LT and 128 B
+  // of YC per warp (one shared-memory wavefront each)
+  const int lane = tid & 31, wrp = tid >> 5;
+  const int tr = 4 * (wrp & 1) + (lane >> 3), tc = 8 * (wrp >> 1) + (lane & 7);
   const int nblk = (n + NB - 1) / NB;
   const int ncol = n + bq;
   float* LT = sm;                       // [32][kRtLd]

@@ -43,8 +43,8 @@ constexpr int kStages = 2;
 constexpr uint32_t kABytes = 128 * 64 * 2;        // one A plane slice: 128 rows x 64 K
 constexpr uint32_t kBBytes = 64 * 256 * 2;        // one B plane slice: 64 K x up to 256 columns
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr uint32_t kStgBytes = 128 * 64;                // one 128 x 32 chunk of one 2-byte plane
-constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + hi/lo staging per epilogue group
+constexpr uint32_t kStgBytes = 128 * 64;                // 8 KB; the epilogue's staging is 4 kStgBytes
+constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + two 2 KB hi/lo buffers per epilogue warp
 constexpr int kPlanes = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
 
@@ -198,8 +198,7 @@ __device__ __forceinline__ void xq_row(const uint16_t* __restrict__ xh, const ui
   }
 }
 
-// named barriers: 1 + group for one epilogue group (128 threads), 3 for both groups (256 threads)
-__device__ __forceinline__ void group_bar(int grp) { asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory"); }
+// named barrier 3 for the 256 epilogue threads
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 3, 256;" ::: "memory"); }
 // barrier 3 with an OR over the 256 epilogue threads' predicates
 __device__ __forceinline__ bool epi_bar_or(bool p) {
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc::tc_fence_after();
   const uint32_t tmem = sh.tmem;
   const size_t plane_elems = (size_t)g.R * g.LD;
-  uint8_t* const stg = stage_mem + kStages * kStageBytes;   // per epilogue group: hi, lo chunks of 128 x 32 x 2 B
+  uint8_t* const stg = stage_mem + kStages * kStageBytes;   // epilogue staging: 4 KB per epilogue warp
   const int sub0 = blockIdx.x * kSlots;                      // scratch sub-slot of this CTA's slot 0
   uint32_t arm_phase[kStages] = {0, 0};                      // producer: parity of the last load armed per stage
   bool armed[kStages] = {false, false};
@@ -392,8 +391,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int etid = tid - 128;              // 0..255
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
-    const int gbase = 128 + 128 * grp;       // first thread of this epilogue group (issues its TMA stores)
     uint32_t tcount = 0;
+    uint32_t wsc = 0;                        // staging halves this warp has used
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
     auto start_slot = [&](int s) {
@@ -655,31 +654,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                 reinterpret_cast<uint4*>(dst)[0] = make_uint4(w8[0], w8[1], w8[2], w8[3]);
                 reinterpret_cast<uint4*>(dst)[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
               }
-            } else {
-              // stage the chunk in shared memory (64-byte swizzle: 16-byte unit c of row r sits at
-              // unit c ^ ((r >> 1) & 3)) and write it with TMA tensor stores
-              uint8_t* shi = stg + grp * 2 * kStgBytes;
-              uint8_t* slo = shi + kStgBytes;
-              if (tid == gbase) tc::bulk_wait_read<0>();   // the group's previous store has read the buffer
-              group_bar(grp);
-              if (live) {
-                uint32_t h[16], l[16];
-                split_pack(v, d.fo, h, l);
-                const int lr = 32 * q + lane;
+            } else if (live) {
+              // each warp stores its own 32 rows, in two 16-column halves through two alternating
+              // staging buffers (hi 1 KB, lo 1 KB each; row r at 32 r bytes), with TMA tensor stores issued
+              // by its lane 0: no barrier between warps, and a buffer is reused only when the store from
+              // it two halves earlier has read it
+              uint32_t h[16], l[16];
+              split_pack(v, d.fo, h, l);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                  const int off = lr * 64 + ((c ^ ((lr >> 1) & 3)) << 4);
-                  *reinterpret_cast<uint4*>(shi + off) = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
-                  if (d.fo.terms > 1)
-                    *reinterpret_cast<uint4*>(slo + off) = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+              for (int hf = 0; hf < 2; ++hf) {
+                uint8_t* wb = stg + (size_t)(warp - 4) * 4096 + (wsc & 1) * 2048;
+                if (lane == 0) tc::bulk_wait_read<1>();
+                __syncwarp();
+                uint4* dh = reinterpret_cast<uint4*>(wb + lane * 32);
+                dh[0] = make_uint4(h[8 * hf], h[8 * hf + 1], h[8 * hf + 2], h[8 * hf + 3]);
+                dh[1] = make_uint4(h[8 * hf + 4], h[8 * hf + 5], h[8 * hf + 6], h[8 * hf + 7]);
+                if (d.fo.terms > 1) {
+                  uint4* dl = reinterpret_cast<uint4*>(wb + 1024 + lane * 32);
+                  dl[0] = make_uint4(l[8 * hf], l[8 * hf + 1], l[8 * hf + 2], l[8 * hf + 3]);
+                  dl[1] = make_uint4(l[8 * hf + 4], l[8 * hf + 5], l[8 * hf + 6], l[8 * hf + 7]);
                 }
-              }
-              tc::fence_proxy_async_smem();
-              group_bar(grp);
-              if (tid == gbase && !bad) {
-                tc::tma_store_3d(&mapS, shi, col0, 128 * mb, d.zo);
-                if (d.fo.terms > 1) tc::tma_store_3d(&mapS, slo, col0, 128 * mb, d.zo + 1);
-                tc::bulk_commit();
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                  tc::tma_store_3d(&mapS, wb, col0 + 16 * hf, 128 * mb + 32 * q, d.zo);
+                  if (d.fo.terms > 1) tc::tma_store_3d(&mapS, wb + 1024, col0 + 16 * hf, 128 * mb + 32 * q, d.zo + 1);
+                  tc::bulk_commit();
+                }
+                ++wsc;
               }
             }
           }
@@ -687,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!bad) tc::mbar_arrive(&sh.acce[buf]);
           ++tcount;
         }
-      if (tid == gbase) tc::bulk_wait<0>();   // this product's stores are written before anyone reads them
+      if (lane == 0) tc::bulk_wait<0>();   // this warp's stores are written before anyone reads them
       tc::fence_proxy_async_global();
       // ---- end of the product: one uniform error decision, then the slot's next state
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -883,8 +885,8 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64) ||
-      !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 128,
-                     CU_TENSOR_MAP_SWIZZLE_64B)) {
+      !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 16, 32,
+                     CU_TENSOR_MAP_SWIZZLE_NONE)) {
     set_error("cuTensorMapEncodeTiled rejected the scratch layout (R %d, LD %d, slots %d)", S->R, S->LD, S->slots);
     return NOLSM_ERR_CUDA;
   }
@@ -1045,7 +1047,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64) ||
-      !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 128, CU_TENSOR_MAP_SWIZZLE_64B)) {
+      !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 16, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
     set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
     return NOLSM_ERR_CUDA;
   }
