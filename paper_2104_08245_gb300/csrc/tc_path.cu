@@ -44,7 +44,7 @@ constexpr uint32_t kABytes = 128 * 64 * 2;        // one A plane slice: 128 rows
 constexpr uint32_t kBBytes = 64 * 256 * 2;        // one B plane slice: 64 K x up to 256 columns
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
 constexpr uint32_t kStgBytes = 128 * 64;                // 8 KB; the epilogue's staging is 4 kStgBytes
-constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + two 2 KB hi/lo buffers per epilogue warp
+constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + a 4 KB hi/lo buffer per epilogue warp
 constexpr int kPlanes = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
 
@@ -392,7 +392,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
     uint32_t tcount = 0;
-    uint32_t wsc = 0;                        // staging halves this warp has used
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
     auto start_slot = [&](int s) {
@@ -655,33 +654,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 reinterpret_cast<uint4*>(dst)[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
               }
             } else if (live) {
-              // each warp stores its own 32 rows, in two 16-column halves through two alternating
-              // staging buffers (hi 1 KB, lo 1 KB each; row r at 32 r bytes), with TMA tensor stores issued
-              // by its lane 0: no barrier between warps, and a buffer is reused only when the store from
-              // it two halves earlier has read it
+              // each warp stores its own 32 rows x 32 columns through its own 4 KB staging buffer (hi 2 KB,
+              // lo 2 KB; 64-byte swizzle: 16-byte unit c of row r at unit c ^ ((r >> 1) & 3)), with TMA
+              // tensor stores issued by its lane 0: no barrier between warps, and one store per plane
+              // and chunk (fewer, larger TMA operations measured faster than double-buffered halves)
               uint32_t h[16], l[16];
               split_pack(v, d.fo, h, l);
+              uint8_t* wb = stg + (size_t)(warp - 4) * 4096;
+              if (lane == 0) tc::bulk_wait_read<0>();   // this warp's previous store has read the buffer
+              __syncwarp();
+              uint4* dh = reinterpret_cast<uint4*>(wb + lane * 64);
 #pragma unroll
-              for (int hf = 0; hf < 2; ++hf) {
-                uint8_t* wb = stg + (size_t)(warp - 4) * 4096 + (wsc & 1) * 2048;
-                if (lane == 0) tc::bulk_wait_read<1>();
-                __syncwarp();
-                uint4* dh = reinterpret_cast<uint4*>(wb + lane * 32);
-                dh[0] = make_uint4(h[8 * hf], h[8 * hf + 1], h[8 * hf + 2], h[8 * hf + 3]);
-                dh[1] = make_uint4(h[8 * hf + 4], h[8 * hf + 5], h[8 * hf + 6], h[8 * hf + 7]);
-                if (d.fo.terms > 1) {
-                  uint4* dl = reinterpret_cast<uint4*>(wb + 1024 + lane * 32);
-                  dl[0] = make_uint4(l[8 * hf], l[8 * hf + 1], l[8 * hf + 2], l[8 * hf + 3]);
-                  dl[1] = make_uint4(l[8 * hf + 4], l[8 * hf + 5], l[8 * hf + 6], l[8 * hf + 7]);
-                }
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                  tc::tma_store_3d(&mapS, wb, col0 + 16 * hf, 128 * mb + 32 * q, d.zo);
-                  if (d.fo.terms > 1) tc::tma_store_3d(&mapS, wb + 1024, col0 + 16 * hf, 128 * mb + 32 * q, d.zo + 1);
-                  tc::bulk_commit();
-                }
-                ++wsc;
+              for (int c = 0; c < 4; ++c) dh[c ^ ((lane >> 1) & 3)] = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+              if (d.fo.terms > 1) {
+                uint4* dl = reinterpret_cast<uint4*>(wb + 2048 + lane * 64);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                  dl[c ^ ((lane >> 1) & 3)] = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+              }
+              tc::fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) {
+                tc::tma_store_3d(&mapS, wb, col0, 128 * mb + 32 * q, d.zo);
+                if (d.fo.terms > 1) tc::tma_store_3d(&mapS, wb + 2048, col0, 128 * mb + 32 * q, d.zo + 1);
+                tc::bulk_commit();
               }
             }
           }
@@ -885,8 +881,8 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64) ||
-      !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 16, 32,
-                     CU_TENSOR_MAP_SWIZZLE_NONE)) {
+      !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 32,
+                     CU_TENSOR_MAP_SWIZZLE_64B)) {
     set_error("cuTensorMapEncodeTiled rejected the scratch layout (R %d, LD %d, slots %d)", S->R, S->LD, S->slots);
     return NOLSM_ERR_CUDA;
   }
@@ -1047,7 +1043,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   CUtensorMap mA, mB, mS;
   if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64) ||
-      !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 16, 32, CU_TENSOR_MAP_SWIZZLE_NONE)) {
+      !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B)) {
     set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
     return NOLSM_ERR_CUDA;
   }
