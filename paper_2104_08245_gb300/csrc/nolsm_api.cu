@@ -23,13 +23,42 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+// Workspaces come from the device's default stream-ordered memory pool, which keeps freed memory
+// (release threshold raised once per device) so that a plan built per geometry reuses the previous
+// plan's pages instead of mapping new ones. Allocation and release are made complete before they
+// return, like cudaMalloc and cudaFree, so buffers may be used on any stream.
+static void pool_keep_freed_memory() {
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 nolsm_status dev_alloc(nolsm_plan* plan, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  pool_keep_freed_memory();
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = cudaMallocAsync(&p, bytes, 0);
+  if (e == cudaErrorMemoryAllocation) {   // give the pool's kept pages back to the device and retry once
+    cudaGetLastError();
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      cudaDeviceSynchronize();
+      cudaMemPoolTrimTo(pool, 0);
+    }
+    e = cudaMallocAsync(&p, bytes, 0);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    set_error("cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? NOLSM_ERR_OOM : NOLSM_ERR_CUDA;
   }
   b.p = p;
@@ -40,7 +69,9 @@ nolsm_status dev_alloc(nolsm_plan* plan, DevBuf& b, size_t bytes) {
 
 void dev_free(nolsm_plan* plan, DevBuf& b) {
   if (b.p) {
-    cudaFree(b.p);
+    cudaDeviceSynchronize();   // no work still using the buffer, whatever stream it runs on
+    cudaFreeAsync(b.p, 0);
+    cudaStreamSynchronize(0);
     plan->bytes -= (int64_t)b.bytes;
   }
   b.p = nullptr;
