@@ -215,19 +215,27 @@ __device__ bool cholesky(T* __restrict__ S, int n, T* __restrict__ Ps, T (*Xs)[N
 // pivot column travels by shuffles) and inverts it (X_r = L_11^-1, row by row, each finished row
 // broadcast); then every thread forms rows of L_21 = A_21 X_r^T; the trailing update is the tiled one above.
 // Xs is [NB][NB + 4] (16-byte rows). Same results up to rounding order as cholesky<float>.
-__device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps, float (*Xs)[NB + 4],
-                           int* s_bad) {
+// S64 is the FP64 T_J(S): the first panel and the first trailing update read it (rounded to FP32) in
+// place of S, so S needs no separate FP32 copy of T_J(S) before the factorisation.
+__device__ bool cholesky32(float* __restrict__ S, const double* __restrict__ S64, int n, float* __restrict__ Ps,
+                           float (*Xs)[NB + 4], int* s_bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int LDP = Ld<float>::v;
   for (int k0 = 0; k0 < n; k0 += NB) {
     const int kb = min(NB, n - k0), mt = n - k0;
     // panel rows by warp, lanes along the row, zero beyond kb; the copies are asynchronous, all in flight
-    for (int i = warp; i < mt; i += kThreads / 32) {
-      float* dst = Ps + i * LDP + lane;
-      if (lane < kb) cp_async4(dst, S + (size_t)(k0 + i) * n + k0 + lane);
-      else *dst = 0.0f;
+    if (k0 == 0) {
+#pragma unroll 4
+      for (int i = warp; i < mt; i += kThreads / 32)
+        Ps[i * LDP + lane] = lane < kb ? (float)S64[(size_t)i * n + lane] : 0.0f;
+    } else {
+      for (int i = warp; i < mt; i += kThreads / 32) {
+        float* dst = Ps + i * LDP + lane;
+        if (lane < kb) cp_async4(dst, S + (size_t)(k0 + i) * n + k0 + lane);
+        else *dst = 0.0f;
+      }
+      cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     if (warp == 0) {
       // factor the diagonal block in the panel itself: lane i owns row i (rows beyond kb idle)
@@ -347,7 +355,9 @@ __device__ bool cholesky32(float* __restrict__ S, int n, float* __restrict__ Ps,
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 2; ++b)
-            sv[a][b] = (vi[a] && vj[b] && jj[b] <= ii[a]) ? S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]] : 0.0f;
+            sv[a][b] = !(vi[a] && vj[b] && jj[b] <= ii[a]) ? 0.0f
+                       : k0 == 0 ? (float)S64[(size_t)ii[a] * n + jj[b]]
+                                 : S[(size_t)(k0 + ii[a]) * n + k0 + jj[b]];
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int t = 0; t < kb; t += 4) {
           float4 av[4], bv[2];
@@ -976,10 +986,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   float* L = g.L32 + (g.a_off[J] - g.a_base);
   float (*Acc)[kMaxB + 1] = reinterpret_cast<float (*)[kMaxB + 1]>(Pf);   // solve_cols32 (after the solves)
   if (tid == 0) s_bad = 0;
-  for (int i = warp; i < n; i += kThreads / 32)
-    for (int j = lane; j <= i; j += 32) L[(size_t)i * n + j] = (float)S[(size_t)i * n + j];
   __syncthreads();
-  bool ok = cholesky32(L, n, Pf, Xs, &s_bad);
+  bool ok = cholesky32(L, S, n, Pf, Xs, &s_bad);
   if (ok) {
     // A_J = L^-T L^-1 T_J(H0) in FP32, and the FP32 first solve of Q when its b columns fit in the
     // last column batch
