@@ -909,14 +909,27 @@ template <typename TA>
 __device__ void gershgorin(const TA* __restrict__ A, int n, double* lam, float* rlo, float* rhi) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float lo = INFINITY, hi = -INFINITY;
-  for (int i = warp; i < n; i += kThreads / 32) {   // one warp per row, lanes along it
-    const TA* Ai = A + (size_t)i * n;
-    float r = 0.0f;
-    for (int j = lane; j < n; j += 32) r += j != i ? fabsf((float)Ai[j]) : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    const float d = (float)Ai[i];
-    lo = fminf(lo, d - r);
-    hi = fmaxf(hi, d + r);
+  for (int i0 = 4 * warp; i0 < n; i0 += 4 * (kThreads / 32)) {   // four rows per warp pass, lanes along them
+    float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int j = lane; j < n; j += 32) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        if (i < n && j != i) r[u] += fabsf((float)A[(size_t)i * n + j]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      for (int o = 16; o > 0; o >>= 1) r[u] += __shfl_xor_sync(0xffffffffu, r[u], o);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u;
+      if (i < n) {
+        const float d = (float)A[(size_t)i * n + i];
+        lo = fminf(lo, d - r[u]);
+        hi = fmaxf(hi, d + r[u]);
+      }
+    }
   }
   rlo[threadIdx.x] = lo;
   rhi[threadIdx.x] = hi;
