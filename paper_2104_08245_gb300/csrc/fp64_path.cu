@@ -380,7 +380,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
   }
   int max_nq = 1;
   for (int64_t J = j0; J < j1; ++J) max_nq = std::max(max_nq, plan->h_nb_ptr[J + 1] - plan->h_nb_ptr[J]);
-  const int64_t budget = (int64_t)1 << 31;  // bytes of gathered T_J(S), T_J(H0) per chunk
+  const int64_t budget = (int64_t)1 << 34;  // bytes of gathered T_J(S), T_J(H0) per chunk (16 GB of the 288)
   int64_t J = j0;
   while (J < j1) {
     while (J < j1 && P.done[J]) ++J;
@@ -440,6 +440,17 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       pa.Qp = plan->ws_refine.as<float2>();
       pa.W32 = reinterpret_cast<float*>(pa.Qp + std::max<int64_t>(nbc, 1));
       pa.fallback_max_n = sym ? 0 : prepare_fp64_max_n();   // no FP64 fallback for the symmetric form
+      {   // CTAs take the chunk's submatrices largest first, so that the last wave is made of small ones
+        std::vector<int32_t> ord((size_t)(e - J));
+        for (int64_t k = J; k < e; ++k) ord[(size_t)(k - J)] = (int32_t)k;
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int32_t a, int32_t b) { return plan->h_sub_n[a] > plan->h_sub_n[b]; });
+        NOLSM_TRY(ensure(plan, plan->prep_order, sizeof(int32_t) * ord.size()));
+        NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->prep_order.p, ord.data(), sizeof(int32_t) * ord.size(),
+                                       cudaMemcpyHostToDevice, st));
+        NOLSM_CUDA_TRY(cudaStreamSynchronize(st));   // ord is a host temporary
+        pa.order = plan->prep_order.as<int32_t>();
+      }
       NOLSM_TRY(launch_prepare_mixed(pa, (int)(e - J), chunk_max_n, P.A.as<float>(), st));
       plan->stats.launches += 3;
     }

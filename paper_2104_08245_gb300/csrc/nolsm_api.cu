@@ -126,7 +126,7 @@ using namespace nolsm;
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &Lsym, &Wc, &Dc,
-                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &ws_ns,
+                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
                    &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);

@@ -107,6 +107,7 @@ struct nolsm_plan {
   nolsm::DevBuf ws_dense;           // gathered T_J(S), T_J(H0) of one preparation chunk (FP64)
   nolsm::DevBuf ws_l32;             // FP32 factors of one preparation chunk (low-precision paths)
   nolsm::DevBuf ws_refine;          // q as FP32 pairs and FP32 corrections of Q for one chunk
+  nolsm::DevBuf prep_order;         // submatrices of one chunk, largest first (mixed preparation)
   nolsm::DevBuf ws_ysym;            // L^-1 T_J(H0) of one preparation chunk (symmetric form)
   nolsm::DevBuf ws_ns;              // per-CTA Newton-Schulz buffers (FP64 path)
   void* tc = nullptr;               // tensor-core path state (tc_path.cu)

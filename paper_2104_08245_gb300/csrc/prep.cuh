@@ -6,6 +6,7 @@ namespace nolsm {
 
 struct PrepArgs {
   int32_t j0;                 // first submatrix of the chunk (one CTA per submatrix)
+  const int32_t* order = nullptr;   // mixed preparation: CTA -> submatrix, largest first (null: j0 + CTA)
   const int32_t* sub_n; const int32_t* sub_c0; const int32_t* nbf;
   const int64_t* a_off; const int64_t* c_off;
   int64_t a_base;             // a_off of the chunk's first submatrix

@@ -990,7 +990,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   __shared__ float red_d[kThreads / 32];
   __shared__ double red_q[kThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int J = g.j0 + blockIdx.x;
+  const int J = g.order ? g.order[blockIdx.x] : g.j0 + (int)blockIdx.x;   // largest submatrices first
   const int n = g.sub_n[J];
   const int bJ = g.nbf[J];
   const int c0 = g.sub_c0[J];
