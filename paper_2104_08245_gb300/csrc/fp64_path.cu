@@ -33,10 +33,10 @@ __device__ __forceinline__ int find_sorted(const int32_t* __restrict__ a, int lo
 }
 
 // ------------------------------------------------------------------------------------ a1: gather
-// One block per row band (J, a): rows of molecule I_a inside T_J. For every molecule I_c of N(J) the
-// block (I_a, I_c) of S and of H0 is looked up by binary search in block row I_a; the band is written
-// in full (zeros where no block is stored), so the workspace needs no clearing. Also writes the centre
-// columns of T_J(S) and T_J(H0) into the geometry caches.
+// One warp per row band (J, a): rows of molecule I_a inside T_J, eight bands per block. For every
+// molecule I_c of N(J) the block (I_a, I_c) of S and of H0 is looked up by binary search in block row
+// I_a; the band is written in full (zeros where no block is stored), so the workspace needs no clearing.
+// Also writes the centre columns of T_J(S) and T_J(H0) into the geometry caches.
 struct GatherArgs {
   int32_t n_mol;
   const int32_t* nbf;
@@ -47,57 +47,57 @@ struct GatherArgs {
   const int64_t* a_off; const int64_t* c_off;
   int64_t a_base;       // a_off of the chunk's first submatrix
   int64_t chunk_n2;     // sum of n^2 over the chunk (offset of the T(H0) half)
-  int64_t p0;           // first row band of the chunk
+  int64_t p0, p1;       // row bands [p0, p1) of the chunk
+  int32_t max_nq;       // largest |N(J)|: each warp's lookup tables hold 3 max_nq ints
   double* ws;           // [2*chunk_n2]
   double* Sc; double* Hc;
 };
 
-__global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
+constexpr int kGatherWarps = 8;
+
+__global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
   extern __shared__ int32_t sm[];
-  const int64_t p = g.p0 + blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t p = g.p0 + (int64_t)blockIdx.x * kGatherWarps + w;
+  if (p >= g.p1) return;   // whole warps only; no block-wide barrier follows
   const int J = owner_of(g.nb_ptr, g.n_mol, p);
   const int q0 = g.nb_ptr[J], nq = g.nb_ptr[J + 1] - q0;
   const int Ia = g.nb_idx[p];
   const int ba = g.nbf[Ia];
   const int offa = g.nb_off[p];
   const int n = g.sub_n[J];
-  int32_t* s_slot = sm;
-  int32_t* h_slot = sm + nq;
-  int32_t* coff = sm + 2 * nq;
-  for (int c = threadIdx.x; c < nq; c += blockDim.x) {
+  int32_t* s_slot = sm + w * 3 * g.max_nq;
+  int32_t* h_slot = s_slot + nq;
+  int32_t* coff = s_slot + 2 * nq;
+  for (int c = lane; c < nq; c += 32) {
     const int32_t Ic = g.nb_idx[q0 + c];
     s_slot[c] = find_sorted(g.sci, g.srp[Ia], g.srp[Ia + 1], Ic);
     h_slot[c] = find_sorted(g.hci, g.hrp[Ia], g.hrp[Ia + 1], Ic);
     coff[c] = g.nb_off[q0 + c];
   }
-  __syncthreads();
+  __syncwarp();
   const int c0 = g.sub_c0[J];
   const int bJ = g.nbf[J];
   double* TS = g.ws + (g.a_off[J] - g.a_base);
   double* TH = TS + g.chunk_n2;
   double* Sc = g.Sc + g.c_off[J];
   double* Hc = g.Hc + g.c_off[J];
-  const int total = ba * n;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int r = e / n, col = e - r * n;
-    // molecule block containing col: largest c with coff[c] <= col
-    int lo = 0, hi = nq;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (coff[mid] <= col) lo = mid; else hi = mid;
-    }
-    const int c = lo;
-    const int bc = g.nbf[g.nb_idx[q0 + c]];
-    const int cc = col - coff[c];
-    const int ss = s_slot[c], hs = h_slot[c];
-    const double vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
-    const double vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
-    const int64_t at = (int64_t)(offa + r) * n + col;
-    TS[at] = vs;
-    TH[at] = vh;
-    if (col >= c0 && col < c0 + bJ) {
-      Sc[(int64_t)(offa + r) * bJ + (col - c0)] = vs;
-      Hc[(int64_t)(offa + r) * bJ + (col - c0)] = vh;
+  for (int r = 0; r < ba; ++r) {
+    int c = 0;   // molecule block of column col; columns advance by 32, blocks by at least one function
+    for (int col = lane; col < n; col += 32) {
+      while (c + 1 < nq && coff[c + 1] <= col) ++c;
+      const int bc = g.nbf[g.nb_idx[q0 + c]];
+      const int cc = col - coff[c];
+      const int ss = s_slot[c], hs = h_slot[c];
+      const double vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
+      const double vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
+      const int64_t at = (int64_t)(offa + r) * n + col;
+      TS[at] = vs;
+      TH[at] = vh;
+      if (col >= c0 && col < c0 + bJ) {
+        Sc[(int64_t)(offa + r) * bJ + (col - c0)] = vs;
+        Hc[(int64_t)(offa + r) * bJ + (col - c0)] = vh;
+      }
     }
   }
 }
@@ -407,8 +407,12 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     g.ws = plan->ws_dense.as<double>();
     g.Sc = plan->Sc.as<double>(); g.Hc = plan->Hc.as<double>();
     const int64_t bands = plan->h_nb_ptr[e] - plan->h_nb_ptr[J];
+    g.p1 = plan->h_nb_ptr[e];
+    g.max_nq = max_nq;
     pmark(plan, st);
-    k_gather<<<(unsigned)bands, 256, sizeof(int32_t) * 3 * max_nq, st>>>(g);
+    const size_t gsm = sizeof(int32_t) * 3 * kGatherWarps * (size_t)max_nq;
+    if (gsm > 48 * 1024) NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    k_gather<<<(unsigned)((bands + kGatherWarps - 1) / kGatherWarps), 32 * kGatherWarps, gsm, st>>>(g);
     NOLSM_LAUNCH_CHECK();
     pmark(plan, st);
     PrepArgs pa;
