@@ -767,10 +767,18 @@ __device__ void forward_cols32(const float* __restrict__ L, int n, int b, float*
     const int r0 = rbk * NB, rb = min(NB, n - r0);
     for (int e = tid; e < rb * b; e += kThreads) {
       const int i = e / b, c = e - i * b;
-      float s = W[(size_t)(r0 + i) * b + c];
       const float* Li = L + (size_t)(r0 + i) * n;
-      for (int q = 0; q < r0; ++q) s = fmaf(-Li[q], W[(size_t)q * b + c], s);
-      Acc[i][c] = s;
+      // four independent partial sums (the FMA chain is the latency bound here)
+      float s0 = W[(size_t)(r0 + i) * b + c], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+      int q = 0;
+      for (; q + 4 <= r0; q += 4) {
+        s0 = fmaf(-Li[q], W[(size_t)q * b + c], s0);
+        s1 = fmaf(-Li[q + 1], W[(size_t)(q + 1) * b + c], s1);
+        s2 = fmaf(-Li[q + 2], W[(size_t)(q + 2) * b + c], s2);
+        s3 = fmaf(-Li[q + 3], W[(size_t)(q + 3) * b + c], s3);
+      }
+      for (; q < r0; ++q) s0 = fmaf(-Li[q], W[(size_t)q * b + c], s0);
+      Acc[i][c] = (s0 + s1) + (s2 + s3);
     }
     for (int e = tid; e < NB * NB; e += kThreads) {
       const int a = e >> 5, t = e & 31;
@@ -796,9 +804,17 @@ __device__ void backward_cols32(const float* __restrict__ L, int n, int b, float
     const int r0 = rbk * NB, rb = min(NB, n - r0);
     for (int e = tid; e < rb * b; e += kThreads) {
       const int i = e / b, c = e - i * b;
-      float s = W[(size_t)(r0 + i) * b + c];
-      for (int q = r0 + rb; q < n; ++q) s = fmaf(-L[(size_t)q * n + r0 + i], W[(size_t)q * b + c], s);
-      Acc[i][c] = s;
+      // four independent partial sums (the FMA chain is the latency bound here)
+      float s0 = W[(size_t)(r0 + i) * b + c], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+      int q = r0 + rb;
+      for (; q + 4 <= n; q += 4) {
+        s0 = fmaf(-L[(size_t)q * n + r0 + i], W[(size_t)q * b + c], s0);
+        s1 = fmaf(-L[(size_t)(q + 1) * n + r0 + i], W[(size_t)(q + 1) * b + c], s1);
+        s2 = fmaf(-L[(size_t)(q + 2) * n + r0 + i], W[(size_t)(q + 2) * b + c], s2);
+        s3 = fmaf(-L[(size_t)(q + 3) * n + r0 + i], W[(size_t)(q + 3) * b + c], s3);
+      }
+      for (; q < n; ++q) s0 = fmaf(-L[(size_t)q * n + r0 + i], W[(size_t)q * b + c], s0);
+      Acc[i][c] = (s0 + s1) + (s2 + s3);
     }
     for (int e = tid; e < NB * NB; e += kThreads) {
       const int a = e >> 5, t = e & 31;
