@@ -201,15 +201,17 @@ def test_submatrices_larger_than_one_tile(nl):
 
 def test_full_size_sampled(nl):
     """32,768 molecules with the density field, every submatrix in one launch (the benchmark's
-    launch configuration); 48 sampled submatrices against the oracle."""
+    launch configuration); 512 sampled submatrices (the smallest and largest among them) against the
+    oracle."""
     from synth import spec_batched_uneven
     sysm = make_system(spec_batched_uneven())
     mu = -0.1
     plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
     po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
     rng = np.random.default_rng(7)
-    subs = sorted(int(j) for j in rng.choice(sysm.n_mol, size=48, replace=False))
-    subs += [int(np.argmax(po.sub_n)), int(np.argmin(po.sub_n))]
+    subs = set(int(j) for j in rng.choice(sysm.n_mol, size=510, replace=False))
+    subs |= {int(np.argmax(po.sub_n)), int(np.argmin(po.sub_n))}
+    subs = sorted(subs)
     ref = orc.solve(sysm, mu, subs=subs, plan=po)
     for prec in ("fp32", "bf16x3", "fp16"):
         r = nl.nolsm_solve_batch(plan, mu, nl.options(prec))
@@ -264,3 +266,48 @@ def test_symmetric_form_full_size_sampled(nl):
     print(f"symmetric form, 4096 molecules: sampled max|dD| = {err:.3e}")
     assert err <= TOL["fp32"]
     assert np.all(r.sub_status.cpu().numpy() == 0)
+
+
+def test_split_valence_sampled(nl):
+    """512 molecules with 23 functions each: n = 598..713, so five or six row blocks, three column tiles,
+    up to twelve K slices, the ping-pong X planes, and three column groups of b in the centre-column
+    phase. mu from the GPU bisection; 6 sampled submatrices against the oracle at that mu in the FP32,
+    BF16X3 and E4M3 modes."""
+    sysm = make_system(SystemSpec(8, 8, 8, nbf="23", seed=1104))
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    m = plan.find_mu(float(np.sum(sysm.occ)), 0.0, 0.0, nl.options("fp32"))
+    rng = np.random.default_rng(11)
+    subs = sorted({int(np.argmin(po.sub_n)), int(np.argmax(po.sub_n))} |
+                  set(int(j) for j in rng.choice(sysm.n_mol, size=4, replace=False)))
+    ref = orc.solve(sysm, m.mu, subs=subs, plan=po)
+    n_max = int(po.sub_n.max())
+    for prec, tol in (("fp32", 1e-6 * np.sqrt(n_max / 300.0)), ("bf16x3", 1e-4), ("fp8e4m3", 1e-1)):
+        r = nl.nolsm_solve_batch(plan, m.mu, nl.options(prec))
+        D = plan.scatter().cpu().numpy()
+        err = d_error(po, ref, D, subs)
+        it = r.iters.cpu().numpy()
+        print(f"23 functions, n {po.sub_n.min()}..{n_max}, mu {m.mu:.4f}: {prec} sampled max|dD| = {err:.3e}, "
+              f"steps {it.min()}..{it.max()}")
+        assert err <= tol
+        assert np.all(r.sub_status.cpu().numpy() == 0)
+
+
+def test_submatrix_ranges_are_bit_identical_on_tensor_path(nl):
+    """Solving the system in two ranges (the streamed configuration's batches) gives, submatrix by
+    submatrix, the same bits as one solve of every submatrix: each submatrix's arithmetic does not depend
+    on the launch that carries it."""
+    from synth import spec_batched_uneven_4096
+    sysm = make_system(spec_batched_uneven_4096())
+    mu = -0.35
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    nl.nolsm_solve_batch(plan, mu, nl.options("bf16x3"))
+    D_all = plan.scatter().cpu().numpy()
+    plan2 = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    half = sysm.n_mol // 2 + 7
+    D_rng = None
+    for j0, j1 in ((0, half), (half, sysm.n_mol)):   # each range written back after its solve
+        r = nl.nolsm_solve_batch(plan2, mu, nl.options("bf16x3", sub_begin=j0, sub_end=j1))
+        assert r.status == 0
+        D_rng = plan2.scatter(D_rng)
+    assert np.array_equal(D_all, D_rng.cpu().numpy())
