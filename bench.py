@@ -449,7 +449,8 @@ def main():
                     "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
                     "traffic": kernel_traffic("k_prepare_mixed", n_mol / chunks), "launches_per_step": chunks,
                     "peak_source": "FP32 SIMT peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                    "algorithmic": "FP32 flops 2 (n^3/3 + 2 n^3 + 4 n^2 b) per submatrix"}
+                    "algorithmic": "FP32 flops 2 (n^3/3 + n^3 + 3 n^2 b) per submatrix: Cholesky, the two "
+                                   "triangular solves for A, the Q solve, its residual and correction"}
     else:
         roofline = roof_sign
 

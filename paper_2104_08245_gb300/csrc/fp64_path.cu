@@ -464,14 +464,13 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
       // algorithmic flops (2 per FMA): Cholesky m^3/3 FMAs; two triangular solves with m right-hand sides
       // m^3 FMAs (A = L^-T L^-1 H, or M = L^-1 (L^-1 H)^T); the Q solves m^2 b FMAs each (FP64 path: one;
-      // mixed: the first solve and one correction, plus m^2 b / 2 for W_c in the symmetric form); the FP64
-      // residual of the refinement m^2 b FMAs
+      // mixed: the first solve and one correction, plus m^2 b / 2 for W_c in the symmetric form); the
+      // residual of the refinement m^2 b FMAs (counted once, not its double-FP32 emulation)
       const double fma_fact = m * m * m / 3.0 + m * m * m;
       if (keep_fp64_A) {
         plan->stats.flops_fp64 += 2.0 * (fma_fact + m * m * b);
       } else {
-        plan->stats.flops_fp32 += 2.0 * (fma_fact + (sym ? 2.5 : 2.0) * m * m * b);
-        plan->stats.flops_fp64 += 2.0 * m * m * b;
+        plan->stats.flops_fp32 += 2.0 * (fma_fact + (sym ? 3.5 : 3.0) * m * m * b);
       }
       P.done[k] = 1;
     }
