@@ -326,7 +326,13 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    sysm = synth.make_system(getattr(synth, spec_name)())
+    # weak scaling: with N ranks the lattice is N times longer along x and rank r owns the r-th slab of
+    # the one-GPU workload's size (molecule index runs fastest along z, slowest along x)
+    spec = getattr(synth, spec_name)()
+    if world > 1:
+        import dataclasses
+        spec = dataclasses.replace(spec, nx=spec.nx * world)
+    sysm = synth.make_system(spec)
     n_mol = sysm.n_mol
     n_occ = sysm.n_occ
     peaks = measured_peaks()
@@ -539,7 +545,8 @@ def main():
         "dtype": {"fp64": "f64", "fp32": "fp16x3", "bf16x3": "bf16x3", "bf16": "bf16", "fp16": "fp16"}.get(args.precision,
                                                                                            args.precision),
         "data": "synthetic",
-        "config": {"workload": desc, "precision": args.precision, "molecules": n_mol,
+        "config": {"workload": desc if world == 1 else f"{desc}; lattice {world}x longer along x, one slab per GPU",
+                   "precision": args.precision, "molecules": n_mol, "molecules_per_gpu": n_mol // world,
                    "l2": "inputs larger than L2 (block-CSR S and H, %.0f MB each)" % (sysm.S.vals.nbytes / 1e6),
                    "bracket": "Gershgorin interval of all submatrices"},
         "e2e": {"value": n_mol / (ms_e2e / 1e3), "unit": "submatrices/s", "h2d_bytes_per_step": h2d,
