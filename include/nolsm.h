@@ -128,7 +128,12 @@ typedef struct {
  * max_bisect 100, Gershgorin bounds, all submatrices. */
 void nolsm_options_default(nolsm_options* opts, int32_t precision);
 
-typedef struct nolsm_plan nolsm_plan; /* opaque; owns all device workspaces */
+/* A plan owns all its device workspaces. They come from the device's default stream-ordered memory pool
+ * (cudaMallocAsync), whose release threshold the library raises once per device so that freed pages
+ * stay in the pool for the next plan (a plan per geometry then maps no new pages); allocations and
+ * releases complete before the calls return. If an allocation fails, the pool is trimmed and the
+ * allocation retried once. */
+typedef struct nolsm_plan nolsm_plan; /* opaque */
 
 typedef struct {
   int32_t n_mol;       /* = number of submatrices */
