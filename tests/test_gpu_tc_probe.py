@@ -6,7 +6,6 @@ import ctypes
 import os
 import subprocess
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu

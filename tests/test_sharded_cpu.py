@@ -9,7 +9,7 @@ import pytest
 import torch.multiprocessing as mp
 
 from oracle import nolsm_oracle as orc
-from synth import spec_tiny, make_system, SystemSpec
+from synth import make_system, SystemSpec
 
 
 def _free_port():
