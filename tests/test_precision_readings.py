@@ -1,0 +1,92 @@
+"""CPU checks of the precision readings the tensor-core modes rest on (no GPU).
+
+1. E4M3 iterates (3 mantissa bits, operands scaled by 2^7) hold the Newton-Schulz defect
+   ||I - X^2||_F / sqrt(n) at a floor of a few hundredths, so the E4M3 phase must end on its own test
+   (a defect of 0.1, or a defect that stops halving) rather than on tol_ns = 1e-2; the exact iteration
+   from the same start converges quadratically past that point.
+2. A rounding error made in a late step persists in D: the Frechet derivative of the sign at an
+   involution S is E -> (E - S E S) / 2, the identity on the part of E that anticommutes with S.
+The E4M3 rounding is PyTorch's float8_e4m3fn conversion (round to nearest even, 448 the largest normal),
+the matrices a submatrix of the 64-molecule system in its symmetric form."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import nolsm_oracle as orc
+from synth import make_system, spec_small_fp64
+
+
+def _e4m3(x):
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn in this PyTorch")
+    return torch.from_numpy(x * 128.0).to(torch.float8_e4m3fn).to(torch.float64).numpy() / 128.0
+
+
+def _symmetric_start(J=0, mu=-0.1):
+    sysm = make_system(spec_small_fp64())
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    S = orc.gather(po, J, sysm.S.row_ptr, sysm.S.col_idx, sysm.S.blk_off, sysm.S.vals)
+    H = orc.gather(po, J, sysm.H.row_ptr, sysm.H.col_idx, sysm.H.blk_off, sysm.H.vals)
+    L = np.linalg.cholesky(S)
+    Li = scipy.linalg.solve_triangular(L, np.eye(len(S)), lower=True)
+    M = Li @ H @ Li.T
+    M = 0.5 * (M + M.T)
+    n = len(M)
+    A = M - mu * np.eye(n)
+    alpha = np.max(np.abs(np.linalg.eigvalsh(A))) * 1.3   # a bound above the spectral radius
+    return A / alpha
+
+
+def _defect(X):
+    n = len(X)
+    return np.linalg.norm(np.eye(n) - X @ X) / np.sqrt(n)
+
+
+def test_e4m3_defect_floor_and_exact_convergence():
+    X0 = _symmetric_start()
+    n = len(X0)
+    Xq, Xe = _e4m3(X0), X0.copy()
+    dq, de = [], []
+    for _ in range(10):
+        dq.append(_defect(Xq))
+        de.append(_defect(Xe))
+        Tq = _e4m3(3.0 * np.eye(n) - Xq @ Xq)
+        Xq = _e4m3(0.5 * Xq @ Tq)
+        Xe = 0.5 * Xe @ (3.0 * np.eye(n) - Xe @ Xe)
+    floor = min(dq)
+    assert 0.01 < floor < 0.1          # the E4M3 phase cannot reach tol_ns = 1e-2 ...
+    assert min(de) < 1e-12             # ... while the exact iteration converges
+    # once the defect is below 0.25 the exact iteration at least halves it every step; E4M3 stops doing so
+    late = [i for i in range(1, len(dq)) if dq[i - 1] < 0.25]
+    assert any(dq[i] > 0.5 * dq[i - 1] for i in late)
+    assert all(de[i] <= 0.5 * de[i - 1] for i in range(1, len(de)) if de[i - 1] < 0.25 and de[i - 1] > 1e-14)
+
+
+def test_sign_derivative_keeps_anticommuting_errors():
+    X0 = _symmetric_start()
+    w, V = np.linalg.eigh(X0)
+    S = V @ np.diag(np.sign(w)) @ V.T                 # sign(X0), an involution
+    rng = np.random.default_rng(3)
+    E = rng.standard_normal(S.shape)
+    E = 0.5 * (E + E.T)
+    E_anti = 0.5 * (E - S @ E @ S)                    # the part anticommuting with S
+    E_comm = E - E_anti
+    eps = 1e-6
+
+    def sign_of(Y):
+        w2, V2 = np.linalg.eigh(Y)
+        return V2 @ np.diag(np.sign(w2)) @ V2.T
+
+    def ns(Y, steps=60):                              # Newton-Schulz from Y (converges to sign(Y))
+        for _ in range(steps):
+            Y = 0.5 * Y @ (3.0 * np.eye(len(Y)) - Y @ Y)
+        return Y
+
+    # started at S + eps E, the iteration keeps the anticommuting part and removes the commuting one
+    Ya = ns(S + eps * E_anti)
+    Yc = ns(S + eps * E_comm)
+    assert np.linalg.norm(Ya - S - eps * E_anti) < 1e-3 * eps * np.linalg.norm(E_anti)
+    assert np.linalg.norm(Yc - S) < 1e-3 * eps * np.linalg.norm(E_comm)
+    # and the limit is the sign of the perturbed matrix, to first order the same
+    assert np.linalg.norm(Ya - sign_of(S + eps * E_anti)) < 1e-3 * eps * np.linalg.norm(E_anti)
