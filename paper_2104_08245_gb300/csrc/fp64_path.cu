@@ -186,6 +186,7 @@ struct NsArgs {
   double* ws; int64_t slot_elems;
   int32_t* next;               // work counter
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
+  int32_t* nbelow;             // eigenvalues below mu: (n - Tr X) / 2
 };
 
 __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
@@ -263,8 +264,11 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
       ps += d * Sc[e];
       ph += d * Hc[e];
     }
+    double px = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) px += x[(int64_t)i * n + i];
     const double ts = block_sum(ps, red);
     const double th = block_sum(ph, red);
+    const double tx = block_sum(px, red);
     if (threadIdx.x == 0) {
       if (st == kSubOk && !(isfinite(ts) && isfinite(th))) st = kSubNonFinite;
       g.tS[J] = ts;
@@ -272,6 +276,7 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
       g.iters[J] = it;
       g.rsteps[J] = 0;
       g.status[J] = st;
+      g.nbelow[J] = (int32_t)lrint(0.5 * (n - tx));
     }
     __syncthreads();
   }
@@ -489,6 +494,7 @@ nolsm_status ensure_results(nolsm_plan* plan) {
     NOLSM_TRY(dev_alloc(plan, plan->status, sizeof(int32_t) * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->sums, sizeof(double) * 8));
     NOLSM_TRY(dev_alloc(plan, plan->rsteps, sizeof(int32_t) * n_mol));
+    NOLSM_TRY(dev_alloc(plan, plan->nbelow, sizeof(int32_t) * n_mol));
     NOLSM_TRY(dev_alloc(plan, plan->counter, sizeof(int32_t) * 4));
   }
   return NOLSM_OK;
@@ -523,6 +529,7 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
   g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
+  g.nbelow = plan->nbelow.as<int32_t>();
   k_ns_fp64<<<slots, 256, 0, st>>>(g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;

@@ -126,7 +126,7 @@ using namespace nolsm;
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &Lsym, &Wc, &Dc,
-                   &t_S, &t_H, &iters, &status, &rsteps, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
+                   &t_S, &t_H, &iters, &status, &rsteps, &nbelow, &nb_lo, &nb_hi, &active, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
                    &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
@@ -266,14 +266,13 @@ static nolsm_status bound_spec(nolsm_plan* plan, int source, double mu, const no
   return NOLSM_OK;
 }
 
-nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
-                               double* trace_DS, double* trace_DH, double* sub_t_S, double* sub_t_H,
-                               int32_t* iters, int32_t* status) {
-  if (!plan) { set_error("nolsm_solve_batch: NULL plan"); return NOLSM_ERR_ARG; }
-  if (!std::isfinite(mu)) { set_error("nolsm_solve_batch: mu is not finite"); return NOLSM_ERR_ARG; }
+// The solve of nolsm_solve_batch, restricted to the device list[0, count) of submatrices of the range
+// when `list` is set (the others keep their previous results; the trace sums cover the whole range).
+static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options* opts, cudaStream_t st,
+                               const int32_t* list, int32_t count, double* trace_DS, double* trace_DH,
+                               double* sub_t_S, double* sub_t_H, int32_t* iters, int32_t* status) {
   int64_t j0, j1;
   NOLSM_TRY(check_options(plan, opts, &j0, &j1));
-  cudaStream_t st = (cudaStream_t)stream;
   NOLSM_TRY(ensure_results(plan));
   const bool fp64 = opts->precision == NOLSM_FP64;
   const int cls = prep_class(*opts);
@@ -282,6 +281,10 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   int level = opts->bound_source;
   SolveSpec spec;
   NOLSM_TRY(bound_spec(plan, level, mu, *opts, cls, j0, j1, st, &spec));
+  if (list) {
+    spec.list = list;
+    spec.count = count;
+  }
   mark(plan, 1, st);
   NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, spec, st) : solve_tc(plan, mu, *opts, j0, j1, spec, st));
   // submatrices that failed the convergence test under learned bounds are solved again with power
@@ -319,7 +322,7 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
   plan->stats.ms_sign += elapsed(plan, 1, 2);
   plan->stats.ms_reduce += elapsed(plan, 2, 3);
   plan->stats.solves += 1;
-  plan->stats.sub_solves += j1 - j0;
+  plan->stats.sub_solves += list ? count : j1 - j0;
   if (trace_DS) *trace_DS = tS;
   if (trace_DH) *trace_DH = tH;
   plan->solved_begin = j0;
@@ -330,6 +333,47 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
     return (nolsm_status)bad;
   }
   return NOLSM_OK;
+}
+
+nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                               double* trace_DS, double* trace_DH, double* sub_t_S, double* sub_t_H,
+                               int32_t* iters, int32_t* status) {
+  if (!plan) { set_error("nolsm_solve_batch: NULL plan"); return NOLSM_ERR_ARG; }
+  if (!std::isfinite(mu)) { set_error("nolsm_solve_batch: mu is not finite"); return NOLSM_ERR_ARG; }
+  return solve_impl(plan, mu, opts, (cudaStream_t)stream, nullptr, 0, trace_DS, trace_DH, sub_t_S, sub_t_H, iters,
+                    status);
+}
+
+static nolsm_status ensure_dev(nolsm_plan* plan, DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return NOLSM_OK;
+  dev_free(plan, b);
+  return dev_alloc(plan, b, bytes);
+}
+
+// a9 support. n_below(J, mu) = (n - Tr sign(A_J - mu I)) / 2 counts the eigenvalues of submatrix J below mu;
+// where it is equal at both ends of the bracket, no eigenvalue of J lies inside, T_J(D) is the same for
+// every mu in the bracket, and J needs no further solve: its centre columns and traces stay valid.
+__global__ void k_bracket_init(int32_t j0, int32_t j1, const int32_t* __restrict__ sub_n, int known,
+                               int32_t* __restrict__ nb_lo, int32_t* __restrict__ nb_hi) {
+  for (int32_t J = j0 + blockIdx.x * blockDim.x + threadIdx.x; J < j1; J += gridDim.x * blockDim.x) {
+    nb_lo[J] = known ? 0 : -1;            // the default bracket contains every submatrix's spectrum
+    nb_hi[J] = known ? sub_n[J] : -1;
+  }
+}
+
+__global__ void k_active_list(int32_t j0, int32_t j1, const int32_t* __restrict__ nb_lo,
+                              const int32_t* __restrict__ nb_hi, int32_t* __restrict__ list, int32_t* __restrict__ count) {
+  for (int32_t J = j0 + blockIdx.x * blockDim.x + threadIdx.x; J < j1; J += gridDim.x * blockDim.x)
+    if (nb_lo[J] < 0 || nb_hi[J] < 0 || nb_lo[J] != nb_hi[J]) list[atomicAdd(count, 1)] = J;
+}
+
+__global__ void k_bracket_update(int32_t j0, int32_t j1, const int32_t* __restrict__ list, int32_t count,
+                                 const int32_t* __restrict__ nbelow, int32_t* __restrict__ nb_side) {
+  const int32_t m = list ? count : j1 - j0;
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    const int32_t J = list ? list[e] : j0 + e;
+    nb_side[J] = nbelow[J];
+  }
 }
 
 nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream) {
@@ -384,21 +428,57 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
     set_error("nolsm_find_mu: invalid arguments");
     return NOLSM_ERR_ARG;
   }
-  if (!(lo < hi)) {
+  const bool default_bracket = !(lo < hi);
+  if (default_bracket) {
     NOLSM_TRY(nolsm_spectral_bracket(plan, opts, stream, &lo, &hi));
   }
   const int max_steps = opts->max_bisect > 0 ? opts->max_bisect : 100;
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  const size_t nm = (size_t)plan->n_mol;
+  NOLSM_TRY(ensure_dev(plan, plan->nb_lo, sizeof(int32_t) * nm));
+  NOLSM_TRY(ensure_dev(plan, plan->nb_hi, sizeof(int32_t) * nm));
+  NOLSM_TRY(ensure_dev(plan, plan->active, sizeof(int32_t) * (nm + 1)));
+  int32_t* nb_lo = plan->nb_lo.as<int32_t>();
+  int32_t* nb_hi = plan->nb_hi.as<int32_t>();
+  int32_t* act = plan->active.as<int32_t>();
+  int32_t* act_count = act + nm;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (j1 - j0 + 255) / 256));
+  k_bracket_init<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->sub_n.as<int32_t>(), default_bracket ? 1 : 0,
+                                         nb_lo, nb_hi);
+  NOLSM_LAUNCH_CHECK();
   double mu = 0.5 * (lo + hi), t = 0.0;
   nolsm_status result = NOLSM_ERR_NO_PLATEAU;
   int step = 0;
   while (step < max_steps) {
     mu = 0.5 * (lo + hi);
-    nolsm_status s = nolsm_solve_batch(plan, mu, opts, stream, &t, nullptr, nullptr, nullptr, nullptr, nullptr);
+    // the submatrices with an eigenvalue in [lo, hi] (all of them at the first point)
+    const int32_t* list = nullptr;
+    int32_t count = (int32_t)(j1 - j0);
+    if (step > 0) {
+      NOLSM_CUDA_TRY(cudaMemsetAsync(act_count, 0, sizeof(int32_t), st));
+      k_active_list<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, nb_lo, nb_hi, act, act_count);
+      NOLSM_LAUNCH_CHECK();
+      NOLSM_CUDA_TRY(cudaMemcpyAsync(&count, act_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+      list = act;
+    }
+    nolsm_status s = NOLSM_OK;
+    if (count > 0) {
+      s = solve_impl(plan, mu, opts, st, list, count, &t, nullptr, nullptr, nullptr, nullptr, nullptr);
+    }   // else no submatrix changes inside the bracket: Tr(DS) is the last point's
     if (mu_history) mu_history[step] = mu;
     ++step;
     if (s != NOLSM_OK) { result = s; break; }
     const double f = t - n_occ;
     if (std::fabs(f) <= opts->tol_n * std::fabs(n_occ)) { result = NOLSM_OK; break; }
+    if (count > 0) {
+      k_bracket_update<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, list, count, plan->nbelow.as<int32_t>(),
+                                               f < 0.0 ? nb_lo : nb_hi);
+      NOLSM_LAUNCH_CHECK();
+    }
     if (f < 0.0) lo = mu; else hi = mu;
     if (hi - lo <= opts->tol_mu) break;
   }

@@ -98,6 +98,9 @@ struct nolsm_plan {
   nolsm::DevBuf t_S, t_H;           // float64 [n_mol]
   nolsm::DevBuf iters, status;      // int32 [n_mol]
   nolsm::DevBuf rsteps;             // int32 [n_mol]: steps taken in the refinement format
+  nolsm::DevBuf nbelow;             // int32 [n_mol]: eigenvalues below mu, (n - Tr sign) / 2 of the last solve
+  nolsm::DevBuf nb_lo, nb_hi;       // int32 [n_mol]: the same at the ends of find_mu's bracket (-1: unknown)
+  nolsm::DevBuf active;             // int32 [n_mol]: find_mu's submatrices with an eigenvalue in the bracket
   nolsm::DevBuf sums;               // float64 [4]
   nolsm::DevBuf counter;            // int32 work counters of persistent kernels
   int64_t solved_begin = 0, solved_end = 0;

@@ -83,6 +83,7 @@ struct TcArgs {
   int32_t* next;              // work counter
   int32_t* err;               // global error flag (timeouts)
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
+  int32_t* nbelow;            // eigenvalues below mu, (n - Tr X) / 2 (nullable)
 };
 
 constexpr int kSlots = 2;   // submatrices in flight per CTA (their products interleave)
@@ -118,7 +119,7 @@ struct Shared {
   SlotState slot[kSlots];
   Desc ring[kRing];
   float red[2][8];               // defect partial sums, by product parity
-  double dred[2][8];
+  double dred[3][8];
 };
 
 __device__ __forceinline__ float from_bits(uint16_t b, int fmt) {
@@ -561,21 +562,31 @@ __global__ void __launch_bounds__(kThreads, 1)
           ph += dv * Hc[e];
         }
       }
+      double px = 0.0;   // the trace of the final X: (n - Tr X) / 2 eigenvalues lie below mu
+      for (int i = etid; i < n; i += 256) {
+        float x = from_bits(xh[(size_t)i * g.LD + i], xfmt.fmt);
+        if (xfmt.terms > 1) x += from_bits(xl[(size_t)i * g.LD + i], xfmt.fmt);
+        px += x;
+      }
       for (int o = 16; o > 0; o >>= 1) {
         ps += __shfl_xor_sync(0xffffffffu, ps, o);
         ph += __shfl_xor_sync(0xffffffffu, ph, o);
+        px += __shfl_xor_sync(0xffffffffu, px, o);
       }
       if (lane == 0) {
         sh.dred[0][warp - 4] = ps;
         sh.dred[1][warp - 4] = ph;
+        sh.dred[2][warp - 4] = px;
       }
       epi_bar();
       if (tid == 128) {
-        double ts = 0.0, th = 0.0;
+        double ts = 0.0, th = 0.0, tx = 0.0;
         for (int w = 0; w < 8; ++w) {
           ts += sh.dred[0][w];
           th += sh.dred[1][w];
+          tx += sh.dred[2][w];
         }
+        if (g.nbelow) g.nbelow[J] = (int32_t)lrint(0.5 * (n - tx));
         int stt = st.status;
         if (stt == kSubOk && !(isfinite(ts) && isfinite(th))) stt = kSubNonFinite;
         g.tS[J] = ts;
@@ -918,6 +929,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.Dc = plan->Dc.as<double>(); g.tS = plan->t_S.as<double>(); g.tH = plan->t_H.as<double>();
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
+  g.nbelow = plan->nbelow.as<int32_t>();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   // one-byte views of the same planes (rows of 2 LD bytes) for E4M3 operands, both loaded K-major
   CUtensorMap mA8, mB8;
@@ -1066,6 +1078,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.err = ints + 3 * kNaMaxSub + 32;
   g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
   g.rsteps = ints + 2 * kNaMaxSub;
+  g.nbelow = nullptr;
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   k_ns_tc<<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
   NOLSM_LAUNCH_CHECK();
