@@ -311,3 +311,29 @@ def test_submatrix_ranges_are_bit_identical_on_tensor_path(nl):
         assert r.status == 0
         D_rng = plan2.scatter(D_rng)
     assert np.array_equal(D_all, D_rng.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-6)])
+def test_find_mu_solves_only_bracketed_submatrices(nl, prec, tol):
+    """A system without a common gap (6 and 23 functions mixed) makes the bisection take many points;
+    from the second one on, only submatrices with an eigenvalue left in the bracket are solved. At the
+    final mu the density is as close to the oracle's as a solve of every submatrix at that mu (kept
+    blocks come from an earlier mu of the same bracket, where the same D holds)."""
+    sysm = make_system(VARIANTS["mixed_nbf"])
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    plan.stats_reset()
+    m = plan.find_mu(float(sysm.n_occ), 0.0, 0.0, nl.options(prec))
+    solved = plan.stats()["sub_solves"]
+    D = plan.scatter().cpu().numpy()
+    plan2 = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    r = nl.nolsm_solve_batch(plan2, m.mu, nl.options(prec), check=False)
+    D2 = plan2.scatter().cpu().numpy()
+    ref = orc.solve(sysm, m.mu)
+    e_kept = float(np.max(np.abs(D - ref.D_vals)))
+    e_fresh = float(np.max(np.abs(D2 - ref.D_vals)))
+    print(f"{prec}: {m.steps} bisection points, {solved} submatrix solves of {m.steps * sysm.n_mol}; "
+          f"max|dD| {e_kept:.3e} (kept blocks) vs {e_fresh:.3e} (every block solved at the final mu)")
+    assert m.steps > 2
+    assert solved < m.steps * sysm.n_mol
+    assert e_kept <= e_fresh + tol
+    assert abs(m.trace_DS - ref.trace_DS) <= abs(r.trace_DS - ref.trace_DS) + tol * sysm.n_mol
