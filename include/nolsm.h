@@ -197,6 +197,25 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
                            nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
                            double* mu_history);
 
+/* The bisection of nolsm_find_mu one point at a time, for callers that drive it themselves (several
+ * ranks summing Tr(DS) per point). Each point solves only the submatrices that can change inside the
+ * bracket: a submatrix whose count of eigenvalues below mu, (n - Tr sign(A_J - mu I)) / 2, is the same
+ * at both ends of the bracket has no eigenvalue inside, so its centre columns and traces from its last
+ * solve hold for every mu in the bracket.
+ * nolsm_bisect_begin: starts a bisection over the options' range; bracket_contains_spectrum = 1 when
+ *   the bracket holds every eigenvalue of every submatrix of the range (then the counts at its ends are
+ *   0 and n; a Gershgorin bracket from nolsm_spectral_bracket does), 0 when unknown.
+ * nolsm_bisect_point: one point mu (inside the current bracket): solves the submatrices that can change
+ *   (all of them at the first point) and returns Tr(DS) over the range (host) and how many submatrices
+ *   it solved (host, may be NULL). The plan keeps the solution for nolsm_scatter_density.
+ * nolsm_bisect_side: after a point, records that it becomes the bracket's lower end (raises_lo = 1, when
+ *   Tr(DS) summed over all ranks is below n_occ) or its upper end (0). */
+nolsm_status nolsm_bisect_begin(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream,
+                                int32_t bracket_contains_spectrum);
+nolsm_status nolsm_bisect_point(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                                double* trace_DS, int32_t* solved);
+nolsm_status nolsm_bisect_side(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, int32_t raises_lo);
+
 /* The union [lo, hi] of the Gershgorin intervals of A_J = T_J(S)^-1 T_J(H0) over the options' range
  * of submatrices (prepares a1-a3 for the range first): a bracket of every submatrix eigenvalue, used
  * as the default bisection bracket (Sec. "Simulation Details" gives no bracket). lo, hi: host. */

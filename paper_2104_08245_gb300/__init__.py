@@ -133,6 +133,29 @@ def nolsm_spectral_bracket(plan: "Plan", opts: NolsmOptions, stream=None):
     return lo.value, hi.value
 
 
+def nolsm_bisect_begin(plan: "Plan", opts: NolsmOptions, bracket_contains_spectrum: bool, stream=None) -> None:
+    rc = _abi.load().nolsm_bisect_begin(plan.handle, ctypes.byref(opts), _stream(stream),
+                                        1 if bracket_contains_spectrum else 0)
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_bisect_begin")
+
+
+def nolsm_bisect_point(plan: "Plan", mu: float, opts: NolsmOptions, stream=None, check: bool = True):
+    """One bisection point: (status, Tr(DS) over the options' range, submatrices solved)."""
+    t, solved = ctypes.c_double(), ctypes.c_int32()
+    rc = _abi.load().nolsm_bisect_point(plan.handle, float(mu), ctypes.byref(opts), _stream(stream),
+                                        ctypes.byref(t), ctypes.byref(solved))
+    if rc in (_abi.ERR_ARG, _abi.ERR_CUDA, _abi.ERR_OOM, _abi.ERR_UNSUPPORTED) or (check and rc != 0):
+        raise NolsmError(rc, "nolsm_bisect_point")
+    return rc, t.value, solved.value
+
+
+def nolsm_bisect_side(plan: "Plan", opts: NolsmOptions, raises_lo: bool, stream=None) -> None:
+    rc = _abi.load().nolsm_bisect_side(plan.handle, ctypes.byref(opts), _stream(stream), 1 if raises_lo else 0)
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_bisect_side")
+
+
 def nolsm_plan_stats(plan: "Plan") -> dict:
     st = NolsmStats()
     rc = _abi.load().nolsm_plan_stats(plan.handle, ctypes.byref(st))

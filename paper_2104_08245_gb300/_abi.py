@@ -63,6 +63,10 @@ SIGNATURES = [
                                 ctypes.POINTER(c_double)]),
     ("nolsm_spectral_bracket", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p,
                                          ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    ("nolsm_bisect_begin", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_int32]),
+    ("nolsm_bisect_point", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
+                                     ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
+    ("nolsm_bisect_side", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_int32]),
     ("nolsm_plan_stats", c_int32, [c_void_p, ctypes.POINTER(NolsmStats)]),
     ("nolsm_plan_stats_reset", c_int32, [c_void_p]),
     ("nolsm_plan_destroy", None, [c_void_p]),

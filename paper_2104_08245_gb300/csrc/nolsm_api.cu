@@ -421,6 +421,85 @@ nolsm_status nolsm_spectral_bracket(nolsm_plan* plan, const nolsm_options* opts,
   return NOLSM_OK;
 }
 
+// The bisection's per-point state lives in the plan: counts of eigenvalues below mu at the bracket's
+// ends (nb_lo, nb_hi; -1 unknown), the count of the last point (nbelow) and its work list.
+nolsm_status nolsm_bisect_begin(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream,
+                                int32_t bracket_contains_spectrum) {
+  if (!plan || !opts) { set_error("nolsm_bisect_begin: NULL argument"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  const size_t nm = (size_t)plan->n_mol;
+  NOLSM_TRY(ensure_dev(plan, plan->nb_lo, sizeof(int32_t) * nm));
+  NOLSM_TRY(ensure_dev(plan, plan->nb_hi, sizeof(int32_t) * nm));
+  NOLSM_TRY(ensure_dev(plan, plan->active, sizeof(int32_t) * (nm + 1)));
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (j1 - j0 + 255) / 256));
+  k_bracket_init<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->sub_n.as<int32_t>(),
+                                         bracket_contains_spectrum ? 1 : 0, plan->nb_lo.as<int32_t>(),
+                                         plan->nb_hi.as<int32_t>());
+  NOLSM_LAUNCH_CHECK();
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  plan->bisect_first = true;
+  plan->bisect_count = -1;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_bisect_point(nolsm_plan* plan, double mu, const nolsm_options* opts, nolsm_stream_t stream,
+                                double* trace_DS, int32_t* solved) {
+  if (!plan || !opts || !std::isfinite(mu)) { set_error("nolsm_bisect_point: invalid argument"); return NOLSM_ERR_ARG; }
+  if (!plan->nb_lo.p) { set_error("nolsm_bisect_point: no nolsm_bisect_begin"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nm = (size_t)plan->n_mol;
+  int32_t* act = plan->active.as<int32_t>();
+  const int32_t* list = nullptr;
+  int32_t count = (int32_t)(j1 - j0);
+  if (!plan->bisect_first) {   // the submatrices with an eigenvalue in the bracket (all at the first point)
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (j1 - j0 + 255) / 256));
+    NOLSM_CUDA_TRY(cudaMemsetAsync(act + nm, 0, sizeof(int32_t), st));
+    k_active_list<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->nb_lo.as<int32_t>(), plan->nb_hi.as<int32_t>(),
+                                          act, act + nm);
+    NOLSM_LAUNCH_CHECK();
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(&count, act + nm, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+    list = act;
+  }
+  plan->bisect_first = false;
+  plan->bisect_count = count;
+  plan->bisect_listed = list != nullptr;
+  if (solved) *solved = count;
+  if (count == 0) {   // no submatrix changes inside the bracket: Tr(DS) is the last point's
+    if (trace_DS) *trace_DS = plan->bisect_trace;
+    return NOLSM_OK;
+  }
+  double t = 0.0;
+  nolsm_status s = solve_impl(plan, mu, opts, st, list, count, &t, nullptr, nullptr, nullptr, nullptr, nullptr);
+  plan->bisect_trace = t;
+  if (trace_DS) *trace_DS = t;
+  return s;
+}
+
+nolsm_status nolsm_bisect_side(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, int32_t raises_lo) {
+  if (!plan || !opts) { set_error("nolsm_bisect_side: NULL argument"); return NOLSM_ERR_ARG; }
+  if (plan->bisect_count < 0) { set_error("nolsm_bisect_side: no nolsm_bisect_point"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->bisect_count > 0) {
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (j1 - j0 + 255) / 256));
+    k_bracket_update<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1,
+                                             plan->bisect_listed ? plan->active.as<int32_t>() : nullptr,
+                                             plan->bisect_count, plan->nbelow.as<int32_t>(),
+                                             raises_lo ? plan->nb_lo.as<int32_t>() : plan->nb_hi.as<int32_t>());
+    NOLSM_LAUNCH_CHECK();
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  plan->bisect_count = -1;
+  return NOLSM_OK;
+}
+
 nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
                            nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
                            double* mu_history) {
@@ -433,52 +512,19 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
     NOLSM_TRY(nolsm_spectral_bracket(plan, opts, stream, &lo, &hi));
   }
   const int max_steps = opts->max_bisect > 0 ? opts->max_bisect : 100;
-  int64_t j0, j1;
-  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
-  cudaStream_t st = (cudaStream_t)stream;
-  NOLSM_TRY(ensure_results(plan));
-  const size_t nm = (size_t)plan->n_mol;
-  NOLSM_TRY(ensure_dev(plan, plan->nb_lo, sizeof(int32_t) * nm));
-  NOLSM_TRY(ensure_dev(plan, plan->nb_hi, sizeof(int32_t) * nm));
-  NOLSM_TRY(ensure_dev(plan, plan->active, sizeof(int32_t) * (nm + 1)));
-  int32_t* nb_lo = plan->nb_lo.as<int32_t>();
-  int32_t* nb_hi = plan->nb_hi.as<int32_t>();
-  int32_t* act = plan->active.as<int32_t>();
-  int32_t* act_count = act + nm;
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, (j1 - j0 + 255) / 256));
-  k_bracket_init<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->sub_n.as<int32_t>(), default_bracket ? 1 : 0,
-                                         nb_lo, nb_hi);
-  NOLSM_LAUNCH_CHECK();
+  NOLSM_TRY(nolsm_bisect_begin(plan, opts, stream, default_bracket ? 1 : 0));
   double mu = 0.5 * (lo + hi), t = 0.0;
   nolsm_status result = NOLSM_ERR_NO_PLATEAU;
   int step = 0;
   while (step < max_steps) {
     mu = 0.5 * (lo + hi);
-    // the submatrices with an eigenvalue in [lo, hi] (all of them at the first point)
-    const int32_t* list = nullptr;
-    int32_t count = (int32_t)(j1 - j0);
-    if (step > 0) {
-      NOLSM_CUDA_TRY(cudaMemsetAsync(act_count, 0, sizeof(int32_t), st));
-      k_active_list<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, nb_lo, nb_hi, act, act_count);
-      NOLSM_LAUNCH_CHECK();
-      NOLSM_CUDA_TRY(cudaMemcpyAsync(&count, act_count, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
-      list = act;
-    }
-    nolsm_status s = NOLSM_OK;
-    if (count > 0) {
-      s = solve_impl(plan, mu, opts, st, list, count, &t, nullptr, nullptr, nullptr, nullptr, nullptr);
-    }   // else no submatrix changes inside the bracket: Tr(DS) is the last point's
+    nolsm_status s = nolsm_bisect_point(plan, mu, opts, stream, &t, nullptr);
     if (mu_history) mu_history[step] = mu;
     ++step;
     if (s != NOLSM_OK) { result = s; break; }
     const double f = t - n_occ;
     if (std::fabs(f) <= opts->tol_n * std::fabs(n_occ)) { result = NOLSM_OK; break; }
-    if (count > 0) {
-      k_bracket_update<<<blocks, 256, 0, st>>>((int32_t)j0, (int32_t)j1, list, count, plan->nbelow.as<int32_t>(),
-                                               f < 0.0 ? nb_lo : nb_hi);
-      NOLSM_LAUNCH_CHECK();
-    }
+    NOLSM_TRY(nolsm_bisect_side(plan, opts, stream, f < 0.0 ? 1 : 0));
     if (f < 0.0) lo = mu; else hi = mu;
     if (hi - lo <= opts->tol_mu) break;
   }

@@ -101,6 +101,10 @@ struct nolsm_plan {
   nolsm::DevBuf nbelow;             // int32 [n_mol]: eigenvalues below mu, (n - Tr sign) / 2 of the last solve
   nolsm::DevBuf nb_lo, nb_hi;       // int32 [n_mol]: the same at the ends of find_mu's bracket (-1: unknown)
   nolsm::DevBuf active;             // int32 [n_mol]: find_mu's submatrices with an eigenvalue in the bracket
+  bool bisect_first = true;         // the next bisection point is the first (solves every submatrix)
+  bool bisect_listed = false;       // the last point solved the work list (else the whole range)
+  int32_t bisect_count = -1;        // submatrices the last point solved (-1: no point since the last side)
+  double bisect_trace = 0.0;        // Tr(DS) of the last point
   nolsm::DevBuf sums;               // float64 [4]
   nolsm::DevBuf counter;            // int32 work counters of persistent kernels
   int64_t solved_begin = 0, solved_end = 0;

@@ -10,7 +10,7 @@ max_bisect points. The bracket is the union of the ranks' spectral brackets.
 from __future__ import annotations
 
 import dataclasses
-from typing import Callable, Tuple
+from typing import Callable, Optional, Tuple
 
 
 @dataclasses.dataclass
@@ -23,8 +23,10 @@ class ShardedMu:
 
 
 def bisect_allreduce(count_local: Callable[[float], float], bracket_local: Tuple[float, float], n_occ: float,
-                     tol_n: float, tol_mu: float, max_steps: int, group=None) -> ShardedMu:
-    """The bisection with the partial counts summed over the process group (FP64 all-reduce)."""
+                     tol_n: float, tol_mu: float, max_steps: int, group=None,
+                     side_local: Optional[Callable[[bool], None]] = None) -> ShardedMu:
+    """The bisection with the partial counts summed over the process group (FP64 all-reduce);
+    side_local(raises_lo) is told which end of the bracket each point becomes."""
     import torch
     import torch.distributed as dist
 
@@ -46,6 +48,8 @@ def bisect_allreduce(count_local: Callable[[float], float], bracket_local: Tuple
         if abs(f) <= tol_n * abs(n_occ):
             status = 0
             break
+        if side_local is not None:
+            side_local(f < 0.0)
         if f < 0.0:
             lo = mu
         else:
@@ -56,12 +60,18 @@ def bisect_allreduce(count_local: Callable[[float], float], bracket_local: Tuple
 
 
 def sharded_find_mu(plan, n_occ: float, opts, group=None) -> ShardedMu:
-    """nolsm_find_mu for a plan whose options select this rank's range of submatrices."""
+    """nolsm_find_mu for a plan whose options select this rank's range of submatrices: each point
+    solves only the rank's submatrices with an eigenvalue left in the bracket (the union of the ranks'
+    Gershgorin brackets holds every eigenvalue, so the counts at its ends are known)."""
     import paper_2104_08245_gb300 as nl
     lo, hi = nl.nolsm_spectral_bracket(plan, opts)
+    nl.nolsm_bisect_begin(plan, opts, True)
 
     def count(mu):
-        return nl.nolsm_solve_batch(plan, mu, opts, per_sub=False).trace_DS
+        return nl.nolsm_bisect_point(plan, mu, opts)[1]
+
+    def side(raises_lo):
+        nl.nolsm_bisect_side(plan, opts, raises_lo)
 
     return bisect_allreduce(count, (lo, hi), n_occ, opts.tol_n, opts.tol_mu,
-                            opts.max_bisect if opts.max_bisect > 0 else 100, group)
+                            opts.max_bisect if opts.max_bisect > 0 else 100, group, side)

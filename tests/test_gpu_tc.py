@@ -337,3 +337,32 @@ def test_find_mu_solves_only_bracketed_submatrices(nl, prec, tol):
     assert solved < m.steps * sysm.n_mol
     assert e_kept <= e_fresh + tol
     assert abs(m.trace_DS - ref.trace_DS) <= abs(r.trace_DS - ref.trace_DS) + tol * sysm.n_mol
+
+
+def test_sharded_bisection_with_one_rank_matches_find_mu(nl):
+    """The point-by-point bisection API (begin / point / side) driven by the multi-rank loop of
+    sharded.py on a one-rank gloo group takes the same points, mu and Tr(DS) as nolsm_find_mu, and solves
+    as few submatrices."""
+    import torch.distributed as dist
+    from paper_2104_08245_gb300.sharded import sharded_find_mu
+    sysm = make_system(VARIANTS["mixed_nbf"])
+    opts = nl.options("fp64")
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    plan.stats_reset()
+    m = plan.find_mu(float(sysm.n_occ), 0.0, 0.0, opts)
+    solved_single = plan.stats()["sub_solves"]
+    D = plan.scatter().cpu().numpy()
+    plan2 = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    plan2.stats_reset()
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:29531", rank=0, world_size=1)
+    try:
+        r = sharded_find_mu(plan2, float(sysm.n_occ), opts)
+    finally:
+        dist.destroy_process_group()
+    solved_sharded = plan2.stats()["sub_solves"]
+    D2 = plan2.scatter().cpu().numpy()
+    print(f"{r.steps} points; solves {solved_sharded} (sharded loop) vs {solved_single} (find_mu)")
+    assert r.history == m.history
+    assert r.mu == m.mu and r.trace_DS == m.trace_DS
+    assert solved_sharded == solved_single
+    assert np.array_equal(D, D2)
