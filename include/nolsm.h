@@ -187,7 +187,8 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
 nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream);
 
 /* a9: chemical potential by bisection (Sec. "Simulation Details"): f(mu) = Tr(DS) - n_occ with
- * Tr(DS) from nolsm_solve_batch over the options' range; mu = (lo+hi)/2; f < 0 raises lo, otherwise
+ * Tr(DS) over the options' range (a point solves only the submatrices with an eigenvalue left in the
+ * bracket, see nolsm_bisect_point); mu = (lo+hi)/2; f < 0 raises lo, otherwise
  * hi is lowered; stops at the first |f| <= tol_n * n_occ (NOLSM_OK), when hi - lo <= tol_mu
  * (NOLSM_ERR_NO_PLATEAU) or after max_bisect evaluations (NOLSM_ERR_NO_PLATEAU). If lo >= hi the
  * bracket is the union of the Gershgorin intervals of all A_J in the range (prepared first). The plan
