@@ -16,6 +16,9 @@ method (NOLSM) in float64, in the order the paper gives the steps:
 * write-back of the centre molecule's columns into the sparse D            (Sec. "The Submatrix
   Method", step (iii); columns of one molecule coalesced, Sec. "Simulation Details");
 * E_elec = Tr(D H0) = sum_ij D_ij H0_ji and the electron count Tr(D S)     (Eq. e_elec);
+* the energy-weighted density matrix W = D H0 D, in submatrix form
+  T_J(W) = T_J(D) T_J(H0) T_J(D), its centre columns written back like D  (NOLSM section, the
+  equation after Eq. e_elec and its submatrix form after Eq. purification_submatrix);
 * the chemical potential by bisection on the electron count               (Sec. "Simulation Details").
 
 Readings of points the paper leaves open (each one also listed in the design notes):
@@ -207,6 +210,44 @@ def solve(system, mu: float, subs: Optional[Sequence[int]] = None, tol: float = 
     return OracleResult(plan, out, tS, tH, D_vals)
 
 
+@dataclasses.dataclass
+class WResult:
+    W_cols: dict           # J -> centre columns of T_J(W), n_J x b_J
+    t_S: dict              # J -> sum over centre columns j and rows i of T_J(W)_ij T_J(S)_ij
+    trace_WS: float        # sum of t_S over the submatrices
+    W_vals: Optional[np.ndarray]   # W in the merged pattern of D, or None for a subset
+
+
+def submatrix_energy_weighted(D_sub: np.ndarray, H_sub: np.ndarray) -> np.ndarray:
+    """T_J(W) = T_J(D) T_J(H0) T_J(D) (NOLSM section, energy-weighted density matrix in submatrix
+    form), as the two products the definition names."""
+    return (D_sub @ H_sub) @ D_sub
+
+
+def energy_weighted(system, res: OracleResult) -> WResult:
+    """T_J(W) of every submatrix of an oracle solve, from its full T_J(D); the centre columns are
+    written back into the merged pattern as for D (when ``res`` covers the whole system).
+    Tr(W S) = Tr(D H0 D S) = Tr(D H0) for the full matrices when D S D = D, so the traces sum to an
+    approximation of E_elec (Eq. e_elec)."""
+    plan = res.plan
+    cols, tS = {}, {}
+    total = 0.0
+    for J, r in res.subs.items():
+        S_sub = gather(plan, J, system.S.row_ptr, system.S.col_idx, system.S.blk_off, system.S.vals)
+        H_sub = gather(plan, J, system.H.row_ptr, system.H.col_idx, system.H.blk_off, system.H.vals)
+        W = submatrix_energy_weighted(r.D_sub, H_sub)
+        c0, b = int(plan.sub_c0[J]), int(plan.nbf[J])
+        cols[J] = W[:, c0:c0 + b].copy()
+        t = 0.0
+        for j in range(c0, c0 + b):
+            for i in range(W.shape[0]):
+                t += W[i, j] * S_sub[i, j]
+        tS[J] = t
+        total += t
+    W_vals = write_back_cols(plan, cols) if res.D_vals is not None else None
+    return WResult(cols, tS, total, W_vals)
+
+
 def d_block_offsets(plan: OraclePlan) -> np.ndarray:
     """Element offsets of the blocks of D stored in the merged pattern, block row I = N(I) in order,
     block (I, J) b_I x b_J row-major."""
@@ -220,14 +261,19 @@ def d_block_offsets(plan: OraclePlan) -> np.ndarray:
 def write_back(plan: OraclePlan, subs: dict) -> np.ndarray:
     """Column block J of D <- the centre columns of T_J(D), placed on the rows of N(J)
     (Sec. "The Submatrix Method", step (iii))."""
+    return write_back_cols(plan, {J: r.D_cols for J, r in subs.items()})
+
+
+def write_back_cols(plan: OraclePlan, cols: dict) -> np.ndarray:
+    """The write-back of ``write_back`` for any per-submatrix centre columns (J -> n_J x b_J array):
+    block (I, J) of the result, for I in N(J), is the rows of I in J's columns."""
     off = d_block_offsets(plan)
     D = np.zeros(int(off[-1]), dtype=np.float64)
-    for J, r in subs.items():
-        bJ = int(plan.nbf[J])
+    for J, C in cols.items():
         for p in range(int(plan.nb_ptr[J]), int(plan.nb_ptr[J + 1])):
             I = int(plan.nb_idx[p])
             bI = int(plan.nbf[I])
-            rows = r.D_cols[int(plan.nb_off[p]):int(plan.nb_off[p]) + bI, :]
+            rows = C[int(plan.nb_off[p]):int(plan.nb_off[p]) + bI, :]
             # slot of block (I, J) in block row I
             q = int(plan.nb_ptr[I]) + int(np.nonzero(plan.nb_idx[plan.nb_ptr[I]:plan.nb_ptr[I + 1]] == J)[0][0])
             D[off[q]:off[q + 1]] = rows.reshape(-1)
