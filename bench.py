@@ -493,6 +493,34 @@ def main():
             paths[prec]["_D"] = plan.scatter().cpu().numpy()
         plan.close()
 
+    # energy-weighted density matrix T_J(W) = T_J(D) T_J(H0) T_J(D) at mu* (once per geometry, after the
+    # bisection; not part of the timed step): the kernel alone, timed by the library's CUDA events
+    energy_weighted = {}
+    if not args.no_extra and not fp64_path:
+        plan = nl.nolsm_build_submatrices(dsys)
+        nl.nolsm_solve_batch(plan, mu_star, opts, check=False)
+        W = torch.zeros(info.d_nvals, dtype=torch.float64, device=dev)
+        plan.energy_weighted(W)
+        plan.stats_reset()
+        reps = 5
+        for _ in range(reps):
+            _, tw = plan.energy_weighted(W)
+        ms_ew = plan.stats()["ms_energy_weighted"] / reps
+        sub_n = plan.maps()["sub_n"].cpu().numpy().astype(np.float64)[j0:j1]
+        nbf = sysm.nbf.astype(np.float64)[j0:j1]
+        bytes_ew = float(np.sum(sub_n * sub_n * 4.0 + 3.0 * sub_n * nbf * 8.0))
+        ach_ew = bytes_ew / (ms_ew / 1e3) / 1e9 if ms_ew > 0 else 0.0
+        energy_weighted = {
+            "ms_kernel": ms_ew, "trace_WS": tw,
+            "roofline": {"bound": "hbm", "kernel": "k_energy_weighted (W_c = A_J D_c)", "achieved": ach_ew,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": ach_ew / peaks["hbm_gbs"] if peaks["hbm_gbs"] else None,
+                         "traffic": kernel_traffic("k_energy_weighted", j1 - j0),
+                         "peak_source": peaks["source"] + " HBM copy bandwidth",
+                         "algorithmic": "FP32 A_J read once (n^2 x 4 B), D_c and the centre columns of "
+                                        "T_J(S) read and W_c written (3 n b x 8 B) per submatrix"}}
+        plan.close()
+
     bounds = {}
     if not args.no_extra and not fp64_path:
         bounds = bound_sources_leg(nl, synth, spec_name, dsys, mu_star, args.precision, dev)
@@ -561,6 +589,7 @@ def main():
         "extra": extra,
         "paths_one_mu": paths,
         "bound_sources": bounds,
+        "energy_weighted": energy_weighted,
     }
     print(json.dumps(line), flush=True)
     return 0

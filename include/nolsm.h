@@ -186,6 +186,21 @@ nolsm_status nolsm_solve_batch(nolsm_plan* plan, double mu, const nolsm_options*
  * nolsm_plan_get_maps); blocks of submatrices outside the last solved range are left untouched. */
 nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_stream_t stream);
 
+/* Energy-weighted density matrix (NOLSM section: W = D H0 D, for the Pulay forces; submatrix form
+ * T_J(W) = T_J(D) T_J(H0) T_J(D)) for the submatrices of the most recent solve (nolsm_solve_batch,
+ * nolsm_bisect_point or nolsm_find_mu), at the solution the plan holds. The centre columns are
+ * evaluated as W_c = A_J D_c with A_J = T_J(S)^-1 T_J(H0): the projector 1/2 (I - sign(A_J - mu I)) commutes
+ * with A_J and is idempotent, so T_J(D) T_J(H0) T_J(D) = A_J T_J(D). The FP64 path multiplies in FP64; the
+ * tensor-core paths multiply their FP32 A_J by D_c rounded to FP32 with FP32 accumulation.
+ *   W_vals (device, float64 [d_nvals], may be NULL): block (I, J) of W, for I in N(J), set to the rows of I
+ *     in the centre columns of T_J(W), laid out like D (nolsm_scatter_density); blocks of submatrices
+ *     outside the last solved range are left untouched.
+ *   trace_WS (host, may be NULL): sum over J of sum_{j centre, i} T_J(W)_ij T_J(S)_ij, the submatrix
+ *     approximation of Tr(W S) = Tr(D H0) (Eq. e_elec) for the full matrices.
+ * NOLSM_ERR_NO_SOLUTION before any solve; NOLSM_ERR_UNSUPPORTED when the last solve used the symmetric
+ * form (NOLSM_FP8E4M3 or symmetric_form = 1), which does not keep A_J. Synchronises the stream. */
+nolsm_status nolsm_energy_weighted(nolsm_plan* plan, nolsm_stream_t stream, double* W_vals, double* trace_WS);
+
 /* a9: chemical potential by bisection (Sec. "Simulation Details"): f(mu) = Tr(DS) - n_occ with
  * Tr(DS) over the options' range (a point solves only the submatrices with an eigenvalue left in the
  * bracket, see nolsm_bisect_point); mu = (lo+hi)/2; f < 0 raises lo, otherwise
@@ -246,6 +261,7 @@ typedef struct {
   double ms_factor;            /* a2-a3 factorisation and solve kernels alone (part of ms_prepare) */
   double flops_fp32;           /* FP32 flops of the low-precision paths' factorisation and solves */
   int64_t factor_launches;     /* preparation chunks (one factorisation kernel launch each) */
+  double ms_energy_weighted;   /* the centre columns of T_J(W) (nolsm_energy_weighted), kernel alone */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);

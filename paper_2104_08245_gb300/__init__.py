@@ -15,7 +15,7 @@ from . import _abi
 from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP16, FP32, FP64,  # noqa: F401
                    PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmStats, NolsmSystem)
 
-__all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
+__all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density", "nolsm_energy_weighted",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
            "nolsm_spectral_bracket", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
            "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
@@ -214,6 +214,20 @@ def nolsm_scatter_density(plan: "Plan", D_vals=None, stream=None):
     return D_vals
 
 
+def nolsm_energy_weighted(plan: "Plan", W_vals=None, stream=None):
+    """(W in the merged pattern of D, sum of the T_J(W) T_J(S) partial traces) at the plan's solution;
+    W_vals=False skips the write-back (trace only)."""
+    torch = _torch()
+    if W_vals is None:
+        W_vals = torch.zeros(nolsm_plan_query(plan).d_nvals, dtype=torch.float64, device=plan.dsys.nbf.device)
+    tw = ctypes.c_double()
+    rc = _abi.load().nolsm_energy_weighted(plan.handle, _stream(stream), W_vals.data_ptr() if W_vals is not False
+                                           else None, ctypes.byref(tw))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_energy_weighted")
+    return (W_vals if W_vals is not False else None), tw.value
+
+
 @dataclasses.dataclass
 class MuResult:
     status: int
@@ -269,6 +283,9 @@ class Plan:
 
     def find_mu(self, n_occ, lo, hi, opts, **kw):
         return nolsm_find_mu(self, n_occ, lo, hi, opts, **kw)
+
+    def energy_weighted(self, W_vals=None, stream=None):
+        return nolsm_energy_weighted(self, W_vals, stream)
 
     def stats(self):
         return nolsm_plan_stats(self)

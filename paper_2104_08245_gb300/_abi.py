@@ -41,7 +41,8 @@ class NolsmStats(ctypes.Structure):
                 ("ms_scatter", c_double), ("solves", c_int64), ("sub_solves", c_int64), ("ns_steps", c_int64),
                 ("flops_paper", c_double), ("flops_tensor", c_double), ("flops_tensor_padded", c_double),
                 ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64), ("ms_gather", c_double),
-                ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64)]
+                ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64),
+                ("ms_energy_weighted", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -58,6 +59,7 @@ SIGNATURES = [
                                     ctypes.POINTER(c_double), ctypes.POINTER(c_double), c_void_p, c_void_p,
                                     c_void_p, c_void_p]),
     ("nolsm_scatter_density", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("nolsm_energy_weighted", c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     ("nolsm_find_mu", c_int32, [c_void_p, c_double, c_double, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
                                 ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int32),
                                 ctypes.POINTER(c_double)]),

@@ -556,14 +556,14 @@ nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_m
   return NOLSM_OK;
 }
 
-nolsm_status scatter(nolsm_plan* plan, double* D, int64_t j0, int64_t j1, cudaStream_t st) {
+nolsm_status scatter(nolsm_plan* plan, double* D, int64_t j0, int64_t j1, cudaStream_t st, const double* src) {
   const int64_t p0 = plan->h_nb_ptr[j0], p1 = plan->h_nb_ptr[j1];
   if (p1 <= p0) return NOLSM_OK;
   const int64_t threads = (p1 - p0) * 32;
   k_scatter<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       plan->n_mol, p0, p1, plan->sys.nbf, plan->nb_ptr.as<int32_t>(), plan->nb_idx.as<int32_t>(),
       plan->nb_off.as<int32_t>(), plan->d_slot.as<int32_t>(), plan->d_blk_off.as<int64_t>(), plan->c_off.as<int64_t>(),
-      plan->Dc.as<double>(), D);
+      src ? src : plan->Dc.as<double>(), D);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;
   return NOLSM_OK;

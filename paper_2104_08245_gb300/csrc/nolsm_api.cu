@@ -127,7 +127,7 @@ nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &Lsym, &Wc, &Dc,
                    &t_S, &t_H, &iters, &status, &rsteps, &nbelow, &nb_lo, &nb_hi, &active, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
-                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym};
+                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym, &Wd, &tW};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
   if (ev_ok)
@@ -327,6 +327,7 @@ static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options*
   if (trace_DH) *trace_DH = tH;
   plan->solved_begin = j0;
   plan->solved_end = j1;
+  plan->solved_cls = cls;
   plan->have_solution = true;
   if (bad != 0) {
     set_error("nolsm_solve_batch: a submatrix reported '%s'", nolsm_status_str((nolsm_status)bad));

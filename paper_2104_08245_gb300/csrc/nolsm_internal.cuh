@@ -108,7 +108,10 @@ struct nolsm_plan {
   nolsm::DevBuf sums;               // float64 [4]
   nolsm::DevBuf counter;            // int32 work counters of persistent kernels
   int64_t solved_begin = 0, solved_end = 0;
+  int solved_cls = -1;              // preparation class of the last solve (kPrepFP64, kPrepMixed, kPrepSym)
   bool have_solution = false;
+  nolsm::DevBuf Wd;                 // centre columns of T_J(W) (energy-weighted), FP64, at c_off[J]
+  nolsm::DevBuf tW;                 // float64 [n_mol]: t_S of T_J(W)
 
   // workspaces
   nolsm::DevBuf ws_dense;           // gathered T_J(S), T_J(H0) of one preparation chunk (FP64)
@@ -182,7 +185,11 @@ void prep_times(nolsm_plan* plan);
 // shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
 nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
                            double* tH, int32_t* first_bad_status);
-nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st);
+// write-back of centre columns (default: those of T_J(D)) into the merged pattern
+nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st,
+                     const double* src = nullptr);
+// centre columns of the energy-weighted T_J(W) at the plan's solution (energy_weighted.cu)
+nolsm_status energy_weighted(nolsm_plan* plan, cudaStream_t st, double* W_vals, double* trace_WS);
 
 }  // namespace nolsm
 
