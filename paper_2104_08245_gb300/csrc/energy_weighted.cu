@@ -23,6 +23,7 @@ constexpr int kEwThreads = 256;
 constexpr int kEwWarps = kEwThreads / 32;
 constexpr int kEwCols = 8;   // centre columns per pass (D_c staged in shared memory as [n][8])
 constexpr int kEwRows = 4;   // rows of A_J per warp pass: 4 x 8 partial sums per lane
+constexpr int kEwU = 8;      // k values per lane loaded ahead (rows of up to 256 elements in one chunk)
 
 struct EwArgs {
   int32_t j0;
@@ -70,7 +71,8 @@ __device__ __forceinline__ T reduce_scatter32(T (&v)[32], int lane) {
   return v[0];
 }
 
-// One CTA per submatrix; warps take 4 rows of A_J at a time, lanes stride over k (coalesced rows).
+// One CTA per submatrix; warps take 4 rows of A_J at a time, lanes stride over k (coalesced rows) and
+// load up to 8 k values of each row ahead, so that enough of A_J is in flight to cover the HBM latency.
 template <typename TA>
 __global__ void __launch_bounds__(kEwThreads) k_energy_weighted(EwArgs g, const TA* __restrict__ A_all) {
   extern __shared__ __align__(16) unsigned char ew_smem[];
@@ -100,15 +102,26 @@ __global__ void __launch_bounds__(kEwThreads) k_energy_weighted(EwArgs g, const 
       TA acc[kEwRows * kEwCols];
 #pragma unroll
       for (int v = 0; v < kEwRows * kEwCols; ++v) acc[v] = (TA)0;
-#pragma unroll 2
-      for (int k = lane; k < n; k += 32) {
-        TA dv[kEwCols];
-        load8(ds + k * kEwCols, dv);
+      for (int kb = 0; kb < n; kb += 32 * kEwU) {
+        // every load of the chunk is issued before the first multiply (kEwU x 4 loads in flight per lane)
+        TA av[kEwU][kEwRows];
 #pragma unroll
-        for (int r = 0; r < kEwRows; ++r) {
-          const TA a = arow[r][k];
+        for (int u = 0; u < kEwU; ++u) {
+          const int k = kb + lane + 32 * u;
 #pragma unroll
-          for (int c = 0; c < kEwCols; ++c) acc[r * kEwCols + c] = fma(a, dv[c], acc[r * kEwCols + c]);
+          for (int r = 0; r < kEwRows; ++r) av[u][r] = k < n ? arow[r][k] : (TA)0;
+        }
+#pragma unroll
+        for (int u = 0; u < kEwU; ++u) {
+          const int k = kb + lane + 32 * u;
+          if (k < n) {
+            TA dv[kEwCols];
+            load8(ds + k * kEwCols, dv);
+#pragma unroll
+            for (int r = 0; r < kEwRows; ++r)
+#pragma unroll
+              for (int c = 0; c < kEwCols; ++c) acc[r * kEwCols + c] = fma(av[u][r], dv[c], acc[r * kEwCols + c]);
+          }
         }
       }
       const TA sum = reduce_scatter32(acc, lane);
