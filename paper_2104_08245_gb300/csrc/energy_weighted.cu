@@ -35,7 +35,13 @@ struct EwArgs {
   const double* Sc;   // centre columns of T_J(S), same layout
   double* Wd;         // centre columns of T_J(W), same layout
   double* tW;         // [n_mol]: sum over centre columns j and rows i of T_J(W)_ij T_J(S)_ij
+  const void* a_end;  // end of the A_J array (bound of the L2 prefetch)
 };
+
+// Asks the TMA unit to bring [p, p + bytes) into L2 (p and bytes multiples of 16; no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(uintptr_t p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
   const float4 a = *reinterpret_cast<const float4*>(p);
@@ -71,8 +77,8 @@ __device__ __forceinline__ T reduce_scatter32(T (&v)[32], int lane) {
   return v[0];
 }
 
-// One CTA per submatrix; warps take 4 rows of A_J at a time, lanes stride over k (coalesced rows) and
-// load up to 8 k values of each row ahead, so that enough of A_J is in flight to cover the HBM latency.
+// One CTA per submatrix; one thread asks for all of A_J in L2 (bulk prefetch), then warps take 4 rows of
+// A_J at a time, lanes stride over k (coalesced rows) and load up to 8 k values of each row ahead.
 template <typename TA>
 __global__ void __launch_bounds__(kEwThreads) k_energy_weighted(EwArgs g, const TA* __restrict__ A_all) {
   extern __shared__ __align__(16) unsigned char ew_smem[];
@@ -85,6 +91,14 @@ __global__ void __launch_bounds__(kEwThreads) k_energy_weighted(EwArgs g, const 
   const double* __restrict__ S = g.Sc + g.c_off[J];
   double* __restrict__ W = g.Wd + g.c_off[J];
   const int tid = threadIdx.x, lane = tid & 31, wrp = tid >> 5;
+  if (tid == 0) {
+    // the whole of A_J into L2 at once, so that the warps' row loads below find it there: the start rounded
+    // down and the end rounded down to 16 bytes stay inside the A array
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(A) & ~static_cast<uintptr_t>(15);
+    const uintptr_t hi = min(reinterpret_cast<uintptr_t>(A + (size_t)n * n), reinterpret_cast<uintptr_t>(g.a_end)) &
+                         ~static_cast<uintptr_t>(15);
+    for (uintptr_t q = lo; q < hi; q += 32768) prefetch_l2(q, (uint32_t)min(static_cast<uintptr_t>(32768), hi - q));
+  }
   double tw = 0.0;
   for (int c0 = 0; c0 < b; c0 += kEwCols) {
     const int cb = min(kEwCols, b - c0);
@@ -202,9 +216,10 @@ nolsm_status energy_weighted(nolsm_plan* plan, cudaStream_t st, double* W_vals, 
   g.Wd = plan->Wd.as<double>();
   g.tW = plan->tW.as<double>();
   const int count = (int)(j1 - j0);
+  const Prepared& P = prepared(plan, cls);
+  g.a_end = static_cast<const char*>(P.A.p) + (cls == kPrepFP64 ? sizeof(double) : sizeof(float)) * plan->h_a_off[n_mol];
   mark(plan, 6, st);
   if (count > 0) {
-    const Prepared& P = prepared(plan, cls);
     if (cls == kPrepFP64) NOLSM_TRY(launch_ew<double>(g, count, max_n, P.A.as<double>(), st));
     else NOLSM_TRY(launch_ew<float>(g, count, max_n, P.A.as<float>(), st));
     plan->stats.launches += 1;
