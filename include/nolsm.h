@@ -201,6 +201,26 @@ nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_strea
  * form (NOLSM_FP8E4M3 or symmetric_form = 1), which does not keep A_J. Synchronises the stream. */
 nolsm_status nolsm_energy_weighted(nolsm_plan* plan, nolsm_stream_t stream, double* W_vals, double* trace_WS);
 
+/* Submatrix combination heuristic (Sec. "Submatrix Combination Heuristics", Eq. combination_criterion),
+ * a host-side planning step: no device work and no CUDA call (the paper runs it once on a CPU node and
+ * reuses the result). Submatrices i, j of dimensions n_i, n_j with n_c rows in common merge into one of
+ * n_i + n_j - n_c rows iff (n_i + n_j - n_c)^3 < n_i^3 + n_j^3. Start: one submatrix per molecule J with rows
+ * N(J); a group's candidates are the groups owning a molecule among its rows; a sweep lists every ordered
+ * pair (i, j) passing the criterion with its level n_j - n_c and gain n_i^3 + n_j^3 - (n_i + n_j - n_c)^3,
+ * takes the pairs by level ascending, gain descending, i, j ascending, and merges a pair when neither
+ * group merged earlier in that sweep; sweeps repeat until one merges nothing. Dimensions count basis
+ * functions; the cubes are exact 128-bit integers, so the result does not depend on `threads`.
+ *   n_mol; nbf (host, [n_mol], >= 1); nb_ptr (host, [n_mol+1]), nb_idx (host, [nb_ptr[n_mol]]): N(J) of
+ *     every J, strictly ascending, J in N(J), the relation symmetric (as nolsm_plan_get_maps returns it);
+ *   threads: host threads that list the candidate pairs (<= 0: the hardware's count, at most 64).
+ *   group_of (host, [n_mol]): each molecule's group, named by its smallest member; n_groups (host);
+ *   metrics (host, [4], may be NULL): sum of n^3 before and after, sum of n^2 before and after (the
+ *     cubic work metric and the quadratic element metric); sweeps (host, may be NULL).
+ * NOLSM_ERR_ARG on a NULL pointer or a malformed pattern (nothing written). */
+nolsm_status nolsm_combine_submatrices(int32_t n_mol, const int32_t* nbf, const int32_t* nb_ptr, const int32_t* nb_idx,
+                                       int32_t threads, int32_t* group_of, int32_t* n_groups, double* metrics,
+                                       int32_t* sweeps);
+
 /* a9: chemical potential by bisection (Sec. "Simulation Details"): f(mu) = Tr(DS) - n_occ with
  * Tr(DS) over the options' range (a point solves only the submatrices with an eigenvalue left in the
  * bracket, see nolsm_bisect_point); mu = (lo+hi)/2; f < 0 raises lo, otherwise

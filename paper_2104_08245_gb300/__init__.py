@@ -15,7 +15,8 @@ from . import _abi
 from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4M3, FP16, FP32, FP64,  # noqa: F401
                    PRECISIONS, NolsmOptions, NolsmPlanInfo, NolsmStats, NolsmSystem)
 
-__all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density", "nolsm_energy_weighted",
+__all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
+           "nolsm_energy_weighted", "nolsm_combine_submatrices",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
            "nolsm_spectral_bracket", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
            "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
@@ -226,6 +227,34 @@ def nolsm_energy_weighted(plan: "Plan", W_vals=None, stream=None):
     if rc != 0:
         raise NolsmError(rc, "nolsm_energy_weighted")
     return (W_vals if W_vals is not False else None), tw.value
+
+
+@dataclasses.dataclass
+class CombineResult:
+    group_of: "np.ndarray"    # int32 [n_mol]: each molecule's group (its smallest member)
+    n_groups: int
+    sum_n3_before: float
+    sum_n3_after: float
+    sum_n2_before: float
+    sum_n2_after: float
+    sweeps: int
+
+
+def nolsm_combine_submatrices(nbf, nb_ptr, nb_idx, threads: int = 0) -> CombineResult:
+    """Submatrix combination heuristic on a host copy of the merged pattern (numpy arrays or CPU tensors)."""
+    import numpy as np
+    a = [np.ascontiguousarray(np.asarray(x.cpu() if hasattr(x, "cpu") else x), dtype=np.int32)
+         for x in (nbf, nb_ptr, nb_idx)]
+    n_mol = int(a[0].shape[0])
+    group_of = np.zeros(n_mol, dtype=np.int32)
+    metrics = np.zeros(4, dtype=np.float64)
+    ng, sw = ctypes.c_int32(), ctypes.c_int32()
+    rc = _abi.load().nolsm_combine_submatrices(n_mol, a[0].ctypes.data, a[1].ctypes.data, a[2].ctypes.data,
+                                               int(threads), group_of.ctypes.data, ctypes.byref(ng),
+                                               metrics.ctypes.data, ctypes.byref(sw))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_combine_submatrices")
+    return CombineResult(group_of, ng.value, *[float(x) for x in metrics], sw.value)
 
 
 @dataclasses.dataclass

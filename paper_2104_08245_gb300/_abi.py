@@ -60,6 +60,8 @@ SIGNATURES = [
                                     c_void_p, c_void_p]),
     ("nolsm_scatter_density", c_int32, [c_void_p, c_void_p, c_void_p]),
     ("nolsm_energy_weighted", c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    ("nolsm_combine_submatrices", c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                            ctypes.POINTER(c_int32), c_void_p, ctypes.POINTER(c_int32)]),
     ("nolsm_find_mu", c_int32, [c_void_p, c_double, c_double, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
                                 ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int32),
                                 ctypes.POINTER(c_double)]),
