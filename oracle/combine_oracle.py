@@ -100,3 +100,61 @@ def combine(nbf, nb_ptr, nb_idx) -> CombineResult:
     n3_1 = sum(dim(r, nbf) ** 3 for r in rows.values())
     n2_1 = sum(dim(r, nbf) ** 2 for r in rows.values())
     return CombineResult(np.asarray(group_of, dtype=np.int32), members, rows, merges, sweeps, n3_0, n3_1, n2_0, n2_1)
+
+
+# ============================================================================ merged submatrices
+
+def gather_rows(system_matrix, nbf, mols) -> np.ndarray:
+    """The dense submatrix of a block-CSR matrix over the rows and columns of the molecules ``mols``
+    (ascending), blocks placed in that order; absent blocks are zero (Sec. "The Submatrix Method",
+    step (i), for a merged row set)."""
+    from .nolsm_oracle import _block
+    offs = np.concatenate([[0], np.cumsum([int(nbf[m]) for m in mols])]).astype(np.int64)
+    T = np.zeros((int(offs[-1]), int(offs[-1])), dtype=np.float64)
+    for a, I in enumerate(mols):
+        for c, K in enumerate(mols):
+            blk = _block(system_matrix.row_ptr, system_matrix.col_idx, system_matrix.blk_off, system_matrix.vals,
+                         nbf, int(I), int(K))
+            if blk is not None:
+                T[offs[a]:offs[a + 1], offs[c]:offs[c + 1]] = blk
+    return T
+
+
+@dataclasses.dataclass
+class GroupedResult:
+    D_cols: dict           # J -> centre columns of J from its group's T_G(D), on the rows of N(J)
+    t_S: dict              # J -> sum over J's columns j and rows i of T_G(D)_ij T_G(S)_ij
+    trace_DS: float
+    D_vals: np.ndarray     # D in the merged pattern (block (I, J) for I in N(J), as the per-molecule solve)
+
+
+def solve_grouped(system, mu: float, group_of, plan, tol: float = 1e-9) -> GroupedResult:
+    """The density matrix from merged submatrices (Sec. "Submatrix Combination Heuristics": the columns of
+    all molecules of a group share one submatrix T_G over the union of their rows):
+    T_G(D) = 1/2 (I - sign(T_G(S)^-1 T_G(H0) - mu I)) T_G(S)^-1 (Eq. purification_submatrix), and the
+    columns of each member J are written back on the rows of N(J), so that D keeps the merged pattern of S
+    and H0 (reading: the paper notes that merging could keep a denser D; this keeps the output format)."""
+    from .nolsm_oracle import submatrix_density, write_back_cols
+    nbf = plan.nbf
+    group_of = np.asarray(group_of)
+    cols, tS = {}, {}
+    total = 0.0
+    for g in sorted(set(int(x) for x in group_of)):
+        members = [int(J) for J in np.nonzero(group_of == g)[0]]
+        rows = sorted(set(int(m) for J in members for m in plan.nb_idx[plan.nb_ptr[J]:plan.nb_ptr[J + 1]]))
+        offs = dict(zip(rows, np.concatenate([[0], np.cumsum([int(nbf[m]) for m in rows])])[:-1].tolist()))
+        S = gather_rows(system.S, nbf, rows)
+        H = gather_rows(system.H, nbf, rows)
+        r = submatrix_density(S, H, mu, 0, S.shape[0], tol)
+        for J in members:
+            c0, bJ = offs[J], int(nbf[J])
+            nJ = [int(m) for m in plan.nb_idx[plan.nb_ptr[J]:plan.nb_ptr[J + 1]]]
+            sel = np.concatenate([np.arange(offs[m], offs[m] + int(nbf[m])) for m in nJ])
+            cols[J] = r.D_sub[sel, c0:c0 + bJ].copy()
+            t = 0.0
+            for j in range(c0, c0 + bJ):
+                for i in range(S.shape[0]):
+                    t += r.D_sub[i, j] * S[i, j]
+            tS[J] = t
+            total += t
+    return GroupedResult(cols, tS, total, write_back_cols(plan, cols))

@@ -11,9 +11,13 @@ Eq. combination_criterion) against facts fixed by hand or by the structure of th
   falls by exactly the logged gains, and no two final groups with neighbouring members would still
   pass the criterion (the stopping rule);
 * planted mistakes (a criterion on squares, the common rows not subtracted) that the replay or the
-  stopping-rule pin catches.
+  stopping-rule pin catches;
+* the density from merged submatrices: singleton groups give the per-molecule solve exactly, and one
+  group of every molecule gives the full matrix's density (LAPACK's generalized eigensolver).
 """
+import numpy as np
 import pytest
+import scipy.linalg
 
 from oracle import combine_oracle as co
 from oracle import nolsm_oracle as orc
@@ -127,3 +131,35 @@ def test_stopping_rule_catches_planted_mistakes(mistake, monkeypatch):
     except AssertionError:
         replay_ok = False
     assert not replay_ok or _stopping_rule_violations(sp.nbf, r) > 0
+
+
+# ------------------------------------------------------------------ merged submatrices (the solve side)
+
+def test_singleton_groups_reproduce_the_per_molecule_solve():
+    sysm = make_system(SystemSpec(4, 4, 4, nbf="mixed", cutoff=4.5, seed=13))
+    plan = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    ref = orc.solve(sysm, -0.8, plan=plan)
+    g = co.solve_grouped(sysm, -0.8, list(range(sysm.n_mol)), plan)
+    assert (g.D_vals == ref.D_vals).all()
+    assert g.trace_DS == ref.trace_DS
+
+
+@pytest.mark.parametrize("spec", [SystemSpec(4, 4, 4, seed=1001), SystemSpec(4, 4, 4, nbf="mixed", cutoff=4.5, seed=13)])
+def test_one_group_gives_the_full_matrix_density(spec):
+    """A group holding every molecule has the whole matrix as its submatrix: the written-back D is the
+    S-orthogonal projector on the states below mu (LAPACK's generalized eigensolver) on D's pattern, and
+    Tr(DS) is the number of those states."""
+    sysm = make_system(spec)
+    plan = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    S = orc.csr_to_dense(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.S.blk_off, sysm.S.vals)
+    H = orc.csr_to_dense(sysm.nbf, sysm.H.row_ptr, sysm.H.col_idx, sysm.H.blk_off, sysm.H.vals)
+    eps, C = scipy.linalg.eigh(H, S)
+    n_occ = int(sysm.n_occ)
+    mu = 0.5 * (eps[n_occ - 1] + eps[n_occ])
+    P = C[:, :n_occ] @ C[:, :n_occ].T
+    g = co.solve_grouped(sysm, mu, [0] * sysm.n_mol, plan)
+    D = orc.d_to_dense(plan, g.D_vals)
+    mask = orc.d_to_dense(plan, np.ones_like(g.D_vals)) != 0
+    assert np.max(np.abs((D - P)[mask])) < 1e-11
+    assert np.all(D[~mask] == 0.0)
+    assert g.trace_DS == pytest.approx(n_occ, abs=1e-9)
