@@ -529,7 +529,7 @@ def main():
         t0 = time.perf_counter()
         cr = nl.nolsm_combine_submatrices(sp.nbf, sp.nb_ptr, sp.nb_idx)
         dt_c = time.perf_counter() - t0
-        combination = {"workload": "atom-resolved water lattice 16x16x16 with 2 % ions (O 4, H 1, ion 9 functions; "
+        combination = {"workload": "atom-resolved water lattice 16x16x16 with 2 % ions (O 4, H 2, ion 4 functions; "
                                    "6 / 10 Angstrom interaction radii)",
                        "sites": sp.n_sites, "groups": cr.n_groups, "sweeps": cr.sweeps,
                        "sum_n3_reduction": cr.sum_n3_before / cr.sum_n3_after,

@@ -9,6 +9,8 @@ molecule-coalesced water of the main workload. This module makes a stand-in of t
   resolved into three sites: O at the lattice site with ``o_nbf`` functions, two H at 0.96 Angstrom
   from it, 104.5 degrees apart, in a random orientation, with ``h_nbf`` functions each;
 * a fraction ``ion_fraction`` of the lattice sites holding an ion instead (``ion_nbf`` functions);
+* function counts as in the paper's Sec. "Simulation Details": two per hydrogen, four for every other
+  element of its systems but sulfur (so four for O and for a sodium ion);
 * a pair of sites (a, b) is in the pattern when their minimum-image distance is below
   (r_a + r_b) / 2 (strict), r = ``rc`` for water atoms and ``rc_ion`` for ions, so ions get large
   submatrices; every site is its own neighbour.
@@ -29,8 +31,8 @@ class SiteSpec:
     nz: int
     ion_fraction: float = 0.0
     o_nbf: int = 4
-    h_nbf: int = 1
-    ion_nbf: int = 9
+    h_nbf: int = 2
+    ion_nbf: int = 4
     rc: float = 6.0
     rc_ion: float = 10.0
     spacing: float = 3.1
