@@ -1,6 +1,8 @@
 """The sharded bisection on two gloo ranks (CPU): each rank counts electrons of its half of the
 submatrices with the FP64 oracle; the all-reduced bisection must visit exactly the points of the
-single-process bisection over all submatrices and stop at the same mu."""
+single-process bisection over all submatrices and stop at the same mu. Failure detection, made on the
+host: a rank that leaves between two bisection points makes the other rank's next sum fail with an
+error (the group also has a 20 s timeout) instead of hanging."""
 import os
 import socket
 
@@ -69,3 +71,43 @@ def test_two_rank_bisection_matches_single_process():
         assert hist == [m for m, _ in ref.history]
         assert mu == ref.mu
         assert t == pytest.approx(ref.trace_DS, abs=1e-9)
+
+
+def _rank_that_leaves(rank, world, port, out):
+    import datetime
+    import torch.distributed as dist
+    from paper_2104_08245_gb300.sharded import bisect_allreduce
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    points = []
+
+    def count(mu):
+        points.append(mu)
+        if rank == 1 and len(points) == 2:
+            os._exit(0)          # leaves between points, without joining the next sum
+        return 0.0               # every rank below n_occ: the bisection keeps going
+
+    try:
+        bisect_allreduce(count, (-1.0, 1.0), 10.0, 1e-5, 1e-10, 50)
+        out[rank] = "finished"
+    except RuntimeError as e:    # the peer's exit (or the group's timeout) surfaces as an error, not a hang
+        out[rank] = "detected: " + str(e).splitlines()[0][:80]
+
+
+def test_a_rank_that_leaves_is_detected_by_the_others():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    ctx = mp.start_processes(_rank_that_leaves, args=(world, port, out), nprocs=world, join=False,
+                             start_method="spawn")
+    for _ in range(120):                     # bounded wait: at most 120 x 1 s
+        if ctx.join(timeout=1):
+            break
+    else:
+        for p in ctx.processes:
+            p.kill()
+        pytest.fail("the remaining rank hung after its peer left")
+    assert 1 not in out                      # rank 1 left without reporting
+    assert out[0].startswith("detected")
