@@ -3,4 +3,4 @@
 Importable only from ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``.
 The GPU library neither imports nor links anything here.
 """
-from . import nolsm_oracle, mlp_oracle, combine_oracle  # noqa: F401
+from . import nolsm_oracle, mlp_oracle, combine_oracle, inverse_oracle  # noqa: F401
