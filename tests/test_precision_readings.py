@@ -6,6 +6,8 @@
    from the same start converges quadratically past that point.
 2. A rounding error made in a late step persists in D: the Frechet derivative of the sign at an
    involution S is E -> (E - S E S) / 2, the identity on the part of E that anticommutes with S.
+3. A three-term split product (hi and lo parts in FP16 or BF16, FP32 accumulation) carries about twice
+   the format's mantissa bits (limited by the FP32 sums for FP16), a single product one format's worth.
 The E4M3 rounding is PyTorch's float8_e4m3fn conversion (round to nearest even, 448 the largest normal),
 the matrices a submatrix of the 64-molecule system in its symmetric form."""
 import numpy as np
@@ -90,3 +92,34 @@ def test_sign_derivative_keeps_anticommuting_errors():
     assert np.linalg.norm(Yc - S) < 1e-3 * eps * np.linalg.norm(E_comm)
     # and the limit is the sign of the perturbed matrix, to first order the same
     assert np.linalg.norm(Ya - sign_of(S + eps * E_anti)) < 1e-3 * eps * np.linalg.norm(E_anti)
+
+
+@pytest.mark.parametrize("fmt,lo_bound,hi_bound", [("float16", 1e-8, 1e-6), ("bfloat16", 1e-6, 1e-4)])
+def test_three_term_split_products_keep_about_twice_the_format_bits(fmt, lo_bound, hi_bound):
+    """3. The split modes: X = X_hi + X_lo with both parts in the 16-bit format and a product
+    X_hi Y_hi + X_hi Y_lo + X_lo Y_hi accumulated in FP32 (every partial product exact in FP32) carries
+    about twice the format's mantissa bits (FP16: 2 x 11 = 22, BF16: 2 x 8 = 16), against one format's
+    worth for a single product; operands in [-1.7, 1.7] as after the scaling of X_0."""
+    torch = pytest.importorskip("torch")
+    dt = getattr(torch, fmt)
+    rng = np.random.default_rng(5)
+    n = 192
+    A = rng.uniform(-1.7, 1.7, size=(n, n))
+    B = rng.uniform(-1.7, 1.7, size=(n, n))
+    exact = A @ B
+
+    def split(X):
+        t = torch.from_numpy(X)
+        hi = t.to(dt)
+        lo = (t - hi.to(torch.float64)).to(dt)
+        return hi.to(torch.float32), lo.to(torch.float32)
+
+    ah, al = split(A)
+    bh, bl = split(B)
+    three = (ah @ bh + ah @ bl + al @ bh).to(torch.float64).numpy()
+    one = (ah @ bh).to(torch.float64).numpy()
+    scale = np.max(np.abs(exact))
+    e3 = np.max(np.abs(three - exact)) / scale
+    e1 = np.max(np.abs(one - exact)) / scale
+    assert lo_bound < e3 < hi_bound
+    assert e1 > 30.0 * e3
