@@ -59,7 +59,7 @@ def test_struct_layouts_match_header(tmp_path):
     """ctypes offsets and sizes equal those the C compiler gives for the header's structs."""
     from paper_2104_08245_gb300 import _abi
     structs = {"nolsm_system": _abi.NolsmSystem, "nolsm_options": _abi.NolsmOptions,
-               "nolsm_plan_info": _abi.NolsmPlanInfo}
+               "nolsm_plan_info": _abi.NolsmPlanInfo, "nolsm_stats": _abi.NolsmStats}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "nolsm.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -84,3 +84,44 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.nolsm_build_submatrices(None, None, ctypes.byref(out)) == _abi.ERR_ARG
     assert lib.nolsm_scatter_density(None, None, None) == _abi.ERR_ARG
     assert b"NULL" in lib.nolsm_last_error() or lib.nolsm_last_error()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "nolsm.h"
+int main(void) {
+  nolsm_options o;
+  nolsm_options_default(&o, NOLSM_BF16X3);
+  if (o.precision != NOLSM_BF16X3 || o.refine_steps != 2) return 1;
+  nolsm_plan* plan = 0;
+  if (nolsm_build_submatrices(0, 0, &plan) != NOLSM_ERR_ARG) return 2;
+  /* the three-molecule chain: N(0) = {0,1}, N(1) = {0,1,2}, N(2) = {1,2}, one function each */
+  int32_t nbf[3] = {1, 1, 1}, ptr[4] = {0, 2, 5, 7}, idx[7] = {0, 1, 0, 1, 2, 1, 2};
+  int32_t group_of[3], ng = 0, sweeps = 0;
+  double m[4];
+  if (nolsm_combine_submatrices(3, nbf, ptr, idx, 1, group_of, &ng, m, &sweeps) != NOLSM_OK) return 3;
+  printf("%d %d %d %d %d %.0f %.0f\n", group_of[0], group_of[1], group_of[2], ng, sweeps, m[0], m[1]);
+  idx[0] = 1; idx[1] = 0;   /* N(0) no longer ascending */
+  if (nolsm_combine_submatrices(3, nbf, ptr, idx, 1, group_of, &ng, m, &sweeps) != NOLSM_ERR_ARG) return 4;
+  printf("%s\n", nolsm_status_str(NOLSM_ERR_ARG));
+  return 0;
+}
+"""
+
+
+def test_c_program_links_and_calls_the_host_entry_points(lib, tmp_path):
+    """A C program built against include/nolsm.h and linked to the library calls the entry points
+    that need no GPU (options, argument checks, the host-side combination heuristic)."""
+    from paper_2104_08245_gb300 import _abi
+    src = tmp_path / "host_calls.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "host_calls"
+    libdir = os.path.dirname(_abi.lib_path())
+    name = os.path.basename(_abi.lib_path())[3:-3]          # libnolsm.so -> nolsm
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, f"-l{name}",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, run.stdout + run.stderr
+    first, second = run.stdout.splitlines()[:2]
+    assert first == "0 0 0 1 3 43 27"
+    assert second
