@@ -31,6 +31,8 @@ def _site_pattern(spec):
 
 
 CASES = {
+    "empty": lambda: (np.zeros(0, dtype=np.int32), np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32)),
+    "one_molecule": lambda: (np.array([5]), np.array([0, 1]), np.array([0])),
     "chain": lambda: (np.array([1, 1, 1]), np.array([0, 2, 5, 7]), np.array([0, 1, 0, 1, 2, 1, 2])),
     "whole_cell": lambda: _sys_pattern(spec_tiny(2)),
     "isolated": lambda: _sys_pattern(SystemSpec(3, 3, 2, cutoff=1.5, seed=14)),
@@ -84,3 +86,28 @@ def test_malformed_pattern_is_rejected(nl, bad):
     with pytest.raises(nl.NolsmError) as e:
         nl.nolsm_combine_submatrices(nbf, nb_ptr, nb_idx)
     assert e.value.status == 1          # NOLSM_ERR_ARG
+
+
+def _random_pattern(rng, n, p, max_b):
+    adj = rng.random((n, n)) < p
+    adj = adj | adj.T
+    np.fill_diagonal(adj, True)
+    nb_ptr = np.concatenate([[0], np.cumsum(adj.sum(axis=0))]).astype(np.int32)
+    nb_idx = np.concatenate([np.nonzero(adj[:, J])[0] for J in range(n)]).astype(np.int32)
+    nbf = rng.integers(1, max_b + 1, size=n).astype(np.int32)
+    return nbf, nb_ptr, nb_idx
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_native_matches_oracle_on_random_patterns(nl, seed):
+    """Random symmetric patterns (any degree, 1..9 functions per molecule), including dense and almost
+    empty ones: the same groups, sweeps and metrics as the oracle."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 60))
+    p = float(rng.choice([0.02, 0.1, 0.3, 0.8]))
+    nbf, nb_ptr, nb_idx = _random_pattern(rng, n, p, 9)
+    ref = co.combine(nbf, nb_ptr, nb_idx)
+    got = nl.nolsm_combine_submatrices(nbf, nb_ptr, nb_idx, threads=int(rng.integers(1, 5)))
+    assert np.array_equal(got.group_of, ref.group_of)
+    assert got.sweeps == ref.sweeps and got.n_groups == len(ref.members)
+    assert (got.sum_n3_before, got.sum_n3_after) == (float(ref.sum_n3_before), float(ref.sum_n3_after))
