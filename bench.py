@@ -133,58 +133,65 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------ oracle (CPU)
+# The main process builds the oracle's plan and gathers the sampled submatrices (Sec. "The Submatrix
+# Method", step (i)); spawned workers solve them one by one (FP64 oracle), so no worker holds the system.
 
-_ORC = {}
-
-
-def _oracle_init(spec_name, spec_kw):
-    import synth
+def _oracle_sub(item):
     from oracle import nolsm_oracle as orc
-    sysm = synth.make_system(getattr(synth, spec_name)(**spec_kw))
-    _ORC["sys"] = sysm
-    _ORC["plan"] = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    J, S_sub, H_sub, mu, c0, b = item
+    r = orc.submatrix_density(S_sub, H_sub, mu, c0, b)
+    return J, (r.D_cols, r.t_S, r.t_H)
 
 
-def _oracle_solve(args):
-    from oracle import nolsm_oracle as orc
-    subs, mu = args
-    r = orc.solve(_ORC["sys"], mu, subs=subs, plan=_ORC["plan"])
-    return {J: (s.D_cols, s.t_S, s.t_H) for J, s in r.subs.items()}
-
-
-def _oracle_gersh(subs):
-    """Spectral interval of A_J for the listed submatrices (for the reference arm's bracket)."""
+def _oracle_gersh(item):
+    """Gershgorin interval of A = T_J(S)^-1 T_J(H0) of one gathered submatrix (reference arm's bracket)."""
     import numpy as np
     from oracle import nolsm_oracle as orc
-    sysm, plan = _ORC["sys"], _ORC["plan"]
-    lo, hi = np.inf, -np.inf
-    for J in subs:
-        S = orc.gather(plan, J, sysm.S.row_ptr, sysm.S.col_idx, sysm.S.blk_off, sysm.S.vals)
-        H = orc.gather(plan, J, sysm.H.row_ptr, sysm.H.col_idx, sysm.H.blk_off, sysm.H.vals)
-        A = orc.overlap_inverse(S) @ H
-        d = np.diag(A)
-        R = np.sum(np.abs(A), axis=1) - np.abs(d)
-        lo, hi = min(lo, float(np.min(d - R))), max(hi, float(np.max(d + R)))
-    return lo, hi
+    _, S_sub, H_sub = item
+    A = orc.overlap_inverse(S_sub) @ H_sub
+    d = np.diag(A)
+    R = np.sum(np.abs(A), axis=1) - np.abs(d)
+    return float(np.min(d - R)), float(np.max(d + R))
 
 
-def oracle_pool(spec_name, spec_kw, workers):
-    import multiprocessing as mp
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    ctx = mp.get_context("spawn")
-    return ctx.Pool(workers, initializer=_oracle_init, initargs=(spec_name, spec_kw))
+class OracleSample:
+    """The oracle's plan of a system and a pool of spawned workers for sampled submatrices."""
 
+    def __init__(self, sysm, workers):
+        import multiprocessing as mp
+        from oracle import nolsm_oracle as orc
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        self.sysm = sysm
+        self.plan = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+        import numpy as np
+        self.pool.map(_oracle_gersh, [(0, np.eye(1), np.zeros((1, 1)))] * workers)   # start the workers
 
-def run_oracle(pool, subs, mu, workers):
-    chunks = [subs[i::workers] for i in range(workers)]
-    t0 = time.perf_counter()
-    parts = pool.map(_oracle_solve, [(c, mu) for c in chunks if c])
-    dt = time.perf_counter() - t0
-    out = {}
-    for p in parts:
-        out.update(p)
-    return out, dt
+    def gather(self, J):
+        from oracle import nolsm_oracle as orc
+        s, p = self.sysm, self.plan
+        return (orc.gather(p, J, s.S.row_ptr, s.S.col_idx, s.S.blk_off, s.S.vals),
+                orc.gather(p, J, s.H.row_ptr, s.H.col_idx, s.H.blk_off, s.H.vals))
+
+    def solve(self, subs, mu):
+        """({J: (D_cols, t_S, t_H)}, seconds) for the listed submatrices at mu, gather included."""
+        t0 = time.perf_counter()
+        items = []
+        for J in subs:
+            S_sub, H_sub = self.gather(J)
+            items.append((J, S_sub, H_sub, mu, int(self.plan.sub_c0[J]), int(self.plan.nbf[J])))
+        out = dict(self.pool.map(_oracle_sub, items, chunksize=max(1, len(items) // (4 * self.workers))))
+        return out, time.perf_counter() - t0
+
+    def bracket(self, subs):
+        items = [(J, *self.gather(J)) for J in subs]
+        b = self.pool.map(_oracle_gersh, items)
+        return min(x[0] for x in b), max(x[1] for x in b)
+
+    def close(self):
+        self.pool.close()
 
 
 # ------------------------------------------------------------------------------------ reference arm
@@ -194,23 +201,22 @@ def reference_arm(args, spec_name, desc):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    workers = max(1, os.cpu_count() or 1)
-    pool = oracle_pool(spec_name, {}, workers)
     import synth
-    n_mol = getattr(synth, spec_name)().n_mol
+    from oracle import nolsm_oracle as orc
+    sysm = synth.make_system(getattr(synth, spec_name)())
+    n_mol = sysm.n_mol
+    workers = max(1, os.cpu_count() or 1)
+    ora = OracleSample(sysm, workers)
     rng = np.random.default_rng(7)
     sample = sorted(int(j) for j in rng.choice(n_mol, size=min(n_mol, args.ref_sample), replace=False))
-    chunks = [sample[i::workers] for i in range(workers)]
-    bounds = pool.map(_oracle_gersh, [c for c in chunks if c])
-    lo, hi = min(b[0] for b in bounds), max(b[1] for b in bounds)
-    n_occ = 4.0 * len(sample)
+    lo, hi = ora.bracket(sample)
+    n_occ = float(np.sum(sysm.occ[sample]))   # the sample's own electron count
 
     def step():
-        from oracle import nolsm_oracle as orc
         evals = []
 
         def count(mu):
-            res, _ = run_oracle(pool, sample, mu, workers)
+            res, _ = ora.solve(sample, mu)
             evals.append(mu)
             return sum(v[1] for v in res.values())
         r = orc.find_mu(count, n_occ, lo, hi, tol_n=1e-5 * n_occ)
@@ -224,7 +230,7 @@ def reference_arm(args, spec_name, desc):
         t0 = time.perf_counter()
         _, nev = step()
         times.append(time.perf_counter() - t0)
-    pool.close()
+    ora.close()
     ms = 1e3 * statistics.mean(times)
     value = len(sample) / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC,
@@ -235,7 +241,8 @@ def reference_arm(args, spec_name, desc):
                        "molecules_per_gpu": n_mol, "bracket": "Gershgorin interval of the sampled submatrices",
                        "sample": f"{len(sample)} submatrices, their own electron count, {nev} bisection points"},
             "cpu_baseline": {"value": value, "unit": "submatrices/s", "cores": workers, "kind": "oracle",
-                             "sample": f"oracle bisection on {len(sample)} sampled submatrices per step"},
+                             "sample": f"oracle bisection on {len(sample)} sampled submatrices per step "
+                                       "(gathered on one core, solved on all)"},
             "e2e": {"value": value, "unit": "submatrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -243,21 +250,68 @@ def reference_arm(args, spec_name, desc):
 
 # ------------------------------------------------------------------------------------ bound sources
 
-def bound_sources_leg(nl, synth, spec_name, dsys, mu_star, precision, dev):
-    """a4/a10: the learned predictor trained on samples the method produces on this system (power
-    interval and step counts at three chemical potentials around mu*), then Gershgorin, power and
-    learned bounds compared on a fresh system of the same kind (another seed) at mu*."""
-    import dataclasses
+def d_elements(po, subs):
+    """Element indices into D (merged pattern, the oracle's block offsets) of every block (I, J), I in N(J),
+    of the listed submatrices, with the matching (row, column) of J's centre columns."""
+    import numpy as np
+    from oracle import nolsm_oracle as orc
+    off = orc.d_block_offsets(po)
+    idx, where = [], {}
+    pos = 0
+    for J in subs:
+        bJ = int(po.nbf[J])
+        parts = []
+        for p in range(po.nb_ptr[J], po.nb_ptr[J + 1]):
+            I = int(po.nb_idx[p])
+            bI = int(po.nbf[I])
+            q = po.nb_ptr[I] + int(np.nonzero(po.nb_idx[po.nb_ptr[I]:po.nb_ptr[I + 1]] == J)[0][0])
+            parts.append((int(po.nb_off[p]), bI, int(off[q])))
+            idx.append(np.arange(off[q], off[q] + bI * bJ, dtype=np.int64))
+        n = sum(bI for _, bI, _ in parts)
+        where[J] = (pos, parts, bJ)
+        pos += n * bJ
+    return np.concatenate(idx), where
 
+
+def sampled_errors(D_dev, po, subs, ref):
+    """{J: max|dD|} over the blocks (I, J), I in N(J), of the listed submatrices: the device D (merged
+    pattern) against the oracle's centre columns ref[J][0]."""
+    import numpy as np
+    import torch
+    idx, where = d_elements(po, subs)
+    got = D_dev.index_select(0, torch.from_numpy(idx).to(D_dev.device)).cpu().numpy()
+    out = {}
+    for J in subs:
+        pos, parts, bJ = where[J]
+        cols = ref[J][0]
+        err = 0.0
+        for r0, bI, _ in parts:
+            blk = got[pos:pos + bI * bJ].reshape(bI, bJ)
+            pos += bI * bJ
+            err = max(err, float(np.max(np.abs(blk - cols[r0:r0 + bI, :]))))
+        out[J] = err
+    return out
+
+
+def learned_bounds_leg(nl, synth, dsys, plan_sub_range, mu_star, precision, dev, ora_factory):
+    """a4/a10, the learned spectral-bound experiment: the network is trained on samples the method produces
+    on 100,000 submatrices of this system (power-iteration interval and step counts, three chemical
+    potentials around mu*), then Gershgorin, power and learned bounds are compared on a fresh system of
+    65,536 molecules with 6 or 23 functions (50/50) at mu*: Newton-Schulz steps, sign time, reruns, and the
+    error of D against the FP64 oracle on sampled submatrices."""
+    import numpy as np
     import torch
     o = nl.options(precision)
+    n_train = min(100000, plan_sub_range)
     plan = nl.nolsm_build_submatrices(dsys)
     t0 = time.perf_counter()
     xs, ts = [], []
-    for dmu in (-0.05, 0.0, 0.05):
-        x, t = nl.nolsm_training_data(plan, mu_star + dmu, o)
-        xs.append(x)
-        ts.append(t)
+    thirds = [(k * n_train // 3, (k + 1) * n_train // 3) for k in range(3)]
+    for dmu, (a, b) in zip((-0.05, 0.0, 0.05), thirds):
+        ob = nl.options(precision, sub_begin=a, sub_end=b)
+        x, t = nl.nolsm_training_data(plan, mu_star + dmu, ob)
+        xs.append(x[a:b])
+        ts.append(t[a:b])
     x, t = torch.cat(xs), torch.cat(ts)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
@@ -266,14 +320,20 @@ def bound_sources_leg(nl, synth, spec_name, dsys, mu_star, precision, dev):
     t0 = time.perf_counter()
     losses = mlp.train(x, t, epochs=30, batch=1024, lr=2e-3)
     t_train = time.perf_counter() - t0
-    spec = getattr(synth, spec_name)()
-    fresh = synth.make_system(dataclasses.replace(spec, seed=spec.seed + 1000))
+    fresh = synth.make_system(synth.spec_mixed())
     p2 = nl.nolsm_build_submatrices(nl.DeviceSystem(fresh, dev))
     nl.nolsm_plan_set_mlp(p2, mlp)
-    out = {"training_samples": int(x.shape[0]), "epochs": 30, "batch": 1024,
-           "loss_first_last": [losses[0], losses[-1]], "s_training_data": t_data, "s_training": t_train,
-           "evaluated_on": f"fresh system of the same workload (seed {spec.seed + 1000}), mu*"}
-    ref = None
+    out = {"training_submatrices": int(x.shape[0]), "trained_on": "the benchmark system, submatrices 0..%d, "
+           "power-iteration targets at mu* - 0.05, mu*, mu* + 0.05 (a third each)" % n_train,
+           "epochs": 30, "batch": 1024, "loss_first_last": [losses[0], losses[-1]], "s_training_data": t_data,
+           "s_training": t_train,
+           "evaluated_on": "fresh water-like lattice, 65536 molecules (64x32x32), 6 or 23 functions (50/50), "
+                           "seed %d, at mu*" % synth.spec_mixed().seed}
+    ora = ora_factory(fresh)
+    rng = np.random.default_rng(5)
+    subs = sorted(int(j) for j in rng.choice(fresh.n_mol, size=48, replace=False))
+    ref, _ = ora.solve(subs, mu_star)
+    ora.close()
     for name, b in (("gershgorin", nl.BOUND_GERSHGORIN), ("power", nl.BOUND_POWER), ("mlp", nl.BOUND_MLP)):
         ob = nl.options(precision, bound_source=b)
         nl.nolsm_solve_batch(p2, mu_star, ob, check=False)          # geometry caches, power bounds
@@ -284,14 +344,15 @@ def bound_sources_leg(nl, synth, spec_name, dsys, mu_star, precision, dev):
         dt = time.perf_counter() - t0
         s2 = p2.stats()
         D = p2.scatter()
-        if ref is None:
-            ref = D.clone()
+        errs = sampled_errors(D, ora.plan, subs, ref)
         out[name] = {"mean_ns_steps": float(r.iters.float().mean()), "ms_sign": s2["ms_sign"],
                      "ms_solve_call": dt * 1e3, "submatrices_per_s_one_mu": fresh.n_mol / dt,
                      "reruns": int(s2["reruns"]), "status": int(r.status),
                      "not_converged": int((r.sub_status != 0).sum()),
-                     "max_abs_dD_vs_gershgorin": float((D - ref).abs().max())}
+                     "max_abs_dD_vs_oracle_sampled": max(errs.values())}
     p2.close()
+    out["steps_saved_vs_power"] = out["power"]["mean_ns_steps"] - out["mlp"]["mean_ns_steps"]
+    out["steps_saved_vs_gershgorin"] = out["gershgorin"]["mean_ns_steps"] - out["mlp"]["mean_ns_steps"]
     return out
 
 
@@ -304,10 +365,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3")
-    ap.add_argument("--workload", default="batched_uneven", choices=list(WORKLOADS))
-    ap.add_argument("--sample", type=int, default=640, help="oracle submatrices for accuracy and CPU baseline")
+    ap.add_argument("--workload", default="streamed_bf16", choices=list(WORKLOADS))
+    ap.add_argument("--batches", type=int, default=8, help="molecule batches the errors are reported for")
+    ap.add_argument("--sample", type=int, default=640, help="oracle submatrices (errors and CPU baseline)")
     ap.add_argument("--ref-sample", type=int, default=96, help="submatrices per reference-arm step")
-    ap.add_argument("--no-extra", action="store_true", help="skip the per-precision side measurements")
+    ap.add_argument("--no-extra", action="store_true", help="skip the per-precision and learned-bound legs")
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU oracle (profiling runs)")
     args = ap.parse_args()
     spec_name, desc = WORKLOADS[args.workload]
@@ -323,12 +385,6 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
 
     # weak scaling: with N ranks the lattice is N times longer along x and rank r owns the r-th slab of
     # the one-GPU workload's size (molecule index runs fastest along z, slowest along x)
@@ -339,6 +395,16 @@ def main():
     sysm = synth.make_system(spec)
     n_mol = sysm.n_mol
     n_occ = sysm.n_occ
+    workers = max(1, os.cpu_count() or 1)
+    # the oracle's worker pool (spawned) and plan, before the first GPU call
+    ora = OracleSample(sysm, workers) if (rank == 0 and not args.no_oracle) else None
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     peaks = measured_peaks()
     opts = nl.options(args.precision)
 
@@ -403,6 +469,7 @@ def main():
     d_host = torch.empty(info.d_nvals, dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = d_host.numel() * 8
+    D_e2e = torch.zeros_like(D)
 
     class _Sys:  # DeviceSystem built from already-copied device tensors
         pass
@@ -415,9 +482,9 @@ def main():
         e.struct = lambda: nl.DeviceSystem.struct(e)
         plan = nl.nolsm_build_submatrices(e)
         r_ = find_mu(plan)
-        plan.scatter(D)
+        plan.scatter(D_e2e)
         plan.close()
-        d_host.copy_(D, non_blocking=True)
+        d_host.copy_(D_e2e, non_blocking=True)
         return r_
 
     e2e_step()
@@ -434,30 +501,35 @@ def main():
 
     st = stats_all[-1]
     launches = int(np.mean([s["launches"] for s in stats_all]))
-    ms_sign = statistics.mean(s["ms_sign"] for s in stats_all)
-    ms_factor = statistics.mean(s["ms_factor"] for s in stats_all)
-    fl_fp32 = statistics.mean(s["flops_fp32"] for s in stats_all)
-    fl_tensor = statistics.mean(s["flops_tensor"] for s in stats_all)
-    fl_paper = statistics.mean(s["flops_paper"] for s in stats_all)
-    fl_padded = statistics.mean(s["flops_tensor_padded"] for s in stats_all)
+    mean = lambda k: statistics.mean(s[k] for s in stats_all)
+    ms_sign, ms_factor = mean("ms_sign"), mean("ms_factor")
+    fl_paper, fl_tensor, fl_padded, fl_fp32 = (mean("flops_paper"), mean("flops_tensor"),
+                                               mean("flops_tensor_padded"), mean("flops_fp32"))
     evals = st["solves"]
     fp64_path = args.precision == "fp64"
-    achieved = fl_tensor / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0
+    tf = lambda fl, ms: fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
     peak = peaks["bf16_sustained"]
-    # launches of the factorisation kernel per step: one per preparation chunk
     chunks = max(1, int(st["factor_launches"]))
     roof_sign = {"bound": "tensor" if not fp64_path else "alu", "kernel": "k_ns_tc (sign iteration)",
-                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                 "traffic": kernel_traffic("k_ns_tc", n_mol),
+                 "achieved": tf(fl_paper, ms_sign), "peak": peak, "unit": "TFLOP/s",
+                 "frac": tf(fl_paper, ms_sign) / peak if peak else None,
+                 "traffic": kernel_traffic("k_ns_tc", j1 - j0),
                  "peak_source": peaks["source"] + " bf16 sustained (kernel timed inside a long step)",
-                 "algorithmic": "tensor flops the products need: (1 or 3 terms) x 2 n^3 per product, "
-                                "2 products per Newton-Schulz step, unpadded n"}
+                 "algorithmic": "4 k n^3 flops per submatrix (2 n^3 per product, 2 products per Newton-Schulz "
+                                "step, k steps, unpadded n; Sec. 'FLOPs in the NOLSM method'), k counted per "
+                                "submatrix, summed over the step's bisection points",
+                 "achieved_tensor_issued": tf(fl_tensor, ms_sign),
+                 "achieved_tensor_issued_note": "the products the arithmetic needs: x3 for three-term split "
+                                                "steps, unpadded n",
+                 "achieved_padded": tf(fl_padded, ms_sign),
+                 "achieved_padded_note": "split products on the padded tiles the kernel executes"}
     if not fp64_path and ms_factor > ms_sign:
-        ach_f = fl_fp32 / (ms_factor / 1e3) / 1e12 if ms_factor > 0 else 0.0
-        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, double-FP32 refinement of Q)",
+        ach_f = tf(fl_fp32, ms_factor)
+        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, double-FP32 "
+                                              "refinement of Q)",
                     "achieved": ach_f, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
-                    "traffic": kernel_traffic("k_prepare_mixed", n_mol / chunks), "launches_per_step": chunks,
+                    "traffic": kernel_traffic("k_prepare_mixed", (j1 - j0) / chunks), "launches_per_step": chunks,
                     "peak_source": "FP32 SIMT peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
                     "algorithmic": "FP32 flops 2 (n^3/3 + n^3 + 3 n^2 b) per submatrix: Cholesky, the two "
                                    "triangular solves for A, the Q solve, its residual and correction"}
@@ -465,22 +537,51 @@ def main():
         roofline = roof_sign
 
     extra = {"mu": mu_star, "trace_DS": r.trace_DS, "n_occ": n_occ, "bisection_points": evals,
-             "ms_phases": {k: statistics.mean(s[k] for s in stats_all)
-                           for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_sign", "ms_reduce",
-                                     "ms_scatter")},
-             "sign_tflops_paper_convention": fl_paper / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0,
-             "sign_tflops_tensor_padded": fl_padded / (ms_sign / 1e3) / 1e12 if ms_sign > 0 else 0.0,
+             "ms_phases": {k: mean(k) for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_sign",
+                                                 "ms_reduce", "ms_scatter")},
              "ns_steps_per_submatrix": st["ns_steps"] / max(1, st["sub_solves"]),
              "submatrix_n": [info.min_n, info.max_n]}
+
+    # accuracy of the headline result (the D of the last timed step) against the FP64 oracle, batch by
+    # batch (contiguous molecule ranges), and the CPU baseline on the same sample
+    nb = max(1, args.batches)
+    rng = np.random.default_rng(7)
+    per = max(1, min(n_mol // nb, args.sample // nb))
+    batches = [(b * n_mol // nb, (b + 1) * n_mol // nb) for b in range(nb)]
+    sample = sorted({int(j) for a, b in batches for j in rng.choice(np.arange(a, b), size=per, replace=False)})
+    ref, cpu_subs_per_s, errors = {}, None, None
+    if ora is not None:
+        ref, dt_cpu = ora.solve(sample, mu_star)
+        cpu_subs_per_s = len(sample) / dt_cpu / max(1, evals)
+        # per-submatrix traces at mu* from the library (same mode), for the trace errors
+        plan = nl.nolsm_build_submatrices(dsys)
+        rr = nl.nolsm_solve_batch(plan, mu_star, opts, check=False)
+        tS_gpu, tH_gpu = rr.sub_t_S.cpu().numpy(), rr.sub_t_H.cpu().numpy()
+        plan.close()
+        errs = sampled_errors(D, ora.plan, sample, ref)
+        errors = []
+        for b, (a, e) in enumerate(batches):
+            js = [J for J in sample if a <= J < e]
+            sS = sum(ref[J][1] for J in js)
+            sH = sum(ref[J][2] for J in js)
+            errors.append({"batch": b, "molecules": [a, e], "sampled": len(js),
+                           "max_abs_dD": max(errs[J] for J in js),
+                           "rel_err_tr_DH": abs(sum(tH_gpu[J] for J in js) - sH) / abs(sH),
+                           "rel_err_tr_DS": abs(sum(tS_gpu[J] for J in js) - sS) / abs(sS),
+                           "max_rel_err_t_H": max(abs(tH_gpu[J] - ref[J][2]) / abs(ref[J][2]) for J in js)})
+        extra["errors_per_batch"] = errors
+        extra["errors_worst"] = {k: max(x[k] for x in errors) for k in
+                                 ("max_abs_dD", "rel_err_tr_DH", "rel_err_tr_DS", "max_rel_err_t_H")}
 
     # side measurements: one solve at mu* per precision (whole system; FP64 on a range), accuracy
     paths = {}
     if not args.no_extra:
         plan = nl.nolsm_build_submatrices(dsys)
+        fp64_range = (0, min(n_mol, 2 * 152 * 4))
         for prec in ["fp32", "bf16x3", "fp16", "bf16", "fp8e4m3", "fp64"]:
             o = nl.options(prec)
             if prec == "fp64":
-                o.sub_begin, o.sub_end = 0, min(n_mol, 2 * 152 * 4)
+                o.sub_begin, o.sub_end = fp64_range
             nl.nolsm_solve_batch(plan, mu_star, o, check=False)      # prepares the geometry caches
             plan.stats_reset()
             torch.cuda.synchronize()
@@ -489,13 +590,21 @@ def main():
             dt = time.perf_counter() - t0
             s2 = plan.stats()
             cnt = (o.sub_end or n_mol) - o.sub_begin
-            paths[prec] = {"submatrices_per_s_one_mu": cnt / dt, "ms_sign": s2["ms_sign"], "status": rr.status,
-                           "sign_tflops_paper": s2["flops_paper"] / (s2["ms_sign"] / 1e3) / 1e12,
-                           "tensor_tflops": (s2["flops_tensor"] / (s2["ms_sign"] / 1e3) / 1e12
-                                             if prec != "fp64" else None),
-                           "_Dc": {}}
-            paths[prec]["_D"] = plan.scatter().cpu().numpy()
+            pth = {"submatrices_per_s_one_mu": cnt / dt, "ms_sign": s2["ms_sign"], "status": rr.status,
+                   "sign_tflops_paper": tf(s2["flops_paper"], s2["ms_sign"]),
+                   "tensor_tflops_issued": tf(s2["flops_tensor"], s2["ms_sign"]) if prec != "fp64" else None}
+            if ref:
+                Dp = plan.scatter()
+                subs = [J for J in sample if (prec != "fp64" or J < fp64_range[1])][:96]
+                if subs:
+                    pth["max_abs_dD_sampled"] = max(sampled_errors(Dp, ora.plan, subs, ref).values())
+                    pth["sampled_submatrices"] = len(subs)
+                del Dp
+            paths[prec] = pth
         plan.close()
+        fp64_rate = paths["fp64"]["submatrices_per_s_one_mu"]
+        for pth in paths.values():
+            pth["speedup_vs_fp64_path"] = pth["submatrices_per_s_one_mu"] / fp64_rate
 
     # energy-weighted density matrix T_J(W) = T_J(D) T_J(H0) T_J(D) at mu* (once per geometry, after the
     # bisection; not part of the timed step): the kernel alone, timed by the library's CUDA events
@@ -523,6 +632,7 @@ def main():
                          "peak_source": peaks["source"] + " HBM copy bandwidth",
                          "algorithmic": "FP32 A_J read once (n^2 x 4 B), D_c and the centre columns of "
                                         "T_J(S) read and W_c written (3 n b x 8 B) per submatrix"}}
+        del W
         plan.close()
 
     # submatrix combination heuristic (host planning step, Eq. combination_criterion) on an atom-resolved
@@ -541,50 +651,12 @@ def main():
                        "host_s": dt_c, "host_threads": os.cpu_count()}
 
     bounds = {}
-    if not args.no_extra and not fp64_path:
-        bounds = bound_sources_leg(nl, synth, spec_name, dsys, mu_star, args.precision, dev)
+    if not args.no_extra and not fp64_path and ora is not None:
+        bounds = learned_bounds_leg(nl, synth, dsys, j1 - j0, mu_star, args.precision, dev,
+                                    lambda s_: OracleSample(s_, workers))
+    if ora is not None:
+        ora.close()
 
-    # oracle: accuracy on a sample at mu* and the CPU baseline
-    workers = max(1, os.cpu_count() or 1)
-    rng = np.random.default_rng(7)
-    sample = sorted(int(j) for j in rng.choice(n_mol, size=min(n_mol, args.sample), replace=False))
-    ref, cpu_subs_per_s = {}, None
-    if not args.no_oracle:
-        pool = oracle_pool(spec_name, {}, workers)
-        pool.map(_oracle_gersh, [[0]] * workers)   # warm the workers (system generation) before timing
-        ref, dt_cpu = run_oracle(pool, sample, mu_star, workers)
-        pool.close()
-        cpu_subs_per_s = len(sample) / dt_cpu / max(1, evals)
-
-    if paths and ref:
-        from oracle import nolsm_oracle as orc
-        po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
-        off = orc.d_block_offsets(po)
-        acc_sample = sample[:64]
-        for prec, pth in paths.items():
-            Dn = pth["_D"]
-            lim = (0, 2 * 152 * 4) if prec == "fp64" else (0, n_mol)
-            err, rel_tH = 0.0, 0.0
-            subs = [J for J in acc_sample if lim[0] <= J < lim[1]] or [J for J in range(lim[1]) if J in ref][:8]
-            for J in subs:
-                if J not in ref:
-                    continue
-                cols, tS_ref, tH_ref = ref[J]
-                for p in range(po.nb_ptr[J], po.nb_ptr[J + 1]):
-                    I = int(po.nb_idx[p])
-                    q = po.nb_ptr[I] + int(np.nonzero(po.nb_idx[po.nb_ptr[I]:po.nb_ptr[I + 1]] == J)[0][0])
-                    got = Dn[off[q]:off[q + 1]].reshape(6, 6)
-                    err = max(err, float(np.max(np.abs(got - cols[po.nb_off[p]:po.nb_off[p] + 6, :]))))
-            pth["max_abs_dD_sampled"] = err
-            pth["sampled_submatrices"] = len(subs)
-    if paths:
-        fp64_rate = paths["fp64"]["submatrices_per_s_one_mu"]
-        for prec, pth in paths.items():
-            pth["speedup_vs_fp64_path"] = pth["submatrices_per_s_one_mu"] / fp64_rate
-
-    for pth in paths.values():
-        pth.pop("_D", None)
-        pth.pop("_Dc", None)
     line = {
         "metric": METRIC,
         "value": value, "unit": "submatrices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -595,19 +667,20 @@ def main():
         "config": {"workload": desc if world == 1 else f"{desc}; lattice {world}x longer along x, one slab per GPU",
                    "precision": args.precision, "molecules": n_mol, "molecules_per_gpu": n_mol // world,
                    "l2": "inputs larger than L2 (block-CSR S and H, %.0f MB each)" % (sysm.S.vals.nbytes / 1e6),
-                   "bracket": "Gershgorin interval of all submatrices"},
+                   "bracket": "Gershgorin interval of all submatrices",
+                   "batches": f"{nb} contiguous molecule ranges, errors reported per range"},
         "e2e": {"value": n_mol / (ms_e2e / 1e3), "unit": "submatrices/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "roofline_sign": roof_sign,
         "cpu_baseline": {"value": cpu_subs_per_s, "unit": "submatrices/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{len(sample)} submatrices solved once at the final mu, divided by the "
-                                   f"{evals} bisection points of a step"},
+                         "sample": f"{len(sample)} submatrices ({per} per batch) gathered and solved once at the "
+                                   f"final mu, divided by the {evals} bisection points of a step"},
         "clocks": clk.summary(),
         "extra": extra,
         "paths_one_mu": paths,
-        "bound_sources": bounds,
+        "learned_bounds": bounds,
         "energy_weighted": energy_weighted,
         "combination": combination,
     }

@@ -49,8 +49,11 @@ typedef enum {
   NOLSM_ERR_TIMEOUT = 10       /* a bounded device-side wait gave up (the kernel returned early) */
 } nolsm_status;
 
-/* Arithmetic of the sign-iteration products (a5/a6). The overlap factorisation, the centre columns of
- * T_J(S)^-1 and all trace sums are FP64 in every mode.
+/* Arithmetic of the sign-iteration products (a5/a6). The trace sums are FP64 in every mode. The overlap
+ * factorisation is FP64 in NOLSM_FP64; the tensor-core modes factor T_J(S) in FP32, form A_J with FP32
+ * solves, and refine the centre columns of T_J(S)^-1 with a double-FP32 residual (about 48 bits) to about
+ * 1e-12 relative; a submatrix whose refinement does not contract, or whose overlap is too ill-conditioned
+ * for the FP32 factor, is prepared again with the FP64 factorisation.
  *   NOLSM_FP64       every step in FP64 on the CUDA cores (the plain reference path).
  *   NOLSM_FP32       every Newton-Schulz product as a three-term split of FP16 tensor-core products
  *                    (hi*hi + hi*lo + lo*hi, FP32 accumulation): about 22 significant bits.
@@ -252,6 +255,33 @@ nolsm_status nolsm_bisect_point(nolsm_plan* plan, double mu, const nolsm_options
                                 double* trace_DS, int32_t* solved);
 nolsm_status nolsm_bisect_side(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, int32_t raises_lo);
 
+/* The bisection rule itself (Sec. "Simulation Details": mu by bisection for charge neutrality) as host
+ * arithmetic only: no CUDA call, no plan, callable without a GPU. nolsm_find_mu and callers that sum
+ * Tr(DS) over several ranks take every decision through these two calls, so all of them visit the same
+ * points.
+ * nolsm_bisection_start: bracket [lo, hi] (host scalars, lo < hi) for n_occ occupied orbitals; sets
+ *   mu = (lo + hi) / 2, steps = 0, state = NOLSM_BISECT_EVALUATE. NOLSM_ERR_ARG on non-finite input or
+ *   lo >= hi.
+ * nolsm_bisection_update: after the point at b->mu with the total Tr(DS) there (summed over every rank's
+ *   submatrices): steps += 1, f = trace_DS - n_occ; |f| <= tol_n |n_occ| accepts mu (state
+ *   NOLSM_BISECT_ACCEPTED); otherwise mu becomes the bracket's lower end when f < 0 (*raises_lo = 1),
+ *   else its upper end (*raises_lo = 0; pass it to nolsm_bisect_side), and the bisection stops (state
+ *   NOLSM_BISECT_NO_PLATEAU) when hi - lo <= tol_mu or steps >= max_bisect (100 when <= 0), or goes on
+ *   at the new midpoint (state NOLSM_BISECT_EVALUATE, mu updated). raises_lo (host) may be NULL. */
+enum { NOLSM_BISECT_ACCEPTED = 0, NOLSM_BISECT_EVALUATE = 1, NOLSM_BISECT_NO_PLATEAU = 2 };
+typedef struct {
+  double lo, hi;      /* current bracket */
+  double mu;          /* the point to evaluate next (EVALUATE) or the last one evaluated */
+  double n_occ;       /* target Tr(DS) */
+  double trace_DS;    /* total Tr(DS) at the last evaluated point */
+  int32_t steps;      /* points evaluated */
+  int32_t state;      /* NOLSM_BISECT_* */
+} nolsm_bisection;
+
+nolsm_status nolsm_bisection_start(nolsm_bisection* b, double n_occ, double lo, double hi);
+nolsm_status nolsm_bisection_update(nolsm_bisection* b, double trace_DS, const nolsm_options* opts,
+                                    int32_t* raises_lo);
+
 /* The union [lo, hi] of the Gershgorin intervals of A_J = T_J(S)^-1 T_J(H0) over the options' range
  * of submatrices (prepares a1-a3 for the range first): a bracket of every submatrix eigenvalue, used
  * as the default bisection bracket (Sec. "Simulation Details" gives no bracket). lo, hi: host. */
@@ -382,9 +412,12 @@ nolsm_status nolsm_training_data(nolsm_plan* plan, double mu, const nolsm_option
  *   mu, opts (precision NOLSM_FP32, NOLSM_BF16X3 or NOLSM_BF16; tolerances, caps; range fields unused).
  * Outputs (device, caller-owned): Dc (n_i x b_i at c_off[i], the centre columns of T(D)), t_S[i], t_H[i],
  *   iters[i], status[i] (per-submatrix nolsm_status).
- * Limits: 1 <= count <= 4096 and every n_i <= 192, else NOLSM_ERR_UNSUPPORTED with a message; the sizes
- * are read back to the host first (this synchronises the stream), then the work is enqueued and the call
- * returns; results are ready when the stream reaches that point.
+ * Limits: 1 <= count <= 4096 and every n_i <= 192, else NOLSM_ERR_UNSUPPORTED with a message. To check
+ * the dimensions the call copies sub_n to the host and synchronises the stream (work enqueued on it
+ * earlier completes first); then it enqueues the solve and returns without waiting: results are ready
+ * when the stream reaches that point. Every status[i] is first set to NOLSM_ERR_TIMEOUT on the stream and
+ * overwritten by the kernel when it finishes submatrix i, so a submatrix left undone after a device-side
+ * wait gave up reads as timed out.
  * The first call on a device looks up the device address of the static array; make that first call
  * before any stream capture. All calls share the one array (the call resets its counters on the stream
  * first), so calls that overlap on the GPU, from different streams or host threads on one device, race:

@@ -31,6 +31,15 @@ class NolsmOptions(ctypes.Structure):
                 ("symmetric_form", c_int32)]
 
 
+class NolsmBisection(ctypes.Structure):
+    _fields_ = [("lo", c_double), ("hi", c_double), ("mu", c_double), ("n_occ", c_double), ("trace_DS", c_double),
+                ("steps", c_int32), ("state", c_int32)]
+
+
+# nolsm_bisection.state
+BISECT_ACCEPTED, BISECT_EVALUATE, BISECT_NO_PLATEAU = range(3)
+
+
 class NolsmPlanInfo(ctypes.Structure):
     _fields_ = [("n_mol", c_int32), ("d_nnzb", c_int64), ("d_nvals", c_int64), ("max_n", c_int32),
                 ("min_n", c_int32), ("sum_n3", c_double), ("device_bytes", c_int64)]
@@ -71,6 +80,9 @@ SIGNATURES = [
     ("nolsm_bisect_point", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
                                      ctypes.POINTER(c_double), ctypes.POINTER(c_int32)]),
     ("nolsm_bisect_side", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_int32]),
+    ("nolsm_bisection_start", c_int32, [ctypes.POINTER(NolsmBisection), c_double, c_double, c_double]),
+    ("nolsm_bisection_update", c_int32, [ctypes.POINTER(NolsmBisection), c_double, ctypes.POINTER(NolsmOptions),
+                                         ctypes.POINTER(c_int32)]),
     ("nolsm_plan_stats", c_int32, [c_void_p, ctypes.POINTER(NolsmStats)]),
     ("nolsm_plan_stats_reset", c_int32, [c_void_p]),
     ("nolsm_plan_destroy", None, [c_void_p]),

@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsArgs g) {
 __global__ void __launch_bounds__(256) k_reduce(int32_t j0, int32_t j1, const double* __restrict__ tS,
                                                 const double* __restrict__ tH, const int32_t* __restrict__ status,
                                                 const int32_t* __restrict__ iters, const int32_t* __restrict__ rsteps,
-                                                const int32_t* __restrict__ sub_n, int terms_main, double* out) {
+                                                const int32_t* __restrict__ sub_n, int terms_main,
+                                                const int32_t* __restrict__ list, int32_t count, double* out) {
   __shared__ double red[33];
   __shared__ int first[256];
   double a = 0.0, b = 0.0, w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
@@ -298,6 +299,12 @@ __global__ void __launch_bounds__(256) k_reduce(int32_t j0, int32_t j1, const do
     a += tS[J];
     b += tH[J];
     if (status[J] != 0 && J < f) f = J;
+  }
+  // work counters over the submatrices this call solved (the list, else the whole range): submatrices
+  // kept from an earlier solve are not counted again
+  const int32_t m = list ? count : j1 - j0;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    const int J = list ? list[e] : j0 + e;
     const double n = sub_n[J];
     const double n64 = (double)((sub_n[J] + 63) & ~63), R = (double)((sub_n[J] + 127) & ~127);
     const double prod = (double)terms_main * (iters[J] - rsteps[J]) + 3.0 * rsteps[J];
@@ -537,10 +544,10 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
 }
 
 nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
-                           double* tH, int32_t* first_bad_status) {
+                           double* tH, int32_t* first_bad_status, const int32_t* list, int32_t count) {
   k_reduce<<<1, 256, 0, st>>>((int32_t)j0, (int32_t)j1, plan->t_S.as<double>(), plan->t_H.as<double>(),
                               plan->status.as<int32_t>(), plan->iters.as<int32_t>(), plan->rsteps.as<int32_t>(),
-                              plan->sub_n.as<int32_t>(), terms_main, plan->sums.as<double>());
+                              plan->sub_n.as<int32_t>(), terms_main, list, count, plan->sums.as<double>());
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 1;
   double h[8];

@@ -309,7 +309,7 @@ static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options*
   mark(plan, 2, st);
   double tS = 0, tH = 0;
   int32_t bad = 0;
-  NOLSM_TRY(reduce_traces(plan, j0, j1, fp64 ? 1 : main_terms(opts->precision), st, &tS, &tH, &bad));
+  NOLSM_TRY(reduce_traces(plan, j0, j1, fp64 ? 1 : main_terms(opts->precision), st, &tS, &tH, &bad, list, count));
   mark(plan, 3, st);
   const size_t cnt = (size_t)(j1 - j0);
   if (sub_t_S) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_t_S + j0, plan->t_S.as<double>() + j0, 8 * cnt, cudaMemcpyDeviceToDevice, st));
@@ -501,6 +501,46 @@ nolsm_status nolsm_bisect_side(nolsm_plan* plan, const nolsm_options* opts, nols
   return NOLSM_OK;
 }
 
+nolsm_status nolsm_bisection_start(nolsm_bisection* b, double n_occ, double lo, double hi) {
+  if (!b || !std::isfinite(n_occ) || !std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) {
+    set_error("nolsm_bisection_start: invalid bracket [%g, %g] or n_occ %g", lo, hi, n_occ);
+    return NOLSM_ERR_ARG;
+  }
+  b->lo = lo;
+  b->hi = hi;
+  b->mu = 0.5 * (lo + hi);
+  b->n_occ = n_occ;
+  b->trace_DS = 0.0;
+  b->steps = 0;
+  b->state = NOLSM_BISECT_EVALUATE;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_bisection_update(nolsm_bisection* b, double trace_DS, const nolsm_options* opts,
+                                    int32_t* raises_lo) {
+  if (!b || !opts || b->state != NOLSM_BISECT_EVALUATE || !std::isfinite(trace_DS)) {
+    set_error("nolsm_bisection_update: no point to decide on, or a non-finite Tr(DS)");
+    return NOLSM_ERR_ARG;
+  }
+  b->steps += 1;
+  b->trace_DS = trace_DS;
+  const double f = trace_DS - b->n_occ;
+  if (std::fabs(f) <= opts->tol_n * std::fabs(b->n_occ)) {
+    b->state = NOLSM_BISECT_ACCEPTED;
+    return NOLSM_OK;
+  }
+  const int below = f < 0.0 ? 1 : 0;
+  if (raises_lo) *raises_lo = below;
+  if (below) b->lo = b->mu; else b->hi = b->mu;
+  const int cap = opts->max_bisect > 0 ? opts->max_bisect : 100;
+  if (b->hi - b->lo <= opts->tol_mu || b->steps >= cap) {
+    b->state = NOLSM_BISECT_NO_PLATEAU;
+    return NOLSM_OK;
+  }
+  b->mu = 0.5 * (b->lo + b->hi);
+  return NOLSM_OK;
+}
+
 nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi, const nolsm_options* opts,
                            nolsm_stream_t stream, double* mu_out, double* trace_DS_out, int32_t* steps_out,
                            double* mu_history) {
@@ -512,28 +552,33 @@ nolsm_status nolsm_find_mu(nolsm_plan* plan, double n_occ, double lo, double hi,
   if (default_bracket) {
     NOLSM_TRY(nolsm_spectral_bracket(plan, opts, stream, &lo, &hi));
   }
-  const int max_steps = opts->max_bisect > 0 ? opts->max_bisect : 100;
   NOLSM_TRY(nolsm_bisect_begin(plan, opts, stream, default_bracket ? 1 : 0));
-  double mu = 0.5 * (lo + hi), t = 0.0;
-  nolsm_status result = NOLSM_ERR_NO_PLATEAU;
-  int step = 0;
-  while (step < max_steps) {
-    mu = 0.5 * (lo + hi);
+  nolsm_bisection b;
+  NOLSM_TRY(nolsm_bisection_start(&b, n_occ, lo, hi));
+  nolsm_status result = NOLSM_OK;
+  double mu = b.mu;
+  while (b.state == NOLSM_BISECT_EVALUATE) {
+    mu = b.mu;
+    double t = 0.0;
     nolsm_status s = nolsm_bisect_point(plan, mu, opts, stream, &t, nullptr);
-    if (mu_history) mu_history[step] = mu;
-    ++step;
-    if (s != NOLSM_OK) { result = s; break; }
-    const double f = t - n_occ;
-    if (std::fabs(f) <= opts->tol_n * std::fabs(n_occ)) { result = NOLSM_OK; break; }
-    NOLSM_TRY(nolsm_bisect_side(plan, opts, stream, f < 0.0 ? 1 : 0));
-    if (f < 0.0) lo = mu; else hi = mu;
-    if (hi - lo <= opts->tol_mu) break;
+    if (mu_history) mu_history[b.steps] = mu;
+    if (s != NOLSM_OK) {   // the point itself failed: report it at that mu
+      b.steps += 1;
+      b.trace_DS = t;
+      result = s;
+      break;
+    }
+    int32_t raises_lo = 0;
+    NOLSM_TRY(nolsm_bisection_update(&b, t, opts, &raises_lo));
+    if (b.state != NOLSM_BISECT_ACCEPTED) NOLSM_TRY(nolsm_bisect_side(plan, opts, stream, raises_lo));
   }
+  if (result == NOLSM_OK && b.state == NOLSM_BISECT_NO_PLATEAU) result = NOLSM_ERR_NO_PLATEAU;
   if (mu_out) *mu_out = mu;
-  if (trace_DS_out) *trace_DS_out = t;
-  if (steps_out) *steps_out = step;
+  if (trace_DS_out) *trace_DS_out = b.trace_DS;
+  if (steps_out) *steps_out = b.steps;
   if (result == NOLSM_ERR_NO_PLATEAU)
-    set_error("nolsm_find_mu: stopped after %d evaluations at mu=%.12g with Tr(DS)=%.9f, target %.9f", step, mu, t, n_occ);
+    set_error("nolsm_find_mu: stopped after %d evaluations at mu=%.12g with Tr(DS)=%.9f, target %.9f", b.steps, mu,
+              b.trace_DS, n_occ);
   return result;
 }
 

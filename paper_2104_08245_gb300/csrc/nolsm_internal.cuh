@@ -183,8 +183,9 @@ void pmark(nolsm_plan* plan, cudaStream_t st);
 void prep_times(nolsm_plan* plan);
 
 // shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
+// (the work counters cover list[0, count) when list is set: the submatrices the call solved)
 nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_main, cudaStream_t st, double* tS,
-                           double* tH, int32_t* first_bad_status);
+                           double* tH, int32_t* first_bad_status, const int32_t* list = nullptr, int32_t count = 0);
 // write-back of centre columns (default: those of T_J(D)) into the merged pattern
 nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st,
                      const double* src = nullptr);

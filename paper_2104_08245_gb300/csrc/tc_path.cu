@@ -26,6 +26,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "nolsm_internal.cuh"
@@ -802,6 +803,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// Every submatrix of the launch starts as "timed out": the sign kernel overwrites the status of each one it
+// takes, so a submatrix that no block reached (every block gave up on a bounded wait) is reported as such
+// instead of keeping the status of an earlier solve.
+__global__ void k_status_pending(int32_t j0, int32_t count, const int32_t* __restrict__ list,
+                                 int32_t* __restrict__ status) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    status[list ? list[e] : j0 + e] = kSubTimeout;
+}
+
 }  // namespace
 
 // ==================================================================================== host side
@@ -938,9 +948,12 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     set_error("cuTensorMapEncodeTiled rejected the one-byte scratch layout");
     return NOLSM_ERR_CUDA;
   }
+  k_status_pending<<<(unsigned)std::min<int64_t>(1024, (work + 255) / 256), 256, 0, st>>>(
+      (int32_t)j0, (int32_t)work, spec.list, plan->status.as<int32_t>());
+  NOLSM_LAUNCH_CHECK();
   k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, g);
   NOLSM_LAUNCH_CHECK();
-  plan->stats.launches += 1;
+  plan->stats.launches += 2;
   if (sym) {   // D_c = L^-T U and the traces
     SymArgs a;
     a.j0 = (int32_t)j0;
@@ -978,8 +991,10 @@ constexpr size_t kNaBytes = kNaPlanesBytes + kNaIntBytes;   // about 4.8 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
-// Identity work order, zero factorisation status, zero counters: what the kernel expects to find.
-__global__ void k_noalloc_reset(unsigned char* base, int count) {
+// Identity work order, zero factorisation status, zero counters: what the kernel expects to find. Every
+// caller status starts as "timed out": the kernel overwrites it for each submatrix it takes, so one that
+// no block reached (all of them gave up on a wait) cannot keep a stale OK from an earlier call.
+__global__ void k_noalloc_reset(unsigned char* base, int count, int32_t* status) {
   int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
   int32_t* order = ints;
   int32_t* prep = ints + kNaMaxSub;
@@ -989,11 +1004,13 @@ __global__ void k_noalloc_reset(unsigned char* base, int count) {
     order[i] = i;
     prep[i] = kSubOk;
     rst[i] = 0;
+    status[i] = kSubTimeout;
   }
   if (blockIdx.x == 0 && threadIdx.x < 64) ctr[threadIdx.x] = 0;
 }
 
-void* g_na_addr[64] = {};
+// device address of the static array per device ordinal, looked up by the first call on that device
+std::atomic<void*> g_na_addr[64];
 
 }  // namespace
 
@@ -1044,12 +1061,12 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
     set_error("nolsm_sign_noalloc: device ordinal %d out of range", dev);
     return NOLSM_ERR_UNSUPPORTED;
   }
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    NOLSM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_na_addr[dev] = p;
+  void* addr = g_na_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {   // threads that race here look up the same address
+    NOLSM_CUDA_TRY(cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+    g_na_addr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_na_addr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(addr);
   int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
 
   CUtensorMap mA, mB, mS;
@@ -1059,7 +1076,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
     set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
     return NOLSM_ERR_CUDA;
   }
-  k_noalloc_reset<<<(count + 255) / 256, 256, 0, st>>>(base, count);
+  k_noalloc_reset<<<(count + 255) / 256, 256, 0, st>>>(base, count, status);
   NOLSM_LAUNCH_CHECK();
   TcArgs g;
   g.j0 = 0; g.j1 = count;

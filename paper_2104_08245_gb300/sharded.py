@@ -1,16 +1,19 @@
 """Chemical-potential bisection over submatrices sharded across processes.
 
 Submatrices are independent (each molecule's columns are owned by one rank and written back locally),
-so ranks split the molecules into contiguous ranges and exchange only one number per bisection point:
-the FP64 sum of their partial electron counts. The bisection rule is the one of nolsm_find_mu
-(Sec. "Simulation Details": mu by bisection for charge neutrality): mu = (lo + hi)/2, f < 0 raises lo,
-otherwise hi is lowered, stop at |f| <= tol_n * N_occ, on the bracket width tol_mu, or after
-max_bisect points. The bracket is the union of the ranks' spectral brackets.
+so ranks split the molecules into contiguous ranges and exchange only numbers: the union of their
+spectral brackets once, then per bisection point the FP64 sum of their partial electron counts. Every
+decision of the bisection (Sec. "Simulation Details": mu by bisection for charge neutrality) is taken
+by the library's nolsm_bisection_start / nolsm_bisection_update, the same calls nolsm_find_mu makes, so
+the ranks visit the points a single process would. This module only all-reduces.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 from typing import Callable, Optional, Tuple
+
+from . import _abi
 
 
 @dataclasses.dataclass
@@ -23,40 +26,37 @@ class ShardedMu:
 
 
 def bisect_allreduce(count_local: Callable[[float], float], bracket_local: Tuple[float, float], n_occ: float,
-                     tol_n: float, tol_mu: float, max_steps: int, group=None,
-                     side_local: Optional[Callable[[bool], None]] = None) -> ShardedMu:
+                     opts, group=None, side_local: Optional[Callable[[bool], None]] = None) -> ShardedMu:
     """The bisection with the partial counts summed over the process group (FP64 all-reduce);
-    side_local(raises_lo) is told which end of the bracket each point becomes."""
+    side_local(raises_lo) is told which end of the bracket each point becomes. opts: nolsm_options
+    (tol_n, tol_mu, max_bisect)."""
     import torch
     import torch.distributed as dist
 
+    lib = _abi.load(build_if_missing=True)
     dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else \
         torch.device("cpu")
     b = torch.tensor([-bracket_local[0], bracket_local[1]], dtype=torch.float64, device=dev)
     dist.all_reduce(b, op=dist.ReduceOp.MAX, group=group)
-    lo, hi = -float(b[0]), float(b[1])
+    st = _abi.NolsmBisection()
+    rc = lib.nolsm_bisection_start(ctypes.byref(st), float(n_occ), -float(b[0]), float(b[1]))
+    if rc != 0:
+        raise RuntimeError(f"nolsm_bisection_start: {lib.nolsm_last_error().decode()}")
     hist = []
-    mu, t = 0.5 * (lo + hi), float("nan")
-    status = 7
-    for step in range(1, max_steps + 1):
-        mu = 0.5 * (lo + hi)
+    mu = st.mu
+    while st.state == _abi.BISECT_EVALUATE:
+        mu = st.mu
         c = torch.tensor([count_local(mu)], dtype=torch.float64, device=dev)
         dist.all_reduce(c, op=dist.ReduceOp.SUM, group=group)
-        t = float(c.item())
         hist.append(mu)
-        f = t - n_occ
-        if abs(f) <= tol_n * abs(n_occ):
-            status = 0
-            break
-        if side_local is not None:
-            side_local(f < 0.0)
-        if f < 0.0:
-            lo = mu
-        else:
-            hi = mu
-        if hi - lo <= tol_mu:
-            break
-    return ShardedMu(status, mu, t, len(hist), hist)
+        raises = ctypes.c_int32(0)
+        rc = lib.nolsm_bisection_update(ctypes.byref(st), float(c.item()), ctypes.byref(opts), ctypes.byref(raises))
+        if rc != 0:
+            raise RuntimeError(f"nolsm_bisection_update: {lib.nolsm_last_error().decode()}")
+        if st.state != _abi.BISECT_ACCEPTED and side_local is not None:
+            side_local(bool(raises.value))
+    status = 0 if st.state == _abi.BISECT_ACCEPTED else _abi.ERR_NO_PLATEAU
+    return ShardedMu(status, mu, st.trace_DS, st.steps, hist)
 
 
 def sharded_find_mu(plan, n_occ: float, opts, group=None) -> ShardedMu:
@@ -73,5 +73,4 @@ def sharded_find_mu(plan, n_occ: float, opts, group=None) -> ShardedMu:
     def side(raises_lo):
         nl.nolsm_bisect_side(plan, opts, raises_lo)
 
-    return bisect_allreduce(count, (lo, hi), n_occ, opts.tol_n, opts.tol_mu,
-                            opts.max_bisect if opts.max_bisect > 0 else 100, group, side)
+    return bisect_allreduce(count, (lo, hi), n_occ, opts, group, side)

@@ -48,8 +48,10 @@ def _rank(rank, world, port, out):
     plan = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
     n = sysm.n_mol
     subs = list(range(n * rank // world, n * (rank + 1) // world))
+    import paper_2104_08245_gb300 as nl
     r = bisect_allreduce(lambda mu: orc.solve(sysm, mu, subs=subs, plan=plan).trace_DS,
-                         _bracket(sysm, plan, subs), sysm.n_occ, 1e-5, 1e-10, 100)
+                         _bracket(sysm, plan, subs), sysm.n_occ, nl.options("fp64", tol_n=1e-5, tol_mu=1e-10,
+                                                                            max_bisect=100))
     out[rank] = (r.status, r.mu, r.trace_DS, r.history)
     dist.destroy_process_group()
 
@@ -89,7 +91,8 @@ def _rank_that_leaves(rank, world, port, out):
         return 0.0               # every rank below n_occ: the bisection keeps going
 
     try:
-        bisect_allreduce(count, (-1.0, 1.0), 10.0, 1e-5, 1e-10, 50)
+        import paper_2104_08245_gb300 as nl
+        bisect_allreduce(count, (-1.0, 1.0), 10.0, nl.options("fp64", tol_n=1e-5, tol_mu=1e-10, max_bisect=50))
         out[rank] = "finished"
     except RuntimeError as e:    # the peer's exit (or the group's timeout) surfaces as an error, not a hang
         out[rank] = "detected: " + str(e).splitlines()[0][:80]

@@ -4,8 +4,9 @@ nolsm_sign_noalloc serves callers that cannot allocate device memory when they n
 runs the tensor-core sign iteration on caller-held inputs with the library's static scratch array.
 Here it gets the 64 submatrices of the small water-like system (A_i, centre columns, spectral bounds
 prepared on the CPU) and must reproduce, within the BF16X3 tolerance of the other tests, the centre
-columns of D and the partial traces that nolsm_solve_batch + nolsm_scatter_density give, on two
-calls in a row at different chemical potentials (the second call reuses the shared scratch)."""
+columns of D and the partial traces that nolsm_solve_batch + nolsm_scatter_density give, and those of
+the FP64 oracle, on two calls in a row at different chemical potentials (the second call reuses the
+shared scratch)."""
 import ctypes
 
 import numpy as np
@@ -88,8 +89,15 @@ def test_noalloc_matches_solve_batch_on_two_calls():
                 q = po.nb_ptr[I] + int(np.nonzero(po.nb_idx[po.nb_ptr[I]:po.nb_ptr[I + 1]] == J)[0][0])
                 blk = D[off[q]:off[q + 1]].reshape(int(po.nbf[I]), b)
                 err = max(err, float(np.max(np.abs(blk - cols[po.nb_off[p]:po.nb_off[p] + blk.shape[0], :]))))
-        print(f"mu={mu}: no-alloc vs solve_batch max|dD| = {err:.3e}")
+        # the FP64 oracle's centre columns and partial traces at the same mu
+        oref = orc.solve(sysm, mu, plan=po)
+        err_o = max(float(np.max(np.abs(Dc_h[c_off[J]:c_off[J + 1]].reshape(-1, int(po.nbf[J])) -
+                                        oref.subs[J].D_cols))) for J in range(n_mol))
+        tS_o = np.array([oref.subs[J].t_S for J in range(n_mol)])
+        print(f"mu={mu}: no-alloc vs solve_batch max|dD| = {err:.3e}, vs the FP64 oracle {err_o:.3e}")
         assert err <= TOL_D
+        assert err_o <= TOL_D
+        np.testing.assert_allclose(tS.cpu().numpy(), tS_o, rtol=TOL_TR, atol=TOL_TR)
         np.testing.assert_allclose(tS.cpu().numpy(), ref.sub_t_S.cpu().numpy(), rtol=TOL_TR, atol=TOL_TR)
         np.testing.assert_allclose(tH.cpu().numpy(), ref.sub_t_H.cpu().numpy(), rtol=TOL_TR, atol=TOL_TR)
 
