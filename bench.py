@@ -366,6 +366,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--workload", default="streamed_bf16", choices=list(WORKLOADS))
+    ap.add_argument("--inverse", default="cholesky", choices=["cholesky", "ns"],
+                    help="preparation of A_J: FP32 Cholesky, or the tensor-core Newton-Schulz inverse square root")
     ap.add_argument("--batches", type=int, default=8, help="molecule batches the errors are reported for")
     ap.add_argument("--sample", type=int, default=640, help="oracle submatrices (errors and CPU baseline)")
     ap.add_argument("--ref-sample", type=int, default=96, help="submatrices per reference-arm step")
@@ -406,7 +408,8 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     peaks = measured_peaks()
-    opts = nl.options(args.precision)
+    inverse = nl._abi.INVERSE_NEWTON_SCHULZ if args.inverse == "ns" else nl._abi.INVERSE_CHOLESKY
+    opts = nl.options(args.precision, inverse=inverse)
 
     # host copies (pinned) for the e2e leg; device copies for the resident leg
     host = {"nbf": torch.from_numpy(sysm.nbf).pin_memory(),

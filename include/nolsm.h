@@ -124,7 +124,19 @@ typedef struct {
                             the spectrum of A_J and symmetric iterates, and finish with T_J(D) =
                             L^-T 1/2 (I - sign(M - mu I)) L^-1 (Eq. purification_submatrix); always used by
                             NOLSM_FP8E4M3 (every operand is then loaded in the K-major layout) */
+  int32_t inverse;       /* tensor-core modes, standard form: how A_J = T_J(S)^-1 T_J(H0) is prepared.
+                            NOLSM_INVERSE_CHOLESKY: FP32 Cholesky factor and FP32 solves.
+                            NOLSM_INVERSE_NEWTON_SCHULZ: the coupled Newton-Schulz iteration for the inverse
+                            square root of Sec. "Efficient Iterative Matrix Function Solvers on GPU Tensor
+                            Cores" (Eqs. inv1-inv3) on the tensor cores (three-term FP16 split products),
+                            T_J(S)^-1 = Z^2 / c and A_J = T_J(S)^-1 T_J(H0) as two more products; the step whose
+                            ||I - Z_k Y_k||_F / sqrt(n) <= 1e-3 is the last. Either way the centre columns of
+                            T_J(S)^-1 are refined to about 1e-12 with a double-FP32 residual, and a submatrix
+                            that fails is prepared again with the FP64 factorisation. Ignored by NOLSM_FP64 and
+                            the symmetric form (which keep the Cholesky factor). */
 } nolsm_options;
+
+enum { NOLSM_INVERSE_CHOLESKY = 0, NOLSM_INVERSE_NEWTON_SCHULZ = 1 };
 
 /* Defaults for a precision: FP64 tol_ns 1e-9, tol_accept 1e-7, max_iter 100; low-precision modes
  * tol_ns 1e-2, refine_steps 2 (FP8: 3), tol_accept 1e-4; tol_n 1e-5 (relative), tol_mu 1e-10,
@@ -165,6 +177,16 @@ nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info);
  * block row I = nb_idx[nb_ptr[I] .. nb_ptr[I+1]). */
 nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_t* nb_idx, int32_t* nb_off,
                                  int32_t* sub_n, int32_t* sub_c0, int64_t* d_blk_off, nolsm_stream_t stream);
+
+/* The geometry caches of a1-a3 for the options' range and preparation (precision, symmetric_form,
+ * inverse), prepared first if needed, copied to caller device buffers (either may be NULL): A (float32,
+ * or float64 for NOLSM_FP64; A_J = T_J(S)^-1 T_J(H0) row-major n_J x n_J at element offset a_off[J], the
+ * symmetric form's M_J = L^-1 T_J(H0) L^-T instead) and Q (float64, the centre columns of T_J(S)^-1, n_J x
+ * b_J row-major at c_off[J]), where a_off and c_off are the exclusive prefix sums of n_J^2 and n_J b_J over
+ * J = 0 .. n_mol-1 (only the range's entries are written). prep_status (device int32 [n_mol], may be NULL):
+ * NOLSM_OK or NOLSM_ERR_NOT_SPD per submatrix. Synchronises the stream. */
+nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
+                                     double* Q, int32_t* prep_status);
 
 /* a1-a7: every submatrix J in [sub_begin, sub_end) at chemical potential mu:
  *   T_J(S), T_J(H0) gathered (a1); T_J(S) = L L^T in FP64 (a2); A_J = T_J(S)^-1 T_J(H0) (a3);
@@ -312,6 +334,9 @@ typedef struct {
   double flops_fp32;           /* FP32 flops of the low-precision paths' factorisation and solves */
   int64_t factor_launches;     /* preparation chunks (one factorisation kernel launch each) */
   double ms_energy_weighted;   /* the centre columns of T_J(W) (nolsm_energy_weighted), kernel alone */
+  double ms_prep_tensor;       /* the tensor-core inverse-square-root kernel alone (part of ms_factor) */
+  double flops_prep_tensor;    /* its products, 2 n^3 each on the unpadded n (the paper's count) */
+  double flops_prep_tensor_issued; /* the same x3 (three-term split products) */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);

@@ -18,7 +18,7 @@ from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
            "nolsm_energy_weighted", "nolsm_combine_submatrices",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
-           "nolsm_spectral_bracket", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
+           "nolsm_spectral_bracket", "nolsm_plan_get_prepared", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
            "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
            "options", "NolsmError", "Plan", "SolveResult", "MuResult"]
 
@@ -123,6 +123,24 @@ def nolsm_plan_get_maps(plan: "Plan", stream=None) -> dict:
     if rc != 0:
         raise NolsmError(rc, "nolsm_plan_get_maps")
     return out
+
+
+def nolsm_plan_get_prepared(plan: "Plan", opts: NolsmOptions, stream=None):
+    """(A, Q, prep_status) device tensors of the options' preparation: A_J (float32, float64 for FP64) packed
+    at the exclusive prefix sums of n_J^2, Q (float64, centre columns of T_J(S)^-1) at those of n_J b_J."""
+    torch = _torch()
+    maps = nolsm_plan_get_maps(plan, stream)
+    n = maps["sub_n"].to(torch.int64)
+    b = plan.dsys.nbf.to(torch.int64)
+    dev = plan.dsys.nbf.device
+    A = torch.zeros(int((n * n).sum()), dtype=torch.float64 if opts.precision == FP64 else torch.float32, device=dev)
+    Q = torch.zeros(int((n * b).sum()), dtype=torch.float64, device=dev)
+    ps = torch.zeros(plan.dsys.n_mol, dtype=torch.int32, device=dev)
+    rc = _abi.load().nolsm_plan_get_prepared(plan.handle, ctypes.byref(opts), _stream(stream), A.data_ptr(),
+                                             Q.data_ptr(), ps.data_ptr())
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_get_prepared")
+    return A, Q, ps
 
 
 def nolsm_spectral_bracket(plan: "Plan", opts: NolsmOptions, stream=None):

@@ -16,6 +16,8 @@ FP64, FP32, BF16, BF16X3, FP8E4M3, FP16 = range(6)
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "bf16x3": BF16X3, "fp8e4m3": FP8E4M3, "fp16": FP16}
 # nolsm_bound_source
 BOUND_GERSHGORIN, BOUND_POWER, BOUND_MLP = range(3)
+# nolsm_options.inverse
+INVERSE_CHOLESKY, INVERSE_NEWTON_SCHULZ = range(2)
 
 
 class NolsmSystem(ctypes.Structure):
@@ -28,7 +30,7 @@ class NolsmOptions(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_steps", c_int32), ("max_iter", c_int32),
                 ("tol_ns", c_double), ("tol_accept", c_double), ("tol_n", c_double), ("tol_mu", c_double),
                 ("max_bisect", c_int32), ("bound_source", c_int32), ("sub_begin", c_int64), ("sub_end", c_int64),
-                ("symmetric_form", c_int32)]
+                ("symmetric_form", c_int32), ("inverse", c_int32)]
 
 
 class NolsmBisection(ctypes.Structure):
@@ -51,7 +53,8 @@ class NolsmStats(ctypes.Structure):
                 ("flops_paper", c_double), ("flops_tensor", c_double), ("flops_tensor_padded", c_double),
                 ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64), ("ms_gather", c_double),
                 ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64),
-                ("ms_energy_weighted", c_double)]
+                ("ms_energy_weighted", c_double), ("ms_prep_tensor", c_double), ("flops_prep_tensor", c_double),
+                ("flops_prep_tensor_issued", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,6 +77,8 @@ SIGNATURES = [
     ("nolsm_find_mu", c_int32, [c_void_p, c_double, c_double, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
                                 ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int32),
                                 ctypes.POINTER(c_double)]),
+    ("nolsm_plan_get_prepared", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p, c_void_p,
+                                          c_void_p]),
     ("nolsm_spectral_bracket", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p,
                                          ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     ("nolsm_bisect_begin", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_int32]),

@@ -7,6 +7,7 @@
 
 #include "nolsm_internal.cuh"
 #include "prep.cuh"
+#include "tc_path.cuh"
 
 namespace nolsm {
 
@@ -366,6 +367,13 @@ static nolsm_status ensure(nolsm_plan* plan, DevBuf& b, size_t bytes) {
   return dev_alloc(plan, b, bytes);
 }
 
+// Stopping rule of the tensor-core inverse square root: the step whose ||I - Z_k Y_k||_F / sqrt(n) is below
+// kNsInvTol is the last (the iteration converges quadratically, so its Z is about kNsInvTol^2 from the
+// limit, below the three-term products' own rounding); a submatrix still above it after kNsInvMaxSteps
+// steps is prepared with the FP64 factorisation.
+constexpr float kNsInvTol = 1e-3f;
+constexpr int kNsInvMaxSteps = 40;
+
 nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStream_t st) {
   const bool keep_fp64_A = cls == kPrepFP64;
   const bool sym = cls == kPrepSym;
@@ -438,6 +446,43 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     if (keep_fp64_A) {
       NOLSM_TRY(launch_prepare(pa, (int)(e - J), chunk_max_n, true, P.A.p, st));
       plan->stats.launches += 2;
+    } else if (cls == kPrepNS) {
+      // the coupled Newton-Schulz inverse square root on the tensor cores (A_J and X = T_J(S)^-1 in FP32),
+      // then the refinement of the centre columns of T_J(S)^-1 with X, then the FP64 preparation of what
+      // either of them flagged
+      const int64_t nbc = plan->h_c_off[e] - plan->h_c_off[J];
+      NOLSM_TRY(ensure(plan, plan->ws_refine, (sizeof(double) + sizeof(float)) * (size_t)std::max<int64_t>(nbc, 1)));
+      NOLSM_TRY(ensure(plan, plan->ws_l32, sizeof(float) * (size_t)n2));
+      std::vector<int32_t> ord((size_t)(e - J));
+      for (int64_t k = J; k < e; ++k) ord[(size_t)(k - J)] = (int32_t)k;
+      std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return plan->h_sub_n[a] > plan->h_sub_n[b]; });
+      NOLSM_TRY(ensure(plan, plan->prep_order, sizeof(int32_t) * ord.size()));
+      NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->prep_order.p, ord.data(), sizeof(int32_t) * ord.size(),
+                                     cudaMemcpyHostToDevice, st));
+      NOLSM_CUDA_TRY(cudaStreamSynchronize(st));   // ord is a host temporary
+      NsInvArgs ia;
+      ia.order = plan->prep_order.as<int32_t>();
+      ia.count = (int32_t)(e - J);
+      ia.max_n = chunk_max_n;
+      ia.ws = g.ws;
+      ia.a_base = g.a_base;
+      ia.chunk_n2 = n2;
+      ia.Aout = P.A.as<float>();
+      ia.Xout = plan->ws_l32.as<float>();
+      ia.prep_out = plan->prep_status.as<int32_t>();
+      ia.tol_inv = kNsInvTol;
+      ia.max_inv = kNsInvMaxSteps;
+      tmark(plan, st);
+      NOLSM_TRY(launch_ns_inverse(plan, ia, st));
+      tmark(plan, st);
+      pa.order = ia.order;
+      pa.L32 = plan->ws_l32.as<float>();
+      pa.c_base = plan->h_c_off[J];
+      pa.Qp = plan->ws_refine.as<float2>();
+      pa.W32 = reinterpret_cast<float*>(pa.Qp + std::max<int64_t>(nbc, 1));
+      pa.fallback_max_n = prepare_fp64_max_n();
+      NOLSM_TRY(launch_ns_qrefine(pa, (int)(e - J), chunk_max_n, plan->max_b, P.A.as<float>(), st));
+      plan->stats.launches += 2;
     } else {
       // FP32 factor, A in FP32, Q refined to FP64 accuracy; the FP64 factorisation only where flagged
       const int64_t nbc = plan->h_c_off[e] - plan->h_c_off[J];
@@ -481,6 +526,9 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       const double fma_fact = m * m * m / 3.0 + m * m * m;
       if (keep_fp64_A) {
         plan->stats.flops_fp64 += 2.0 * (fma_fact + m * m * b);
+      } else if (cls == kPrepNS) {
+        // the tensor products are counted by launch_ns_inverse; here the refinement's FP32 X r products
+        plan->stats.flops_fp32 += 2.0 * 2.0 * m * m * b;
       } else {
         plan->stats.flops_fp32 += 2.0 * (fma_fact + (sym ? 3.5 : 3.0) * m * m * b);
       }

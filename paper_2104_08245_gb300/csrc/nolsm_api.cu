@@ -95,7 +95,26 @@ void pmark(nolsm_plan* plan, cudaStream_t st) {
   cudaEventRecord(plan->pev[plan->pev_used++], st);
 }
 
+void tmark(nolsm_plan* plan, cudaStream_t st) {
+  if (!plan->ev_ok) return;
+  if (plan->tev_used == plan->tev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    plan->tev.push_back(e);
+  }
+  cudaEventRecord(plan->tev[plan->tev_used++], st);
+}
+
 void prep_times(nolsm_plan* plan) {
+  for (size_t k = 0; k + 1 < plan->tev_used; k += 2) {
+    float a = 0.0f;
+    if (cudaEventElapsedTime(&a, plan->tev[k], plan->tev[k + 1]) == cudaSuccess) plan->stats.ms_prep_tensor += a;
+    else cudaGetLastError();
+  }
+  plan->tev_used = 0;
   for (size_t k = 0; k + 2 < plan->pev_used; k += 3) {
     float a = 0.0f, b = 0.0f;
     if (cudaEventElapsedTime(&a, plan->pev[k], plan->pev[k + 1]) == cudaSuccess &&
@@ -125,7 +144,7 @@ using namespace nolsm;
 
 nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
-                   &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &Lsym, &Wc, &Dc,
+                   &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &prep_ns.A, &Lsym, &Wc, &Dc,
                    &t_S, &t_H, &iters, &status, &rsteps, &nbelow, &nb_lo, &nb_hi, &active, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
                    &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym, &Wd, &tW};
   for (DevBuf* b : all) dev_free(this, *b);
@@ -133,6 +152,7 @@ nolsm_plan::~nolsm_plan() {
   if (ev_ok)
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
   for (cudaEvent_t e : pev) cudaEventDestroy(e);
+  for (cudaEvent_t e : tev) cudaEventDestroy(e);
 }
 
 extern "C" {
@@ -234,7 +254,8 @@ static nolsm_status check_options(const nolsm_plan* plan, const nolsm_options* o
   if (!o) { set_error("options are NULL"); return NOLSM_ERR_ARG; }
   if (o->precision < NOLSM_FP64 || o->precision > NOLSM_FP16 || o->max_iter < 1 || o->max_iter > 10000 ||
       o->refine_steps < 0 || o->refine_steps > 100 || !(o->tol_ns > 0) || !(o->tol_accept > 0) ||
-      o->bound_source < 0 || o->bound_source > NOLSM_BOUND_MLP) {
+      o->bound_source < 0 || o->bound_source > NOLSM_BOUND_MLP || o->inverse < NOLSM_INVERSE_CHOLESKY ||
+      o->inverse > NOLSM_INVERSE_NEWTON_SCHULZ) {
     set_error("invalid options (precision %d, max_iter %d, refine %d, tol_ns %g, tol_accept %g, bound %d)",
               o->precision, o->max_iter, o->refine_steps, o->tol_ns, o->tol_accept, o->bound_source);
     return NOLSM_ERR_ARG;
@@ -385,6 +406,32 @@ nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_strea
   mark(plan, 5, (cudaStream_t)stream);
   NOLSM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   plan->stats.ms_scatter += elapsed(plan, 4, 5);
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
+                                     double* Q, int32_t* prep_status) {
+  if (!plan) { set_error("nolsm_plan_get_prepared: NULL plan"); return NOLSM_ERR_ARG; }
+  int64_t j0, j1;
+  NOLSM_TRY(check_options(plan, opts, &j0, &j1));
+  cudaStream_t st = (cudaStream_t)stream;
+  NOLSM_TRY(ensure_results(plan));
+  const int cls = prep_class(*opts);
+  NOLSM_TRY(prepare(plan, j0, j1, cls, st));
+  prep_times(plan);
+  const Prepared& P = prepared(plan, cls);
+  const size_t esz = P.fp64 ? sizeof(double) : sizeof(float);
+  const int64_t a0 = plan->h_a_off[j0], a1 = plan->h_a_off[j1], c0 = plan->h_c_off[j0], c1 = plan->h_c_off[j1];
+  if (A)
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(A) + esz * a0, static_cast<const char*>(P.A.p) + esz * a0,
+                                   esz * (size_t)(a1 - a0), cudaMemcpyDeviceToDevice, st));
+  if (Q)
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(Q + c0, plan->Q.as<double>() + c0, sizeof(double) * (size_t)(c1 - c0),
+                                   cudaMemcpyDeviceToDevice, st));
+  if (prep_status)
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(prep_status + j0, plan->prep_status.as<int32_t>() + j0,
+                                   sizeof(int32_t) * (size_t)(j1 - j0), cudaMemcpyDeviceToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   return NOLSM_OK;
 }
 

@@ -76,7 +76,7 @@ struct nolsm_plan {
   nolsm::DevBuf Sc, Hc;   // centre columns of T_J(S), T_J(H0) (FP64)
   nolsm::DevBuf lam;      // float64 [2*n_mol]: Gershgorin interval of A_J
   nolsm::DevBuf prep_status;  // int32 [n_mol]: kSubOk or kSubNotSpd from the factorisation
-  nolsm::Prepared prep64, prep32, prep_sym;
+  nolsm::Prepared prep64, prep32, prep_sym, prep_ns;
   nolsm::DevBuf Lsym;               // float32, FP32 factors of every submatrix at a_off (symmetric form)
   nolsm::DevBuf Wc;                 // float64, W_c = L^-1 E_c at c_off (symmetric form)
 
@@ -128,6 +128,8 @@ struct nolsm_plan {
   bool ev_ok = false;
   std::vector<cudaEvent_t> pev;     // preparation chunks: before gather, after gather, after factorisation
   size_t pev_used = 0;
+  std::vector<cudaEvent_t> tev;     // preparation chunks: around the tensor-core inverse kernel
+  size_t tev_used = 0;
 
   ~nolsm_plan();
 };
@@ -143,10 +145,12 @@ nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st);
 // per-geometry preparation and per-mu solve of the FP64 path (fp64_path.cu)
 // Preparation classes: FP64 A (plain FP64 path), FP32 A = T_J(S)^-1 T_J(H0) (tensor-core paths), FP32
 // symmetric form M = L^-1 T_J(H0) L^-T (E4M3, or any tensor-core mode on request).
-enum : int { kPrepFP64 = 0, kPrepMixed = 1, kPrepSym = 2 };
+// A fourth class holds FP32 A prepared by the tensor-core inverse square root (Eqs. inv1-inv3).
+enum : int { kPrepFP64 = 0, kPrepMixed = 1, kPrepSym = 2, kPrepNS = 3 };
 inline int prep_class(const nolsm_options& o) {
   if (o.precision == NOLSM_FP64) return kPrepFP64;
-  return (o.precision == NOLSM_FP8E4M3 || o.symmetric_form) ? kPrepSym : kPrepMixed;
+  if (o.precision == NOLSM_FP8E4M3 || o.symmetric_form) return kPrepSym;
+  return o.inverse == NOLSM_INVERSE_NEWTON_SCHULZ ? kPrepNS : kPrepMixed;
 }
 inline Prepared& prepared(nolsm_plan* plan, int cls);
 nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStream_t st);
@@ -180,6 +184,8 @@ double elapsed(nolsm_plan* plan, int i, int j);
 // The same for the preparation's per-chunk events: pmark records the next one; after a synchronisation
 // prep_times adds the gather and factorisation times to the stats and starts over.
 void pmark(nolsm_plan* plan, cudaStream_t st);
+// the same pairs around the tensor-core inverse kernel (prep_times adds them to ms_prep_tensor)
+void tmark(nolsm_plan* plan, cudaStream_t st);
 void prep_times(nolsm_plan* plan);
 
 // shared epilogue: sum the per-submatrix traces of [j0, j1) (fp64_path.cu)
@@ -195,5 +201,8 @@ nolsm_status energy_weighted(nolsm_plan* plan, cudaStream_t st, double* W_vals, 
 }  // namespace nolsm
 
 inline nolsm::Prepared& nolsm::prepared(nolsm_plan* plan, int cls) {
-  return cls == kPrepFP64 ? plan->prep64 : (cls == kPrepSym ? plan->prep_sym : plan->prep32);
+  return cls == kPrepFP64 ? plan->prep64
+         : cls == kPrepSym ? plan->prep_sym
+         : cls == kPrepNS  ? plan->prep_ns
+                           : plan->prep32;
 }

@@ -4,6 +4,9 @@
 
 namespace nolsm {
 
+// internal preparation status: the submatrix is prepared again with the FP64 factorisation
+constexpr int32_t kSubRefine = 64;
+
 struct PrepArgs {
   int32_t j0;                 // first submatrix of the chunk (one CTA per submatrix)
   const int32_t* order = nullptr;   // mixed preparation: CTA -> submatrix, largest first (null: j0 + CTA)
@@ -44,6 +47,9 @@ nolsm_status launch_prepare(const PrepArgs& g, int count, int max_n, bool fp64_A
 // The same with the FP32 factor and iterative refinement of Q (A in FP32), followed by the FP64
 // preparation of the submatrices it flagged.
 nolsm_status launch_prepare_mixed(const PrepArgs& g, int count, int max_n, float* Acache, cudaStream_t st);
+// After the tensor-core inverse (launch_ns_inverse): the centre columns of T_J(S)^-1 refined with X =
+// T_J(S)^-1 in g.L32, the Gershgorin interval of A_J, then the FP64 preparation of the flagged submatrices.
+nolsm_status launch_ns_qrefine(const PrepArgs& g, int count, int max_n, int max_b, float* Acache, cudaStream_t st);
 // Largest submatrix dimension the FP64 preparation takes.
 int prepare_fp64_max_n();
 nolsm_status launch_sym_finish(const SymArgs& g, int count, int max_n, int max_b, cudaStream_t st);

@@ -964,7 +964,6 @@ __device__ void gershgorin(const TA* __restrict__ A, int n, double* lam, float* 
   }
 }
 
-constexpr int kSubRefine = 64;   // internal prep status: prepare again with the FP64 factor
 
 // ------------------------------------------------------------------------------------ kernels
 template <typename TA>
@@ -1093,6 +1092,76 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   if (tid == 0) g.prep_status[J] = ok ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
 }
 
+// After the tensor-core inverse square root (Eqs. inv1-inv3), which leaves X = T_J(S)^-1 in FP32 (in g.L32,
+// accurate to about 1e-6 of its norm) and A_J in Acache: the centre columns of T_J(S)^-1 by iterative
+// refinement with X as the approximate inverse, q <- q + X (E_c - T_J(S) q) from q = X[:, centre], the
+// residual in double-FP32 arithmetic (as in k_prepare_mixed), until the correction is below 1e-6 of q; then
+// the Gershgorin interval of A_J. A submatrix the inverse kernel flagged, or whose refinement does not
+// contract, is left flagged for the FP64 preparation.
+__global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float* __restrict__ Acache) {
+  extern __shared__ __align__(16) float Wsh[];   // the residual, n x b
+  __shared__ float rlo[kThreads], rhi[kThreads];
+  __shared__ float red_d[kThreads / 32];
+  __shared__ double red_q[kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int J = g.order ? g.order[blockIdx.x] : g.j0 + (int)blockIdx.x;
+  if (g.prep_status[J] != kSubOk) return;
+  const int n = g.sub_n[J], bJ = g.nbf[J], c0 = g.sub_c0[J], nbc = n * bJ;
+  const double* S = g.ws + (g.a_off[J] - g.a_base);
+  const float* X = g.L32 + (g.a_off[J] - g.a_base);
+  float* w = g.W32 + (g.c_off[J] - g.c_base);
+  float2* qp = g.Qp + (g.c_off[J] - g.c_base);
+  double* q = g.Q + g.c_off[J];
+  for (int e = tid; e < nbc; e += kThreads) {
+    const int i = e / bJ, c = e - i * bJ;
+    q[e] = (double)X[(size_t)i * n + c0 + c];
+  }
+  __syncthreads();
+  bool conv = false;
+  for (int it = 0; it < kRefineMax && !conv; ++it) {
+    for (int e = tid; e < nbc; e += kThreads) qp[e] = split_f64(q[e]);
+    __syncthreads();
+    residual_df(S, n, c0, bJ, qp, w);
+    __syncthreads();
+    for (int e = tid; e < nbc; e += kThreads) Wsh[e] = w[e];
+    __syncthreads();
+    float dmax = 0.0f;
+    double qmax = 0.0;
+    bool finite = true;
+    for (int e = tid; e < nbc; e += kThreads) {
+      const int i = e / bJ, c = e - i * bJ;
+      const float* xi = X + (size_t)i * n;
+      float d = 0.0f;
+      for (int k = 0; k < n; ++k) d = fmaf(xi[k], Wsh[k * bJ + c], d);
+      const double qe = q[e] + (double)d;
+      q[e] = qe;
+      finite = finite && isfinite(d) && isfinite(qe);
+      dmax = fmaxf(dmax, fabsf(d));
+      qmax = fmax(qmax, fabs(qe));
+    }
+    if (!finite) dmax = INFINITY;
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+    }
+    if (lane == 0) {
+      red_d[warp] = dmax;
+      red_q[warp] = qmax;
+    }
+    __syncthreads();
+    float dm = 0.0f;
+    double qm = 0.0;
+    for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+      dm = fmaxf(dm, red_d[w2]);
+      qm = fmax(qm, red_q[w2]);
+    }
+    conv = (double)dm <= kRefineTol * qm;   // the same shared values in every thread
+    __syncthreads();
+  }
+  if (conv) gershgorin(Acache + g.a_off[J], n, g.lam + 2 * J, rlo, rhi);
+  if (tid == 0) g.prep_status[J] = conv ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
+}
+
 // The symmetric form's last step, after the sign kernel: its centre-column phase leaves
 // U = 1/2 (I - X~) W_c in Dc (W_c = L^-1 E_c, X~ = sign of M - mu I); here D_c = L^-T U with the FP32 factor
 // (Eq. purification_submatrix: T_J(D) = L^-T 1/2 (I - X~) L^-1), and the partial traces in FP64.
@@ -1174,6 +1243,21 @@ nolsm_status launch_sym_finish(const SymArgs& g, int count, int max_n, int max_b
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_sym_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_sym_finish<<<count, kThreads, smem, st>>>(g);
   NOLSM_LAUNCH_CHECK();
+  return NOLSM_OK;
+}
+
+nolsm_status launch_ns_qrefine(const PrepArgs& g, int count, int max_n, int max_b, float* Acache, cudaStream_t st) {
+  const size_t smem = sizeof(float) * (size_t)max_n * max_b;
+  if (smem > kSmemLimit) {
+    set_error("submatrix dimension %d x %d centre columns exceed the refinement's shared memory", max_n, max_b);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_qrefine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_ns_qrefine<<<count, kThreads, smem, st>>>(g, Acache);
+  NOLSM_LAUNCH_CHECK();
+  PrepArgs f = g;
+  f.only_flagged = 1;
+  NOLSM_TRY(launch_prepare(f, count, std::min(max_n, prepare_fp64_max_n()), false, Acache, st));
   return NOLSM_OK;
 }
 

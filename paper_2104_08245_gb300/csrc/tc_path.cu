@@ -21,6 +21,16 @@
 // double-buffered TMEM accumulators (2 x 256 columns), decide convergence and start and finish the
 // slots' submatrices. All waits are bounded by the global timer; a wait that runs out marks the
 // submatrices in flight as timed out.
+//
+// The same kernel, instantiated in its second mode, prepares A_J = T_J(S)^-1 T_J(H0) on the tensor cores
+// by the coupled Newton-Schulz iteration for the inverse square root (Eqs. inv1-inv3): with Y_0 = T_J(S)/c
+// and Z_0 = I, V_k = Z_k Y_k, Y_{k+1} = 1/2 Y_k (3I - V_k), Z_{k+1} = 1/2 (3I - V_k) Z_k, Z_k tends to
+// (T_J(S)/c)^-1/2, so T_J(S)^-1 = Z^2 / c (Eq. inv3) and A_J = (Z^2 / c) T_J(H0). Every product is a
+// three-term FP16 split. The step whose V_k has ||I - V_k||_F / sqrt(n) <= tol_inv is the last (its Y
+// update is skipped, Z alone is needed); c is the midpoint of T_J(S)'s Gershgorin interval (its upper
+// end when the lower one is not positive), so the eigenvalues of Y_0 lie in (0, 2), where the iteration
+// converges. X = T_J(S)^-1 is also written in FP32 for the refinement of the centre columns of
+// T_J(S)^-1; a submatrix whose iteration does not converge is flagged for the FP64 preparation.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -85,7 +95,26 @@ struct TcArgs {
   int32_t* err;               // global error flag (timeouts)
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
   int32_t* nbelow;            // eigenvalues below mu, (n - Tr X) / 2 (nullable)
+  // inverse-square-root mode: the chunk's gathered T_J(S), T_J(H0) (FP64, at a_off[J] - a_base and
+  // chunk_n2 further), the outputs and the iteration's stopping rule
+  const double* ws;
+  int64_t a_base, chunk_n2;
+  float* Aout;                // FP32 A_J at a_off[J]
+  float* Xout;                // FP32 T_J(S)^-1 at a_off[J] - a_base
+  int32_t* prep_out;          // kSubOk, or kSubRefine when the iteration failed (FP64 preparation next)
+  float tol_inv;
+  int32_t max_inv;
+  double* flops;              // [2]: 2 n^3 per product (method count) and the split's issued flops, summed
 };
+
+// Epilogue of a product: what is done with the accumulator P
+enum : int {
+  kEpiT = 0,      // T = 3I - P to the planes, and the defect ||I - P||_F^2
+  kEpiScale = 1,  // scale * P to the planes
+  kEpiX = 2,      // scale * P to the planes and in FP32 to Xout
+  kEpiA = 3       // P in FP32 to Aout (no planes)
+};
+constexpr int kPlanesInv = 12;   // inverse mode: plane pairs Y, Z, T (then X), Y', Z', T_J(H0)
 
 constexpr int kSlots = 2;   // submatrices in flight per CTA (their products interleave)
 constexpr int kRing = 4;    // product descriptors between the scheduler and the MMA / epilogue warps
@@ -100,6 +129,8 @@ struct SlotState {
   int phase, refine_left, steps, rsteps, status, last;
   float dprev;                   // defect of the previous step (E4M3 stagnation test)
   Fmt fcur, fnxt;
+  int yc, zc;                    // inverse mode: plane pairs of the current Y and Z
+  float cinv;                    // inverse mode: 1 / c
 };
 
 // One product as scheduled by the producer: read in order by the MMA issuer and the epilogue.
@@ -109,6 +140,8 @@ struct Desc {
   Fmt f, fo;                     // format of the operands; of the operand the epilogue writes
   int n, n64, nrb, ncb, nks;
   int za, zb, zo;                // plane indices (hi planes) of A, B and the output
+  int epi;                       // kEpi*
+  float scale;                   // kEpiScale, kEpiX
 };
 
 struct Shared {
@@ -213,10 +246,13 @@ __device__ __forceinline__ bool epi_bar_or(bool p) {
   return r != 0;
 }
 
+// kMode 0: the sign iteration (a4-a7); kMode 1: the inverse square root of T_J(S) and A_J (a2-a3)
+template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
             const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapA8,
             const __grid_constant__ CUtensorMap mapB8, TcArgs g) {
+  constexpr int kPps = kMode == 0 ? kPlanes : kPlanesInv;   // planes per slot
   extern __shared__ uint8_t smraw[];
   uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Shared sh;
@@ -282,16 +318,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         const SlotState& st = sh.slot[pick];
         d.slot = pick;
         d.kind = st.kind;
-        d.last = st.kind == 1 && st.last;
         d.f = st.fcur;
-        d.fo = st.kind == 0 ? st.fcur : st.fnxt;
         d.n = st.n; d.n64 = st.n64; d.nrb = st.nrb; d.ncb = st.ncb; d.nks = st.nks;
-        const int zb = (sub0 + pick) * kPlanes;
-        d.za = zb + 2 * st.cur;
-        d.zb = st.kind == 0 ? d.za : zb + 4;
-        // X_{k+1} overwrites X_k when one column tile covers the matrix: row block mb of X_k is read
-        // (as the A operand) only by tile (mb, 0), whose loads have completed before its epilogue writes
-        d.zo = st.kind == 0 ? zb + 4 : (st.ncb == 1 ? d.za : zb + 2 * (st.cur ^ 1));
+        const int zb = (sub0 + pick) * kPps;
+        if constexpr (kMode == 0) {   // the epilogue derives epi and scale from the kind
+          d.last = st.kind == 1 && st.last;
+          d.fo = st.kind == 0 ? st.fcur : st.fnxt;
+          d.za = zb + 2 * st.cur;
+          d.zb = st.kind == 0 ? d.za : zb + 4;
+          // X_{k+1} overwrites X_k when one column tile covers the matrix: row block mb of X_k is read
+          // (as the A operand) only by tile (mb, 0), whose loads have completed before its epilogue writes
+          d.zo = st.kind == 0 ? zb + 4 : (st.ncb == 1 ? d.za : zb + 2 * (st.cur ^ 1));
+        } else {
+          // pairs: Y in 0 or 3, Z in 1 or 4 (ping-pong), T and then X in 2, T_J(H0) in 5
+          d.last = st.kind == 4;
+          d.scale = 0.5f;
+          d.fo = st.fcur;
+          switch (st.kind) {
+            case 0:  // V = Z Y -> T = 3I - V
+              d.za = zb + 2 * st.zc; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiT; break;
+            case 1:  // Y' = 1/2 Y T
+              d.za = zb + 2 * st.yc; d.zb = zb + 4; d.zo = zb + 2 * (st.yc == 0 ? 3 : 0); d.epi = kEpiScale; break;
+            case 2:  // Z' = 1/2 T Z
+              d.za = zb + 4; d.zb = zb + 2 * st.zc; d.zo = zb + 2 * (st.zc == 1 ? 4 : 1); d.epi = kEpiScale; break;
+            case 3:  // X = Z Z / c = T_J(S)^-1
+              d.za = zb + 2 * st.zc; d.zb = d.za; d.zo = zb + 4; d.epi = kEpiX; d.scale = st.cinv; break;
+            default:  // A_J = X T_J(H0)
+              d.za = zb + 4; d.zb = zb + 10; d.zo = zb + 4; d.epi = kEpiA; break;
+          }
+        }
       }
       sh.ring[i % kRing] = d;
       tc::mbar_arrive(&sh.desc_full[i % kRing]);
@@ -395,6 +450,80 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
     uint32_t tcount = 0;
 
+    // One n64 x n64 operand (zero padded) into the 3-term FP16 planes hi, lo (hi + plane_elems): four rows
+    // per warp pass, 8 consecutive columns per lane, 16-byte stores; value(i, j) for i, j < n.
+    auto fill_pair = [&](uint16_t* hi, int n, int n64, auto value) {
+      uint16_t* lo = hi + plane_elems;
+      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+        for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+            if (i >= n64) break;
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (i < n && j0 + u < n) ? value(i, j0 + u) : 0.0f;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split2(v[2 * u], v[2 * u + 1], FMT_F16, h[u], l[u]);
+            *reinterpret_cast<uint4*>(hi + (size_t)i * g.LD + j0) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(lo + (size_t)i * g.LD + j0) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+        }
+      }
+    };
+
+    // inverse mode, a new submatrix J in slot s: c from the Gershgorin interval of T_J(S), Y_0 = T_J(S) / c,
+    // Z_0 = I (zero on the padding), T_J(H0) into pair 5
+    auto start_inverse = [&](int s, int J) {
+      SlotState& st = sh.slot[s];
+      const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
+      const double* S = g.ws + (g.a_off[J] - g.a_base);
+      const double* H = S + g.chunk_n2;
+      double glo = INFINITY, ghi = -INFINITY;
+      for (int i = warp - 4; i < n; i += 8) {
+        double r = 0.0, dg = 0.0;
+        for (int j = lane; j < n; j += 32) {
+          const double v = S[(size_t)i * n + j];
+          if (j == i) dg = v; else r += fabs(v);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          r += __shfl_xor_sync(0xffffffffu, r, o);
+          dg += __shfl_xor_sync(0xffffffffu, dg, o);
+        }
+        glo = fmin(glo, dg - r);
+        ghi = fmax(ghi, dg + r);
+      }
+      if (lane == 0) {
+        sh.dred[0][warp - 4] = glo;
+        sh.dred[1][warp - 4] = ghi;
+      }
+      epi_bar();
+      double lo = INFINITY, hi = -INFINITY;
+      for (int w = 0; w < 8; ++w) {
+        lo = fmin(lo, sh.dred[0][w]);
+        hi = fmax(hi, sh.dred[1][w]);
+      }
+      const double c = lo > 0.0 ? 0.5 * (lo + hi) : hi;
+      const float inv = (float)(1.0 / c);
+      uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
+      fill_pair(base, n, n64, [&](int i, int j) { return (float)S[(size_t)i * n + j] * inv; });
+      fill_pair(base + 2 * plane_elems, n, n64, [&](int i, int j) { return i == j ? 1.0f : 0.0f; });
+      fill_pair(base + 10 * plane_elems, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
+      if (tid == 128) {
+        st.job = J;
+        st.n = n; st.n64 = n64; st.R = R;
+        st.nrb = R / 128; st.ncb = (n64 + 255) / 256; st.nks = n64 / 64;
+        st.kind = 0; st.yc = 0; st.zc = 1; st.cinv = inv;
+        st.steps = 0; st.rsteps = 0; st.status = kSubOk; st.last = 0;
+        st.fcur = Fmt{FMT_F16, 3}; st.fnxt = st.fcur;
+        st.dprev = INFINITY;
+        // reject a dimension or scale the planes cannot hold
+        if (!(c > 0.0) || !isfinite(c)) st.status = kSubRefine;
+      }
+      epi_bar();   // dred free again
+    };
+
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
     auto start_slot = [&](int s) {
       SlotState& st = sh.slot[s];
@@ -408,6 +537,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         epi_bar();
         if (J < 0) {
           if (tid == 128) st.job = -1;
+          break;
+        }
+        if constexpr (kMode == 1) {
+          start_inverse(s, J);
           break;
         }
         if (g.prep_status[J] != kSubOk) {
@@ -424,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float* A = g.A + g.a_off[J];
         const double alpha = scale_alpha(g.lam, g.lam_g, J, g.mu);
         const float inv = (float)(1.0 / alpha), fmu = (float)g.mu;
-        uint16_t* hi = g.planes + (size_t)(sub0 + s) * kPlanes * plane_elems;
+        uint16_t* hi = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
         uint16_t* lo = hi + plane_elems;
         const Fmt f = g.main_fmt;
         if (f.fmt == FMT_E4M3) {
@@ -495,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       SlotState& st = sh.slot[s];
       const int J = st.job, n = st.n, b = g.nbf[J];
       // the final X_k, hi (+ lo) in the last product's output format
-      const uint16_t* xh = g.planes + ((size_t)(sub0 + s) * kPlanes + 2 * st.cur) * plane_elems;
+      const uint16_t* xh = g.planes + ((size_t)(sub0 + s) * kPps + 2 * st.cur) * plane_elems;
       const uint16_t* xl = xh + plane_elems;
       const Fmt xfmt = st.fcur;
       const double* Q = g.Q + g.c_off[J];
@@ -612,6 +745,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (d.term) break;
       SlotState& st = sh.slot[d.slot];
       const int n = d.n, n64 = d.n64;
+      // the sign iteration's epilogues are fixed by the product kind (no descriptor fields needed)
+      const int epi = kMode == 0 ? (d.kind == 0 ? kEpiT : kEpiScale) : d.epi;
+      const float escale = kMode == 0 ? 0.5f : (epi == kEpiA ? 1.0f : d.scale);
       float part = 0.0f;
       bool bad = false;   // a wait of this warp ran out: keep the barrier schedule, skip the work
       for (int mb = 0; mb < d.nrb; ++mb)
@@ -633,21 +769,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             float v[32];
             if (live) {
               tc::tmem_wait_ld();
-              if (d.kind == 0) {
+              if (epi == kEpiT) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   const int col = col0 + j;
-                  const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - X^2)_ij
+                  const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - P)_ij
                   if (row < n && col < n) part += e * e;
-                  v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - X^2)_ij
+                  v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - P)_ij
                 }
               } else {
+                const float m = escale * sc;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.5f * sc * __uint_as_float(r[j]);
+                for (int j = 0; j < 32; ++j) v[j] = m * __uint_as_float(r[j]);
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
-            if (d.fo.fmt == FMT_E4M3) {
+            if (kMode == 1 && live && epi >= kEpiX && row < n) {
+              // inverse mode: X or A_J in FP32, row-major n x n
+              const int J = sh.slot[d.slot].job;
+              float* dst = (epi == kEpiX ? g.Xout + (g.a_off[J] - g.a_base) : g.Aout + g.a_off[J]) + (size_t)row * n;
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (col0 + j < n) dst[col0 + j] = v[j];
+            }
+            if (kMode == 1 && epi == kEpiA) {
+              // no operand to write
+            } else if (d.fo.fmt == FMT_E4M3) {
               // E4M3 output (scaled by 2^7): this thread's 32 bytes of the row, two 16-byte stores into the
               // one-byte view of the plane (rows of 2 LD bytes)
               if (live) {
@@ -706,7 +853,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 128) sh.err = 1;
         break;
       }
-      if (tid == 128) {
+      if (kMode == 1 && tid == 128) {
+        // inverse mode: the next product of the slot
+        switch (d.kind) {
+          case 0: {
+            float dsum = 0.0f;
+            for (int w = 0; w < 8; ++w) dsum += sh.red[i & 1][w];
+            const float dd = sqrtf(dsum / (float)n);
+            st.steps += 1;
+            if (!isfinite(dd) || (dd > g.tol_inv && st.steps >= g.max_inv)) {
+              st.status = kSubRefine;   // diverged or too slow: the FP64 preparation takes it
+              st.last = 1;
+            } else if (dd <= g.tol_inv) {
+              st.last = 1;                // this step's Z update is the last product of the iteration
+            }
+            st.kind = st.last ? 2 : 1;
+            break;
+          }
+          case 1: st.yc = st.yc == 0 ? 3 : 0; st.kind = 2; break;
+          case 2: st.zc = st.zc == 1 ? 4 : 1; st.kind = st.last ? 3 : 0; break;
+          case 3: st.kind = 4; break;
+          default: break;
+        }
+      } else if (tid == 128) {
         if (d.kind == 0) {
           // defect of X_step and the decision about the following steps
           float dsum = 0.0f;
@@ -764,7 +933,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (d.last) {
-        finish_slot(d.slot);
+        if constexpr (kMode == 1) {
+          if (tid == 128) {
+            const SlotState& sf = sh.slot[d.slot];
+            g.prep_out[sf.job] = sf.status;
+            const double n3 = (double)sf.n * sf.n * sf.n;
+            const double prods = 3.0 * sf.steps + 1.0;   // the last step skips its Y update; X and A follow
+            atomicAdd(&g.flops[0], 2.0 * n3 * prods);
+            atomicAdd(&g.flops[1], 6.0 * n3 * prods);
+          }
+        } else {
+          finish_slot(d.slot);
+        }
         start_slot(d.slot);
       } else {
         tc::mbar_arrive(&sh.epi_done[d.slot]);
@@ -774,7 +954,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // a wait ran out: the submatrices in flight are reported as timed out
       for (int s = 0; s < kSlots; ++s) {
         const int J = sh.slot[s].job;
-        if (J >= 0) {
+        if (J >= 0 && kMode == 1) {
+          g.prep_out[J] = kSubTimeout;
+        } else if (J >= 0) {
           g.status[J] = kSubTimeout;
           g.iters[J] = sh.slot[s].steps;
           g.rsteps[J] = sh.slot[s].rsteps;
@@ -820,6 +1002,8 @@ struct TcState {
   DevBuf planes, order, err;
   int R = 0, LD = 0, slots = 0;
   int64_t ord_j0 = -1, ord_j1 = -1;
+  DevBuf inv_planes, inv_flops;   // inverse mode: its own plane layout (kPlanesInv per slot), flop sums
+  int iR = 0, iLD = 0, islots = 0;
 };
 
 static TcState* state(nolsm_plan* plan) {
@@ -833,6 +1017,8 @@ void tc_release(nolsm_plan* plan) {
   dev_free(plan, s->planes);
   dev_free(plan, s->order);
   dev_free(plan, s->err);
+  dev_free(plan, s->inv_planes);
+  dev_free(plan, s->inv_flops);
   delete s;
   plan->tc = nullptr;
 }
@@ -940,7 +1126,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
   g.nbelow = plan->nbelow.as<int32_t>();
-  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   // one-byte views of the same planes (rows of 2 LD bytes) for E4M3 operands, both loaded K-major
   CUtensorMap mA8, mB8;
   if (!tmap::make_3d(&mA8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, 128) ||
@@ -951,7 +1137,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   k_status_pending<<<(unsigned)std::min<int64_t>(1024, (work + 255) / 256), 256, 0, st>>>(
       (int32_t)j0, (int32_t)work, spec.list, plan->status.as<int32_t>());
   NOLSM_LAUNCH_CHECK();
-  k_ns_tc<<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, g);
+  k_ns_tc<0><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 2;
   if (sym) {   // D_c = L^-T U and the traces
@@ -968,6 +1154,68 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     NOLSM_TRY(launch_sym_finish(a, (int)work, maxn, plan->max_b, st));
     plan->stats.launches += 1;
   }
+  return NOLSM_OK;
+}
+
+// a2-a3 on the tensor cores for the chunk's submatrices order[0, count) (gathered into args.ws): A_J into
+// Aout, T_J(S)^-1 into Xout, prep_out[J] = kSubOk or kSubRefine. Adds the products' flops to the stats.
+nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_t st) {
+  if (a.count <= 0) return NOLSM_OK;
+  TcState* S = state(plan);
+  int dev = 0, sms = 0;
+  NOLSM_CUDA_TRY(cudaGetDevice(&dev));
+  NOLSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int LD = (a.max_n + 63) & ~63, R = (a.max_n + 127) & ~127;
+  const int ctas = (int)std::min<int64_t>(sms, (a.count + kSlots - 1) / kSlots);
+  const int slots = ctas * kSlots;
+  if (!S->inv_planes.p || S->iR < R || S->iLD < LD || S->islots < slots) {
+    const int nR = std::max(R, S->iR), nLD = std::max(LD, S->iLD), nS = std::max(slots, S->islots);
+    dev_free(plan, S->inv_planes);
+    NOLSM_TRY(dev_alloc(plan, S->inv_planes, sizeof(uint16_t) * (size_t)kPlanesInv * nS * nR * nLD));
+    S->iR = nR;
+    S->iLD = nLD;
+    S->islots = nS;
+  }
+  if (!S->err.p) NOLSM_TRY(dev_alloc(plan, S->err, sizeof(int32_t) * 4));
+  if (!S->inv_flops.p) NOLSM_TRY(dev_alloc(plan, S->inv_flops, sizeof(double) * 2));
+  const uint64_t depth = (uint64_t)S->islots * kPlanesInv;
+  CUtensorMap mA, mB, mS;
+  if (!tmap::make_3d(&mA, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 128) ||
+      !tmap::make_3d(&mB, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 64) ||
+      !tmap::make_3d(&mS, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 32,
+                     CU_TENSOR_MAP_SWIZZLE_64B)) {
+    set_error("cuTensorMapEncodeTiled rejected the inverse scratch layout (R %d, LD %d, slots %d)", S->iR, S->iLD,
+              S->islots);
+    return NOLSM_ERR_CUDA;
+  }
+  NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
+  NOLSM_CUDA_TRY(cudaMemsetAsync(S->err.p, 0, sizeof(int32_t), st));
+  NOLSM_CUDA_TRY(cudaMemsetAsync(S->inv_flops.p, 0, sizeof(double) * 2, st));
+  k_status_pending<<<(unsigned)std::min(1024, (a.count + 255) / 256), 256, 0, st>>>(0, a.count, a.order, a.prep_out);
+  NOLSM_LAUNCH_CHECK();
+  TcArgs g{};
+  g.j0 = 0; g.j1 = a.count;
+  g.order = a.order;
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
+  g.main_fmt = Fmt{FMT_F16, 3}; g.refine_fmt = g.main_fmt;
+  g.planes = S->inv_planes.as<uint16_t>();
+  g.R = S->iR; g.LD = S->iLD;
+  g.next = plan->counter.as<int32_t>();
+  g.err = S->err.as<int32_t>();
+  g.ws = a.ws; g.a_base = a.a_base; g.chunk_n2 = a.chunk_n2;
+  g.Aout = a.Aout; g.Xout = a.Xout; g.prep_out = a.prep_out;
+  g.tol_inv = a.tol_inv; g.max_inv = a.max_inv;
+  g.flops = S->inv_flops.as<double>();
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  k_ns_tc<1><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
+  NOLSM_LAUNCH_CHECK();
+  double fl[2];
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(fl, S->inv_flops.p, sizeof(fl), cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  plan->stats.flops_prep_tensor += fl[0];
+  plan->stats.flops_prep_tensor_issued += fl[1];
+  plan->stats.launches += 2;
   return NOLSM_OK;
 }
 
@@ -1096,8 +1344,8 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
   g.rsteps = ints + 2 * kNaMaxSub;
   g.nbelow = nullptr;
-  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
   NOLSM_LAUNCH_CHECK();
   return NOLSM_OK;
 }

@@ -11,6 +11,25 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
 // products per Newton-Schulz product in the main phase of a precision (1 or 3)
 int main_terms(int precision);
 
+// a2-a3 by the coupled Newton-Schulz inverse square root on the tensor cores (Eqs. inv1-inv3), for the
+// submatrices order[0, count) of one preparation chunk: T_J(S), T_J(H0) gathered in FP64 at ws +
+// (a_off[J] - a_base) and chunk_n2 further; A_J (FP32) to Aout + a_off[J]; T_J(S)^-1 (FP32) to Xout +
+// a_off[J] - a_base; prep_out[J] = kSubOk, or kSubRefine when the iteration did not reach tol_inv within
+// max_inv steps (the FP64 preparation then takes the submatrix), or kSubTimeout.
+struct NsInvArgs {
+  const int32_t* order;
+  int32_t count;
+  int32_t max_n;
+  const double* ws;
+  int64_t a_base, chunk_n2;
+  float* Aout;
+  float* Xout;
+  int32_t* prep_out;
+  float tol_inv;
+  int32_t max_inv;
+};
+nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_t st);
+
 // frees the tensor-core path's workspaces held by the plan
 void tc_release(nolsm_plan* plan);
 

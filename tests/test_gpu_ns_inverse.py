@@ -1,0 +1,169 @@
+"""The tensor-core coupled Newton-Schulz inverse square root (Sec. "Efficient Iterative Matrix Function
+Solvers on GPU Tensor Cores", Eqs. inv1-inv3) as the preparation of A_J = T_J(S)^-1 T_J(H0).
+
+With options.inverse = NOLSM_INVERSE_NEWTON_SCHULZ the library iterates Y, Z on the tensor cores
+(three-term FP16 split products, FP32 accumulation), forms T_J(S)^-1 = Z^2 / c and A_J = T_J(S)^-1 T_J(H0)
+as two more products, and refines the centre columns of T_J(S)^-1 with a double-FP32 residual. Checked
+here against the FP64 oracle of Eqs. inv1-inv3 (oracle/inverse_oracle.py: A_J from its T_J(S)^-1, and
+its centre columns), against the Cholesky preparation, and through the whole solve against the FP64
+oracle's density at the tolerances of each mode.
+
+Tolerances: A_J in FP32 from three-term FP16 products accumulated in FP32 carries about 2^-22 sqrt(n)
+relative error per product; 7 products in sequence keep max|dA| / max|A| below 1e-5 for n <= 1000 (the
+numpy emulation of the same arithmetic gives 1.6e-6 at n = 180). The refined centre columns of T_J(S)^-1
+reach the double-FP32 residual's accuracy, about 1e-12 (checked at 1e-10)."""
+import numpy as np
+import pytest
+
+from oracle import inverse_oracle as inv
+from oracle import nolsm_oracle as orc
+from synth import SystemSpec, make_system, spec_small_fp64
+
+pytestmark = pytest.mark.gpu
+
+TOL_D = {"fp32": 1e-6, "bf16x3": 1e-4, "fp16": 1e-4}
+TOL_TR = 1e-5
+TOL_A = 1e-5
+TOL_Q = 1e-10
+
+
+@pytest.fixture(scope="module")
+def nl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_08245_gb300 import build
+    build.build()
+    import paper_2104_08245_gb300 as nl
+    return nl
+
+
+def d_error(po, ref, D, subs):
+    """max|dD| over the blocks (I, J), I in N(J), of the listed submatrices against the oracle's columns."""
+    off = orc.d_block_offsets(po)
+    err = 0.0
+    for J in subs:
+        cols = ref.subs[J].D_cols
+        bJ = int(po.nbf[J])
+        for p in range(po.nb_ptr[J], po.nb_ptr[J + 1]):
+            I = int(po.nb_idx[p])
+            q = po.nb_ptr[I] + int(np.nonzero(po.nb_idx[po.nb_ptr[I]:po.nb_ptr[I + 1]] == J)[0][0])
+            got = D[off[q]:off[q + 1]].reshape(int(po.nbf[I]), bJ)
+            err = max(err, float(np.max(np.abs(got - cols[po.nb_off[p]:po.nb_off[p] + got.shape[0], :]))))
+    return err
+
+
+def prepared_vs_oracle(nl, sysm, subs, prec="fp32"):
+    """(max relative |dA| over subs, max |dQ|, the NS and Cholesky A's relative difference) against the
+    oracle's coupled iteration."""
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    A, Q, ps = nl.nolsm_plan_get_prepared(plan, nl.options(prec, inverse=nl._abi.INVERSE_NEWTON_SCHULZ))
+    A2, _, _ = nl.nolsm_plan_get_prepared(plan, nl.options(prec, inverse=nl._abi.INVERSE_CHOLESKY))
+    assert np.all(ps.cpu().numpy() == 0)
+    A, Q, A2 = A.cpu().numpy(), Q.cpu().numpy(), A2.cpu().numpy()
+    n = po.sub_n.astype(np.int64)
+    a_off = np.concatenate([[0], np.cumsum(n * n)])
+    c_off = np.concatenate([[0], np.cumsum(n * po.nbf.astype(np.int64))])
+    eA = eQ = eC = 0.0
+    for J in subs:
+        S = orc.gather(po, J, sysm.S.row_ptr, sysm.S.col_idx, sysm.S.blk_off, sysm.S.vals)
+        H = orc.gather(po, J, sysm.H.row_ptr, sysm.H.col_idx, sysm.H.blk_off, sysm.H.vals)
+        Sinv, k, ok = inv.overlap_inverse_ns(S)
+        assert ok
+        Aref = Sinv @ H
+        m = int(n[J])
+        Ag = A[a_off[J]:a_off[J + 1]].reshape(m, m).astype(np.float64)
+        Ac = A2[a_off[J]:a_off[J + 1]].reshape(m, m).astype(np.float64)
+        scale = np.max(np.abs(Aref))
+        eA = max(eA, float(np.max(np.abs(Ag - Aref))) / scale)
+        eC = max(eC, float(np.max(np.abs(Ag - Ac))) / scale)
+        c0, b = int(po.sub_c0[J]), int(po.nbf[J])
+        Qg = Q[c_off[J]:c_off[J + 1]].reshape(m, b)
+        eQ = max(eQ, float(np.max(np.abs(Qg - Sinv[:, c0:c0 + b]))))
+    plan.close()
+    return eA, eQ, eC
+
+
+def test_prepared_A_and_Q_match_the_inverse_oracle(nl):
+    sysm = make_system(spec_small_fp64())
+    eA, eQ, eC = prepared_vs_oracle(nl, sysm, range(sysm.n_mol))
+    print(f"64 molecules: max|dA|/max|A| = {eA:.3e} (vs Cholesky preparation {eC:.3e}), max|dQ| = {eQ:.3e}")
+    assert eA <= TOL_A and eC <= TOL_A and eQ <= TOL_Q
+
+
+def test_prepared_larger_than_one_tile(nl):
+    """n about 430 (8 A cutoff): four row blocks, column tiles of 256 + 192, both ping-pong pairs."""
+    sysm = make_system(SystemSpec(6, 6, 6, cutoff=8.0, seed=17))
+    eA, eQ, eC = prepared_vs_oracle(nl, sysm, [0, 37, 101, 215])
+    print(f"n~430: max|dA|/max|A| = {eA:.3e} (vs Cholesky {eC:.3e}), max|dQ| = {eQ:.3e}")
+    assert eA <= TOL_A and eC <= TOL_A and eQ <= TOL_Q
+
+
+def test_prepared_split_valence(nl):
+    """23 functions per molecule: n = 598..713, six row blocks, three column tiles, up to twelve K slices."""
+    sysm = make_system(SystemSpec(8, 8, 8, nbf="23", seed=1104))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    subs = [int(np.argmin(po.sub_n)), int(np.argmax(po.sub_n)), 100]
+    eA, eQ, eC = prepared_vs_oracle(nl, sysm, subs)
+    print(f"23 functions: max|dA|/max|A| = {eA:.3e} (vs Cholesky {eC:.3e}), max|dQ| = {eQ:.3e}")
+    assert eA <= TOL_A and eC <= TOL_A and eQ <= TOL_Q
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16"])
+def test_density_with_the_tensor_core_inverse(nl, prec):
+    sysm = make_system(spec_small_fp64())
+    ref = orc.solve(sysm, -0.1)
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    r = nl.nolsm_solve_batch(plan, -0.1, nl.options(prec, inverse=nl._abi.INVERSE_NEWTON_SCHULZ))
+    D = plan.scatter().cpu().numpy()
+    err = float(np.max(np.abs(D - ref.D_vals)))
+    print(f"{prec} with the tensor-core inverse: max|dD| = {err:.3e}")
+    assert err <= TOL_D[prec]
+    assert abs(r.trace_DH - ref.trace_DH) / abs(ref.trace_DH) <= TOL_TR
+    assert abs(r.trace_DS - ref.trace_DS) / abs(ref.trace_DS) <= TOL_TR
+    assert np.all(r.sub_status.cpu().numpy() == 0)
+    st = plan.stats()
+    assert st["flops_prep_tensor"] > 0 and st["ms_prep_tensor"] > 0
+    plan.close()
+
+
+def test_density_full_size_sampled(nl):
+    """32,768 molecules with the density field (n 114..294), every submatrix in one preparation chunk;
+    512 sampled submatrices against the oracle in the FP32 and BF16X3 modes."""
+    from synth import spec_batched_uneven
+    sysm = make_system(spec_batched_uneven())
+    mu = -0.1
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    rng = np.random.default_rng(17)
+    subs = set(int(j) for j in rng.choice(sysm.n_mol, size=510, replace=False))
+    subs |= {int(np.argmax(po.sub_n)), int(np.argmin(po.sub_n))}
+    subs = sorted(subs)
+    ref = orc.solve(sysm, mu, subs=subs, plan=po)
+    for prec in ("fp32", "bf16x3"):
+        r = nl.nolsm_solve_batch(plan, mu, nl.options(prec, inverse=nl._abi.INVERSE_NEWTON_SCHULZ))
+        D = plan.scatter().cpu().numpy()
+        err = d_error(po, ref, D, subs)
+        tH = r.sub_t_H.cpu().numpy()
+        rel = max(abs(tH[J] - ref.subs[J].t_H) / abs(ref.subs[J].t_H) for J in subs)
+        print(f"full size {prec}, tensor-core inverse: sampled max|dD| = {err:.3e}, max rel t_H = {rel:.3e}")
+        assert err <= TOL_D[prec]
+        assert rel <= TOL_TR
+        assert np.all(r.sub_status.cpu().numpy() == 0)
+    plan.close()
+
+
+def test_not_spd_overlap_falls_back_and_is_reported(nl):
+    """A negated diagonal block of S makes T_J(S) indefinite for the submatrices that contain it: the
+    coupled iteration does not converge, the FP64 factorisation takes them and reports NOT_SPD; the others
+    are prepared on the tensor cores."""
+    sysm = make_system(spec_small_fp64())
+    p = int(np.nonzero(sysm.S.col_idx[sysm.S.row_ptr[5]:sysm.S.row_ptr[6]] == 5)[0][0]) + sysm.S.row_ptr[5]
+    sysm.S.vals[sysm.S.blk_off[p]:sysm.S.blk_off[p + 1]] *= -1.0
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    r = nl.nolsm_solve_batch(plan, -0.1, nl.options("bf16x3", inverse=nl._abi.INVERSE_NEWTON_SCHULZ), check=False)
+    assert r.status == nl._abi.ERR_NOT_SPD
+    st = r.sub_status.cpu().numpy()
+    assert np.sum(st == nl._abi.ERR_NOT_SPD) > 0
+    assert np.sum(st == 0) > 0
