@@ -133,21 +133,44 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------ oracle (CPU)
-# The main process builds the oracle's plan and gathers the sampled submatrices (Sec. "The Submatrix
-# Method", step (i)); spawned workers solve them one by one (FP64 oracle), so no worker holds the system.
+# The main process builds the oracle's plan and writes it with the block-CSR system to a temporary
+# directory; spawned workers map those files read-only (one copy in the page cache), gather their
+# submatrices (Sec. "The Submatrix Method", step (i)) and solve them one by one with the FP64 oracle.
+
+_ORC = {}
+_FIELDS = ("row_ptr", "col_idx", "blk_off", "vals")
+_PLAN_FIELDS = ("nb_ptr", "nb_idx", "nb_off", "sub_n", "sub_c0", "nbf")
+
+
+def _oracle_init(path):
+    import numpy as np
+    from oracle import nolsm_oracle as orc
+    ld = lambda k: np.load(os.path.join(path, k + ".npy"), mmap_mode="r")
+    _ORC["S"] = tuple(ld("S_" + k) for k in _FIELDS)
+    _ORC["H"] = tuple(ld("H_" + k) for k in _FIELDS)
+    _ORC["plan"] = orc.OraclePlan(*(np.asarray(ld("P_" + k)) for k in _PLAN_FIELDS))
+
+
+def _oracle_gather(J):
+    from oracle import nolsm_oracle as orc
+    p = _ORC["plan"]
+    return orc.gather(p, J, *_ORC["S"]), orc.gather(p, J, *_ORC["H"])
+
 
 def _oracle_sub(item):
     from oracle import nolsm_oracle as orc
-    J, S_sub, H_sub, mu, c0, b = item
-    r = orc.submatrix_density(S_sub, H_sub, mu, c0, b)
+    J, mu = item
+    S_sub, H_sub = _oracle_gather(J)
+    p = _ORC["plan"]
+    r = orc.submatrix_density(S_sub, H_sub, mu, int(p.sub_c0[J]), int(p.nbf[J]))
     return J, (r.D_cols, r.t_S, r.t_H)
 
 
-def _oracle_gersh(item):
-    """Gershgorin interval of A = T_J(S)^-1 T_J(H0) of one gathered submatrix (reference arm's bracket)."""
+def _oracle_gersh(J):
+    """Gershgorin interval of A = T_J(S)^-1 T_J(H0) (reference arm's bracket)."""
     import numpy as np
     from oracle import nolsm_oracle as orc
-    _, S_sub, H_sub = item
+    S_sub, H_sub = _oracle_gather(J)
     A = orc.overlap_inverse(S_sub) @ H_sub
     d = np.diag(A)
     R = np.sum(np.abs(A), axis=1) - np.abs(d)
@@ -155,43 +178,43 @@ def _oracle_gersh(item):
 
 
 class OracleSample:
-    """The oracle's plan of a system and a pool of spawned workers for sampled submatrices."""
+    """The oracle's plan of a system and a pool of spawned workers that solve sampled submatrices."""
 
     def __init__(self, sysm, workers):
         import multiprocessing as mp
+        import tempfile
+
+        import numpy as np
         from oracle import nolsm_oracle as orc
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-        self.sysm = sysm
         self.plan = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+        self.dir = tempfile.mkdtemp(prefix="nolsm_oracle_")
+        for name, m in (("S", sysm.S), ("H", sysm.H)):
+            for k in _FIELDS:
+                np.save(os.path.join(self.dir, f"{name}_{k}.npy"), getattr(m, k))
+        for k in _PLAN_FIELDS:
+            np.save(os.path.join(self.dir, f"P_{k}.npy"), getattr(self.plan, k))
         self.workers = workers
-        self.pool = mp.get_context("spawn").Pool(workers)
-        import numpy as np
-        self.pool.map(_oracle_gersh, [(0, np.eye(1), np.zeros((1, 1)))] * workers)   # start the workers
-
-    def gather(self, J):
-        from oracle import nolsm_oracle as orc
-        s, p = self.sysm, self.plan
-        return (orc.gather(p, J, s.S.row_ptr, s.S.col_idx, s.S.blk_off, s.S.vals),
-                orc.gather(p, J, s.H.row_ptr, s.H.col_idx, s.H.blk_off, s.H.vals))
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(self.dir,))
+        self.pool.map(_oracle_gersh, [0] * workers)   # start every worker before anything is timed
 
     def solve(self, subs, mu):
-        """({J: (D_cols, t_S, t_H)}, seconds) for the listed submatrices at mu, gather included."""
+        """({J: (D_cols, t_S, t_H)}, seconds) for the listed submatrices at mu, gathers included."""
         t0 = time.perf_counter()
-        items = []
-        for J in subs:
-            S_sub, H_sub = self.gather(J)
-            items.append((J, S_sub, H_sub, mu, int(self.plan.sub_c0[J]), int(self.plan.nbf[J])))
-        out = dict(self.pool.map(_oracle_sub, items, chunksize=max(1, len(items) // (4 * self.workers))))
+        out = dict(self.pool.map(_oracle_sub, [(J, mu) for J in subs],
+                                 chunksize=max(1, len(subs) // (4 * self.workers))))
         return out, time.perf_counter() - t0
 
     def bracket(self, subs):
-        items = [(J, *self.gather(J)) for J in subs]
-        b = self.pool.map(_oracle_gersh, items)
+        b = self.pool.map(_oracle_gersh, list(subs))
         return min(x[0] for x in b), max(x[1] for x in b)
 
     def close(self):
+        import shutil
         self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
 
 
 # ------------------------------------------------------------------------------------ reference arm
@@ -241,8 +264,7 @@ def reference_arm(args, spec_name, desc):
                        "molecules_per_gpu": n_mol, "bracket": "Gershgorin interval of the sampled submatrices",
                        "sample": f"{len(sample)} submatrices, their own electron count, {nev} bisection points"},
             "cpu_baseline": {"value": value, "unit": "submatrices/s", "cores": workers, "kind": "oracle",
-                             "sample": f"oracle bisection on {len(sample)} sampled submatrices per step "
-                                       "(gathered on one core, solved on all)"},
+                             "sample": f"oracle bisection on {len(sample)} sampled submatrices per step"},
             "e2e": {"value": value, "unit": "submatrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -499,6 +521,42 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = ev0.elapsed_time(ev1) / args.steps
 
+    # the same end to end with the elements generated on the device from the geometry (Sec. "Minimization of
+    # Communication"): per step only the block patterns, positions and on-site energies go to the device
+    mdl = nl.ElementModel(sysm, dev)
+    host_g = {k: host[k] for k in ("nbf", "s_row_ptr", "s_col_idx", "h_row_ptr", "h_col_idx")}
+    host_g["pos"] = mdl.pos.cpu().pin_memory()
+    host_g["onsite"] = mdl.onsite.cpu().pin_memory()
+    h2d_g = sum(t.numel() * t.element_size() for t in host_g.values())
+
+    def e2e_gen_step():
+        e = _Sys()
+        dv = {k: t.to(dev, non_blocking=True) for k, t in host_g.items()}
+        for k in ("nbf", "s_row_ptr", "s_col_idx", "h_row_ptr", "h_col_idx"):
+            setattr(e, k, dv[k])
+        e.s_vals = e.h_vals = None
+        e.n_mol, e.n_occ = n_mol, n_occ
+        e.struct = lambda: nl.DeviceSystem.struct(e)
+        m = nl.ElementModel.__new__(nl.ElementModel)
+        m.pos, m.onsite, m.dirs, m.cell, m.params = dv["pos"], dv["onsite"], mdl.dirs, mdl.cell, mdl.params
+        plan = nl.nolsm_build_submatrices(e)
+        nl.nolsm_plan_set_elements(plan, m)
+        r_ = find_mu(plan)
+        plan.scatter(D_e2e)
+        plan.close()
+        d_host.copy_(D_e2e, non_blocking=True)
+        return r_
+
+    e2e_gen_step()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rg = e2e_gen_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e_gen = ev0.elapsed_time(ev1) / args.steps
+    gen_mu_diff = abs(rg.mu - r0.mu)
+
     if rank != 0:
         return 0
 
@@ -540,8 +598,8 @@ def main():
         roofline = roof_sign
 
     extra = {"mu": mu_star, "trace_DS": r.trace_DS, "n_occ": n_occ, "bisection_points": evals,
-             "ms_phases": {k: mean(k) for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_sign",
-                                                 "ms_reduce", "ms_scatter")},
+             "ms_phases": {k: mean(k) for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_prep_tensor",
+                                                 "ms_sign", "ms_reduce", "ms_scatter")},
              "ns_steps_per_submatrix": st["ns_steps"] / max(1, st["sub_solves"]),
              "submatrix_n": [info.min_n, info.max_n]}
 
@@ -674,6 +732,11 @@ def main():
                    "batches": f"{nb} contiguous molecule ranges, errors reported per range"},
         "e2e": {"value": n_mol / (ms_e2e / 1e3), "unit": "submatrices/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "e2e_generated": {"value": n_mol / (ms_e2e_gen / 1e3), "unit": "submatrices/s", "h2d_bytes_per_step": h2d_g,
+                          "d2h_bytes_per_step": d2h, "mu_difference_to_stored_elements": gen_mu_diff,
+                          "note": "elements of T_J(S), T_J(H0) generated on the device from positions and on-site "
+                                  "energies; per step the block patterns, positions and on-site energies are "
+                                  "copied instead of the block-CSR values"},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "roofline_sign": roof_sign,

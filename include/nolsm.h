@@ -91,7 +91,8 @@ typedef enum {
  * nbf[I] x nbf[J] float64 values row-major; blocks are concatenated in CSR order. The two patterns
  * may differ (their union is the merged pattern); each must be structurally symmetric. All arrays
  * are device memory owned by the caller and must stay valid and unchanged until the plan built from
- * them is destroyed. */
+ * them is destroyed. s_vals and h_vals may be NULL when the plan's elements are generated on the device
+ * from the geometry (nolsm_plan_set_elements): the patterns alone are then the metadata. */
 typedef struct {
   int32_t n_mol;
   const int32_t* nbf;       /* (device) [n_mol], basis functions per molecule, 1..64 */
@@ -134,6 +135,10 @@ typedef struct {
                             T_J(S)^-1 are refined to about 1e-12 with a double-FP32 residual, and a submatrix
                             that fails is prepared again with the FP64 factorisation. Ignored by NOLSM_FP64 and
                             the symmetric form (which keep the Cholesky factor). */
+  int64_t wait_ns;       /* tensor-core sign kernel: limit of each device-side wait of one warp role on another
+                            (a product's operands, its accumulator, the next descriptor), in ns; <= 0: 2 s. A
+                            wait that runs out ends the kernel early: the submatrices in flight and those not
+                            yet taken report NOLSM_ERR_TIMEOUT (a small limit makes that happen on purpose) */
 } nolsm_options;
 
 enum { NOLSM_INVERSE_CHOLESKY = 0, NOLSM_INVERSE_NEWTON_SCHULZ = 1 };
@@ -171,6 +176,34 @@ nolsm_status nolsm_build_submatrices(const nolsm_system* sys, nolsm_stream_t str
 
 nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info);
 
+/* Matrix elements generated on the device (Sec. "Minimization of Communication": only the submatrices' row
+ * indices, species and positions reach the GPU, and the elements of the submatrices are computed there). The
+ * plan's block patterns say which blocks exist; their values come from the synthetic water-like model of
+ * this library's benchmarks (the paper's GFN-xTB element formulas are not part of this work): for molecules
+ * I != J with a stored block and minimum-image vector d from I to J, r = |d|, every entry (a, c) is
+ *   S_IJ[a][c] = exp(-s_exp r^2) / sqrt(b_I b_J) * (1 + aniso (u_a - u_c)),
+ *   H_IJ[a][c] = hop exp(-r / hop_len) / sqrt(b_I b_J) * (1 + aniso (w_a - w_c)),
+ * with u_a = (d / r) . dirs[0][a], w_a = (d / r) . dirs[1][a] (only when aniso != 0); the diagonal blocks are
+ * S_II = identity and H_II = diag(onsite of I). Computed in FP64 (the paper uses FP32 for its special-function
+ * units; here the FP64 path's 1e-9 parity needs the elements to FP64 rounding).
+ *   pos (device, [n_mol][3], Angstrom), cell (host, 3 periodic edges), onsite (device, [sum of nbf]: the
+ *   on-site energies of each molecule's functions, molecules in order), dirs (device, [2][64][3], read only
+ *   when aniso != 0; may be NULL otherwise). The arrays must stay valid until the plan is destroyed.
+ * After this call every preparation generates T_J(S), T_J(H0) (and the centre columns) from the model instead
+ * of reading s_vals / h_vals; geometry caches prepared before are discarded. NOLSM_ERR_ARG on NULL pointers
+ * or non-positive cell edges. */
+typedef struct {
+  const double* pos;
+  double cell[3];
+  const double* onsite;
+  double s_exp;
+  double hop, hop_len;
+  double aniso;
+  const double* dirs;
+} nolsm_element_model;
+
+nolsm_status nolsm_plan_set_elements(nolsm_plan* plan, const nolsm_element_model* model);
+
 /* Copies the plan's integer maps into caller device buffers (any pointer may be NULL):
  * nb_ptr [n_mol+1], nb_idx [d_nnzb], nb_off [d_nnzb], sub_n [n_mol], sub_c0 [n_mol],
  * d_blk_off [d_nnzb+1] (int64 element offsets of the D blocks). The merged pattern of D is
@@ -184,9 +217,16 @@ nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_
  * symmetric form's M_J = L^-1 T_J(H0) L^-T instead) and Q (float64, the centre columns of T_J(S)^-1, n_J x
  * b_J row-major at c_off[J]), where a_off and c_off are the exclusive prefix sums of n_J^2 and n_J b_J over
  * J = 0 .. n_mol-1 (only the range's entries are written). prep_status (device int32 [n_mol], may be NULL):
- * NOLSM_OK or NOLSM_ERR_NOT_SPD per submatrix. Synchronises the stream. */
+ * NOLSM_OK or NOLSM_ERR_NOT_SPD per submatrix. cond_est (device float [n_mol], may be NULL; tensor-core modes
+ * with the standard form only, else left untouched): a lower estimate of cond(T_J(S)), (max_i L_ii /
+ * min_i L_ii)^2 of the FP32 Cholesky factor or max_i S_ii (T_J(S)^-1)_ii after the inverse square root (about
+ * 3.4e38 where the FP32 preparation failed). A tensor-core solve hands every submatrix whose estimate exceeds
+ * 10 (NOLSM_FP32) or 30 (the other tensor-core modes) to the FP64 path before its own solve, and after it
+ * every submatrix that failed the low-precision accept test or turned non-finite; nolsm_stats.ill_conditioned
+ * counts them. Only submatrices of at most 775 rows (the FP64 factorisation's shared-memory panel) are
+ * handed over. Synchronises the stream. */
 nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
-                                     double* Q, int32_t* prep_status);
+                                     double* Q, int32_t* prep_status, float* cond_est);
 
 /* a1-a7: every submatrix J in [sub_begin, sub_end) at chemical potential mu:
  *   T_J(S), T_J(H0) gathered (a1); T_J(S) = L L^T in FP64 (a2); A_J = T_J(S)^-1 T_J(H0) (a3);
@@ -337,6 +377,8 @@ typedef struct {
   double ms_prep_tensor;       /* the tensor-core inverse-square-root kernel alone (part of ms_factor) */
   double flops_prep_tensor;    /* its products, 2 n^3 each on the unpadded n (the paper's count) */
   double flops_prep_tensor_issued; /* the same x3 (three-term split products) */
+  int64_t ill_conditioned;     /* submatrices of tensor-core solves that were solved on the FP64 path: overlap
+                                  too ill-conditioned for the mode, or the low-precision solve failed */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);

@@ -18,7 +18,8 @@ from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
            "nolsm_energy_weighted", "nolsm_combine_submatrices",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
-           "nolsm_spectral_bracket", "nolsm_plan_get_prepared", "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
+           "nolsm_spectral_bracket", "nolsm_plan_get_prepared", "nolsm_plan_set_elements", "ElementModel",
+           "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
            "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
            "options", "NolsmError", "Plan", "SolveResult", "MuResult"]
 
@@ -59,9 +60,10 @@ def options(precision="fp64", **kw) -> NolsmOptions:
 
 
 class DeviceSystem:
-    """Block-CSR S and H0 copied to device tensors (caller-owned memory for the ABI)."""
+    """Block-CSR S and H0 copied to device tensors (caller-owned memory for the ABI). values=False copies
+    the patterns only (the elements are then generated on the device, nolsm_plan_set_elements)."""
 
-    def __init__(self, system, device="cuda"):
+    def __init__(self, system, device="cuda", values=True):
         torch = _torch()
         dev = torch.device(device)
         as_t = lambda a, dt: torch.as_tensor(a, dtype=dt).to(dev)
@@ -69,10 +71,10 @@ class DeviceSystem:
         self.nbf = as_t(system.nbf, torch.int32)
         self.s_row_ptr = as_t(system.S.row_ptr, torch.int32)
         self.s_col_idx = as_t(system.S.col_idx, torch.int32)
-        self.s_vals = as_t(system.S.vals, torch.float64)
+        self.s_vals = as_t(system.S.vals, torch.float64) if values else None
         self.h_row_ptr = as_t(system.H.row_ptr, torch.int32)
         self.h_col_idx = as_t(system.H.col_idx, torch.int32)
-        self.h_vals = as_t(system.H.vals, torch.float64)
+        self.h_vals = as_t(system.H.vals, torch.float64) if values else None
         self.n_occ = float(system.n_occ)
 
     def struct(self) -> NolsmSystem:
@@ -81,10 +83,10 @@ class DeviceSystem:
         s.nbf = self.nbf.data_ptr()
         s.s_nnzb = self.s_col_idx.numel()
         s.s_row_ptr, s.s_col_idx, s.s_vals = (self.s_row_ptr.data_ptr(), self.s_col_idx.data_ptr(),
-                                              self.s_vals.data_ptr())
+                                              _ptr(self.s_vals))
         s.h_nnzb = self.h_col_idx.numel()
         s.h_row_ptr, s.h_col_idx, s.h_vals = (self.h_row_ptr.data_ptr(), self.h_col_idx.data_ptr(),
-                                              self.h_vals.data_ptr())
+                                              _ptr(self.h_vals))
         return s
 
 
@@ -96,6 +98,44 @@ def nolsm_build_submatrices(dsys: DeviceSystem, stream=None) -> "Plan":
     if rc != 0:
         raise NolsmError(rc, "nolsm_build_submatrices")
     return Plan(out, dsys)
+
+
+class ElementModel:
+    """Device copies of the geometry and the parameters of the synthetic element model for
+    nolsm_plan_set_elements: positions [n_mol][3], the cell, every molecule's on-site energies in order, the
+    S and H0 parameters and (for the direction modulation) the direction vectors [2][64][3]."""
+
+    def __init__(self, system, device="cuda"):
+        import numpy as np
+        torch = _torch()
+        dev = torch.device(device)
+        sp = system.spec
+        self.pos = torch.as_tensor(np.ascontiguousarray(system.pos), dtype=torch.float64).to(dev)
+        self.onsite = torch.as_tensor(np.concatenate([np.asarray(o, dtype=np.float64) for o in system.onsite]),
+                                      dtype=torch.float64).to(dev)
+        dirs = np.zeros((2, 64, 3))
+        if system.dirs is not None:
+            dirs[:, :system.dirs.shape[1], :] = system.dirs
+        self.dirs = torch.as_tensor(dirs, dtype=torch.float64).to(dev)
+        self.cell = [float(c) for c in system.cell]
+        self.params = (sp.s_exp, sp.hop, sp.hop_len, sp.aniso)
+
+    def struct(self):
+        m = _abi.NolsmElementModel()
+        m.pos, m.onsite, m.dirs = self.pos.data_ptr(), self.onsite.data_ptr(), self.dirs.data_ptr()
+        for k in range(3):
+            m.cell[k] = self.cell[k]
+        m.s_exp, m.hop, m.hop_len, m.aniso = self.params
+        return m
+
+
+def nolsm_plan_set_elements(plan: "Plan", model: ElementModel) -> None:
+    """Generate the plan's matrix elements on the device from the geometry from now on."""
+    m = model.struct()
+    rc = _abi.load().nolsm_plan_set_elements(plan.handle, ctypes.byref(m))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_plan_set_elements")
+    plan.model = model   # keeps the device arrays alive while the plan may use them
 
 
 def nolsm_plan_query(plan: "Plan") -> NolsmPlanInfo:
@@ -126,8 +166,9 @@ def nolsm_plan_get_maps(plan: "Plan", stream=None) -> dict:
 
 
 def nolsm_plan_get_prepared(plan: "Plan", opts: NolsmOptions, stream=None):
-    """(A, Q, prep_status) device tensors of the options' preparation: A_J (float32, float64 for FP64) packed
-    at the exclusive prefix sums of n_J^2, Q (float64, centre columns of T_J(S)^-1) at those of n_J b_J."""
+    """(A, Q, prep_status, cond_est) device tensors of the options' preparation: A_J (float32, float64 for
+    FP64) packed at the exclusive prefix sums of n_J^2, Q (float64, centre columns of T_J(S)^-1) at those of
+    n_J b_J, and the preparation's lower estimate of cond(T_J(S)) (tensor-core standard form; else zero)."""
     torch = _torch()
     maps = nolsm_plan_get_maps(plan, stream)
     n = maps["sub_n"].to(torch.int64)
@@ -136,11 +177,12 @@ def nolsm_plan_get_prepared(plan: "Plan", opts: NolsmOptions, stream=None):
     A = torch.zeros(int((n * n).sum()), dtype=torch.float64 if opts.precision == FP64 else torch.float32, device=dev)
     Q = torch.zeros(int((n * b).sum()), dtype=torch.float64, device=dev)
     ps = torch.zeros(plan.dsys.n_mol, dtype=torch.int32, device=dev)
+    rr = torch.zeros(plan.dsys.n_mol, dtype=torch.float32, device=dev)
     rc = _abi.load().nolsm_plan_get_prepared(plan.handle, ctypes.byref(opts), _stream(stream), A.data_ptr(),
-                                             Q.data_ptr(), ps.data_ptr())
+                                             Q.data_ptr(), ps.data_ptr(), rr.data_ptr())
     if rc != 0:
         raise NolsmError(rc, "nolsm_plan_get_prepared")
-    return A, Q, ps
+    return A, Q, ps, rr
 
 
 def nolsm_spectral_bracket(plan: "Plan", opts: NolsmOptions, stream=None):

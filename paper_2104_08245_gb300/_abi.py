@@ -30,7 +30,7 @@ class NolsmOptions(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("refine_steps", c_int32), ("max_iter", c_int32),
                 ("tol_ns", c_double), ("tol_accept", c_double), ("tol_n", c_double), ("tol_mu", c_double),
                 ("max_bisect", c_int32), ("bound_source", c_int32), ("sub_begin", c_int64), ("sub_end", c_int64),
-                ("symmetric_form", c_int32), ("inverse", c_int32)]
+                ("symmetric_form", c_int32), ("inverse", c_int32), ("wait_ns", c_int64)]
 
 
 class NolsmBisection(ctypes.Structure):
@@ -40,6 +40,11 @@ class NolsmBisection(ctypes.Structure):
 
 # nolsm_bisection.state
 BISECT_ACCEPTED, BISECT_EVALUATE, BISECT_NO_PLATEAU = range(3)
+
+
+class NolsmElementModel(ctypes.Structure):
+    _fields_ = [("pos", c_void_p), ("cell", c_double * 3), ("onsite", c_void_p), ("s_exp", c_double),
+                ("hop", c_double), ("hop_len", c_double), ("aniso", c_double), ("dirs", c_void_p)]
 
 
 class NolsmPlanInfo(ctypes.Structure):
@@ -54,7 +59,7 @@ class NolsmStats(ctypes.Structure):
                 ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64), ("ms_gather", c_double),
                 ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64),
                 ("ms_energy_weighted", c_double), ("ms_prep_tensor", c_double), ("flops_prep_tensor", c_double),
-                ("flops_prep_tensor_issued", c_double)]
+                ("flops_prep_tensor_issued", c_double), ("ill_conditioned", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,6 +70,7 @@ SIGNATURES = [
     ("nolsm_options_default", None, [ctypes.POINTER(NolsmOptions), c_int32]),
     ("nolsm_build_submatrices", c_int32, [ctypes.POINTER(NolsmSystem), c_void_p, ctypes.POINTER(c_void_p)]),
     ("nolsm_plan_query", c_int32, [c_void_p, ctypes.POINTER(NolsmPlanInfo)]),
+    ("nolsm_plan_set_elements", c_int32, [c_void_p, ctypes.POINTER(NolsmElementModel)]),
     ("nolsm_plan_get_maps", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
     ("nolsm_solve_batch", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p,
@@ -78,7 +84,7 @@ SIGNATURES = [
                                 ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_int32),
                                 ctypes.POINTER(c_double)]),
     ("nolsm_plan_get_prepared", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p, c_void_p,
-                                          c_void_p]),
+                                          c_void_p, c_void_p]),
     ("nolsm_spectral_bracket", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p,
                                          ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     ("nolsm_bisect_begin", c_int32, [c_void_p, ctypes.POINTER(NolsmOptions), c_void_p, c_int32]),

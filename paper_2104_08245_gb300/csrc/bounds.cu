@@ -130,6 +130,20 @@ __global__ void __launch_bounds__(kPowThreads) k_power_bounds(PowArgs g, const T
 }
 
 // On-site statistics per molecule I: sum and sum of squares of diag(H0_II), and b_I.
+// The same sums from the element model's on-site energies (generated elements: H0_II = diag(onsite of I)).
+__global__ void k_onsite_model(int32_t n_mol, const int64_t* __restrict__ off, const double* __restrict__ e,
+                               double* __restrict__ out /* [n_mol][2] */) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n_mol) return;
+  double s = 0.0, q = 0.0;
+  for (int64_t k = off[I]; k < off[I + 1]; ++k) {
+    s += e[k];
+    q += e[k] * e[k];
+  }
+  out[2 * I] = s;
+  out[2 * I + 1] = q;
+}
+
 __global__ void k_onsite(int32_t n_mol, const int32_t* __restrict__ nbf, const int32_t* __restrict__ rp,
                          const int32_t* __restrict__ ci, const int64_t* __restrict__ boff,
                          const double* __restrict__ vals, double* __restrict__ out /* [n_mol][2] */) {
@@ -654,9 +668,13 @@ nolsm_status features(nolsm_plan* plan, double mu, int64_t j0, int64_t j1, cudaS
   NOLSM_TRY(ensure_buf(plan, plan->feat, sizeof(float) * kFeatures * n));
   if (!plan->onsite_done) {
     NOLSM_TRY(ensure_buf(plan, plan->onsite, sizeof(double) * 2 * n));
-    k_onsite<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(plan->n_mol, plan->sys.nbf, plan->sys.h_row_ptr,
-                                                          plan->sys.h_col_idx, plan->h_blk_off.as<int64_t>(),
-                                                          plan->sys.h_vals, plan->onsite.as<double>());
+    if (plan->gen)
+      k_onsite_model<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(plan->n_mol, plan->onsite_off.as<int64_t>(),
+                                                                  plan->model.onsite, plan->onsite.as<double>());
+    else
+      k_onsite<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(plan->n_mol, plan->sys.nbf, plan->sys.h_row_ptr,
+                                                            plan->sys.h_col_idx, plan->h_blk_off.as<int64_t>(),
+                                                            plan->sys.h_vals, plan->onsite.as<double>());
     NOLSM_LAUNCH_CHECK();
     plan->stats.launches += 1;
     plan->onsite_done = true;

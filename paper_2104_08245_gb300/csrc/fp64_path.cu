@@ -52,7 +52,42 @@ struct GatherArgs {
   int32_t max_nq;       // largest |N(J)|: each warp's lookup tables hold 3 max_nq ints
   double* ws;           // [2*chunk_n2]
   double* Sc; double* Hc;
+  // elements generated from the geometry (gen != 0) instead of read from sval / hval
+  int gen;
+  const double* pos; double cell[3]; const double* onsite; const int64_t* onsite_off;
+  double s_exp, hop, hop_len, aniso; const double* dirs;
 };
+
+// The synthetic element model of nolsm_plan_set_elements for the block (Ia, Ic), Ia != Ic: the isotropic
+// values of S and H0 and the unit vector from Ia to Ic. Every product and sum is rounded on its own (no
+// contraction into FMAs), in the order the model states them.
+struct BlockModel { double s, h, ux, uy, uz; };
+__device__ __forceinline__ BlockModel block_model(const GatherArgs& g, int Ia, int Ic, int ba, int bc) {
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double v = __dsub_rn(g.pos[3 * Ic + k], g.pos[3 * Ia + k]);
+    d[k] = __dsub_rn(v, __dmul_rn(g.cell[k], rint(__ddiv_rn(v, g.cell[k]))));   // minimum image
+  }
+  const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+  const double inv = __ddiv_rn(1.0, sqrt((double)(ba * bc)));
+  BlockModel m;
+  m.s = __dmul_rn(inv, exp(__dmul_rn(__dmul_rn(-g.s_exp, r), r)));
+  m.h = __dmul_rn(inv, __dmul_rn(g.hop, exp(__ddiv_rn(-r, g.hop_len))));
+  m.ux = __ddiv_rn(d[0], r);
+  m.uy = __ddiv_rn(d[1], r);
+  m.uz = __ddiv_rn(d[2], r);
+  return m;
+}
+
+// the direction modulation 1 + aniso (u . dirs[k][a] - u . dirs[k][c])
+__device__ __forceinline__ double aniso_factor(const GatherArgs& g, int k, const BlockModel& m, int a, int c) {
+  const double* da = g.dirs + (k * 64 + a) * 3;
+  const double* dc = g.dirs + (k * 64 + c) * 3;
+  const double ua = __dadd_rn(__dadd_rn(__dmul_rn(m.ux, da[0]), __dmul_rn(m.uy, da[1])), __dmul_rn(m.uz, da[2]));
+  const double uc = __dadd_rn(__dadd_rn(__dmul_rn(m.ux, dc[0]), __dmul_rn(m.uy, dc[1])), __dmul_rn(m.uz, dc[2]));
+  return __dadd_rn(1.0, __dmul_rn(g.aniso, __dsub_rn(ua, uc)));
+}
 
 constexpr int kGatherWarps = 8;
 
@@ -61,6 +96,8 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t p = g.p0 + (int64_t)blockIdx.x * kGatherWarps + w;
   if (p >= g.p1) return;   // whole warps only; no block-wide barrier follows
+  // generated elements: the block models of the band, after every warp's integer tables (8-byte aligned)
+  BlockModel* bm = reinterpret_cast<BlockModel*>(sm + ((kGatherWarps * 3 * g.max_nq + 1) & ~1)) + w * g.max_nq;
   const int J = owner_of(g.nb_ptr, g.n_mol, p);
   const int q0 = g.nb_ptr[J], nq = g.nb_ptr[J + 1] - q0;
   const int Ia = g.nb_idx[p];
@@ -75,6 +112,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
     s_slot[c] = find_sorted(g.sci, g.srp[Ia], g.srp[Ia + 1], Ic);
     h_slot[c] = find_sorted(g.hci, g.hrp[Ia], g.hrp[Ia + 1], Ic);
     coff[c] = g.nb_off[q0 + c];
+    if (g.gen && Ic != Ia) bm[c] = block_model(g, Ia, Ic, ba, g.nbf[Ic]);
   }
   __syncwarp();
   const int c0 = g.sub_c0[J];
@@ -90,8 +128,18 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
       const int bc = g.nbf[g.nb_idx[q0 + c]];
       const int cc = col - coff[c];
       const int ss = s_slot[c], hs = h_slot[c];
-      const double vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
-      const double vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
+      double vs, vh;
+      if (!g.gen) {
+        vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
+        vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
+      } else if (g.nb_idx[q0 + c] == Ia) {   // intra-molecular: identity and the on-site energies
+        vs = (ss >= 0 && r == cc) ? 1.0 : 0.0;
+        vh = (hs >= 0 && r == cc) ? g.onsite[g.onsite_off[Ia] + r] : 0.0;
+      } else {
+        const BlockModel& m = bm[c];
+        vs = ss >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.s, aniso_factor(g, 0, m, r, cc)) : m.s) : 0.0;
+        vh = hs >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.h, aniso_factor(g, 1, m, r, cc)) : m.h) : 0.0;
+      }
       const int64_t at = (int64_t)(offa + r) * n + col;
       TS[at] = vs;
       TH[at] = vh;
@@ -394,6 +442,12 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     NOLSM_TRY(dev_alloc(plan, plan->prep_status, sizeof(int32_t) * n_mol));
     NOLSM_CUDA_TRY(cudaMemsetAsync(plan->prep_status.p, 0, sizeof(int32_t) * n_mol, st));
   }
+  const bool ratio = !keep_fp64_A && !sym;   // the tensor-core classes record their cond(T_J(S)) estimate
+  if (ratio && !P.cond.p) {
+    NOLSM_TRY(dev_alloc(plan, P.cond, sizeof(float) * (size_t)std::max(n_mol, 1)));
+    P.h_cond.assign((size_t)n_mol, 0.0f);
+  }
+  bool any_chunk = false;
   if (sym && !plan->Lsym.p) {
     NOLSM_TRY(dev_alloc(plan, plan->Lsym, sizeof(float) * (size_t)std::max<int64_t>(plan->h_a_off[n_mol], 1)));
     NOLSM_TRY(dev_alloc(plan, plan->Wc, sizeof(double) * nc));
@@ -411,7 +465,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       ++e;
     const int64_t n2 = plan->h_a_off[e] - plan->h_a_off[J];
     NOLSM_TRY(ensure(plan, plan->ws_dense, sizeof(double) * 2 * (size_t)n2));
-    GatherArgs g;
+    GatherArgs g{};
     g.n_mol = n_mol;
     g.nbf = plan->sys.nbf;
     g.srp = plan->sys.s_row_ptr; g.sci = plan->sys.s_col_idx; g.soff = plan->s_blk_off.as<int64_t>();
@@ -429,13 +483,29 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     const int64_t bands = plan->h_nb_ptr[e] - plan->h_nb_ptr[J];
     g.p1 = plan->h_nb_ptr[e];
     g.max_nq = max_nq;
+    g.gen = plan->gen ? 1 : 0;
+    if (plan->gen) {
+      const nolsm_element_model& m = plan->model;
+      g.pos = m.pos; g.cell[0] = m.cell[0]; g.cell[1] = m.cell[1]; g.cell[2] = m.cell[2];
+      g.onsite = m.onsite; g.onsite_off = plan->onsite_off.as<int64_t>();
+      g.s_exp = m.s_exp; g.hop = m.hop; g.hop_len = m.hop_len; g.aniso = m.aniso; g.dirs = m.dirs;
+    } else if (!plan->sys.s_vals || !plan->sys.h_vals) {
+      set_error("the plan has neither element values nor an element model (nolsm_plan_set_elements)");
+      return NOLSM_ERR_ARG;
+    }
     pmark(plan, st);
-    const size_t gsm = sizeof(int32_t) * 3 * kGatherWarps * (size_t)max_nq;
+    const size_t gsm = sizeof(int32_t) * (size_t)((kGatherWarps * 3 * max_nq + 1) & ~1) +
+                       (plan->gen ? sizeof(BlockModel) * kGatherWarps * (size_t)max_nq : 0);
     if (gsm > 48 * 1024) NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     k_gather<<<(unsigned)((bands + kGatherWarps - 1) / kGatherWarps), 32 * kGatherWarps, gsm, st>>>(g);
     NOLSM_LAUNCH_CHECK();
     pmark(plan, st);
     PrepArgs pa;
+    any_chunk = true;
+    if (ratio) {   // a submatrix whose FP32 preparation fails keeps this huge estimate (bytes 0x7F: about 3.4e38)
+      pa.cond = P.cond.as<float>();
+      NOLSM_CUDA_TRY(cudaMemsetAsync(pa.cond + J, 0x7F, sizeof(float) * (size_t)(e - J), st));
+    }
     pa.j0 = (int32_t)J;
     pa.sub_n = plan->sub_n.as<int32_t>(); pa.sub_c0 = plan->sub_c0.as<int32_t>(); pa.nbf = plan->sys.nbf;
     pa.a_off = plan->a_off.as<int64_t>(); pa.c_off = plan->c_off.as<int64_t>();
@@ -535,6 +605,11 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       P.done[k] = 1;
     }
     J = e;
+  }
+  if (ratio && any_chunk) {
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(P.h_cond.data() + j0, P.cond.as<float>() + j0, sizeof(float) * (size_t)(j1 - j0),
+                                   cudaMemcpyDeviceToHost, st));
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return NOLSM_OK;
 }

@@ -10,6 +10,7 @@
 
 #include "nolsm_internal.cuh"
 #include "bounds.cuh"
+#include "prep.cuh"
 #include "tc_path.cuh"
 
 namespace nolsm {
@@ -146,7 +147,8 @@ nolsm_plan::~nolsm_plan() {
   DevBuf* all[] = {&s_blk_off, &h_blk_off, &nb_ptr, &nb_idx, &nb_off, &sub_n, &sub_c0, &d_blk_off, &d_slot,
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &prep_ns.A, &Lsym, &Wc, &Dc,
                    &t_S, &t_H, &iters, &status, &rsteps, &nbelow, &nb_lo, &nb_hi, &active, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
-                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym, &Wd, &tW};
+                   &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym, &Wd, &tW,
+                   &prep32.cond, &prep_ns.cond, &ill_list, &onsite_off};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
   if (ev_ok)
@@ -196,7 +198,7 @@ const char* nolsm_last_error(void) { return g_err; }
 nolsm_status nolsm_build_submatrices(const nolsm_system* sys, nolsm_stream_t stream, nolsm_plan** out) {
   if (!out) { set_error("nolsm_build_submatrices: out is NULL"); return NOLSM_ERR_ARG; }
   *out = nullptr;
-  if (!sys || sys->n_mol <= 0 || !sys->nbf || !sys->s_row_ptr || !sys->h_row_ptr || !sys->s_vals || !sys->h_vals ||
+  if (!sys || sys->n_mol <= 0 || !sys->nbf || !sys->s_row_ptr || !sys->h_row_ptr ||
       sys->s_nnzb <= 0 || sys->h_nnzb <= 0 || !sys->s_col_idx || !sys->h_col_idx ||
       sys->s_nnzb > INT32_MAX || sys->h_nnzb > INT32_MAX) {
     set_error("nolsm_build_submatrices: missing or inconsistent system arrays");
@@ -232,6 +234,28 @@ nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info) {
   info->min_n = plan->min_n;
   info->sum_n3 = plan->sum_n3;
   info->device_bytes = plan->bytes;
+  return NOLSM_OK;
+}
+
+nolsm_status nolsm_plan_set_elements(nolsm_plan* plan, const nolsm_element_model* m) {
+  if (!plan || !m || !m->pos || !m->onsite || (m->aniso != 0.0 && !m->dirs) ||
+      !(m->cell[0] > 0.0 && m->cell[1] > 0.0 && m->cell[2] > 0.0) || !std::isfinite(m->s_exp) ||
+      !std::isfinite(m->hop) || !(m->hop_len > 0.0) || !std::isfinite(m->aniso)) {
+    set_error("nolsm_plan_set_elements: NULL array or invalid model parameter");
+    return NOLSM_ERR_ARG;
+  }
+  const int32_t n = plan->n_mol;
+  std::vector<int64_t> off((size_t)n + 1, 0);
+  for (int32_t I = 0; I < n; ++I) off[(size_t)I + 1] = off[(size_t)I] + plan->h_nbf[(size_t)I];
+  if (!plan->onsite_off.p) NOLSM_TRY(dev_alloc(plan, plan->onsite_off, sizeof(int64_t) * off.size()));
+  NOLSM_CUDA_TRY(cudaMemcpy(plan->onsite_off.p, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice));
+  plan->model = *m;
+  plan->gen = true;
+  // the geometry caches were prepared from other elements (or none): prepare again
+  for (Prepared* P : {&plan->prep64, &plan->prep32, &plan->prep_sym, &plan->prep_ns}) P->done.assign(P->done.size(), 0);
+  plan->pow_done.assign(plan->pow_done.size(), 0);
+  plan->onsite_done = false;
+  plan->have_solution = false;
   return NOLSM_OK;
 }
 
@@ -287,6 +311,75 @@ static nolsm_status bound_spec(nolsm_plan* plan, int source, double mu, const no
   return NOLSM_OK;
 }
 
+// Submatrices of a tensor-core solve that go to the FP64 path instead (host list): FP64 preparation of them
+// (in runs of consecutive indices; cached like any preparation), then the FP64 sign iteration on their list.
+static nolsm_status solve_on_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1,
+                                  std::vector<int32_t>& subs, cudaStream_t st) {
+  if (subs.empty()) return NOLSM_OK;
+  std::sort(subs.begin(), subs.end());
+  for (size_t a = 0; a < subs.size();) {
+    size_t b = a + 1;
+    while (b < subs.size() && subs[b] == subs[b - 1] + 1) ++b;
+    NOLSM_TRY(prepare(plan, subs[a], (int64_t)subs[b - 1] + 1, kPrepFP64, st));
+    a = b;
+  }
+  if (!plan->ill_list.p) NOLSM_TRY(dev_alloc(plan, plan->ill_list, sizeof(int32_t) * (size_t)plan->n_mol));
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->ill_list.p, subs.data(), sizeof(int32_t) * subs.size(), cudaMemcpyHostToDevice, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));   // subs is a host vector
+  nolsm_options o64;
+  nolsm_options_default(&o64, NOLSM_FP64);
+  o64.max_iter = std::max(o.max_iter, o64.max_iter);
+  SolveSpec fs;
+  fs.list = plan->ill_list.as<int32_t>();
+  fs.count = (int32_t)subs.size();
+  NOLSM_TRY(solve_fp64(plan, mu, o64, j0, j1, fs, st));
+  plan->stats.ill_conditioned += (int64_t)subs.size();
+  return NOLSM_OK;
+}
+
+// Before a tensor-core solve's own kernel: the submatrices of the work (the list, else the range) whose
+// overlap is too ill-conditioned for the mode (cond estimate above cond_max; the sign kernel skips them).
+static nolsm_status ill_conditioned_list(nolsm_plan* plan, const nolsm_options& o, int cls, int64_t j0, int64_t j1,
+                                         const int32_t* list, int32_t count, cudaStream_t st, std::vector<int32_t>* out) {
+  out->clear();
+  const Prepared& P = prepared(plan, cls);
+  if (!P.cond.p || P.h_cond.empty()) return NOLSM_OK;
+  const float lim = cond_max(o.precision);
+  const int max_n = prepare_fp64_max_n();   // larger submatrices stay on the tensor path
+  auto take = [&](int32_t J) {
+    if (P.h_cond[(size_t)J] > lim && plan->h_sub_n[(size_t)J] <= max_n) out->push_back(J);
+  };
+  if (list) {
+    std::vector<int32_t> cand((size_t)count);
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(cand.data(), list, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost, st));
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int32_t J : cand) take(J);
+  } else {
+    for (int64_t J = j0; J < j1; ++J) take((int32_t)J);
+  }
+  return NOLSM_OK;
+}
+
+// After a tensor-core solve (and its bound-source reruns): the submatrices of the range that failed the accept
+// test or turned non-finite and that the FP64 path can take (a wait that gave up stays reported as such).
+static nolsm_status failed_fp64_list(nolsm_plan* plan, int64_t j0, int64_t j1, cudaStream_t st, std::vector<int32_t>* out) {
+  out->clear();
+  std::vector<int32_t> stv((size_t)(j1 - j0)), ps((size_t)(j1 - j0));
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(stv.data(), plan->status.as<int32_t>() + j0, sizeof(int32_t) * stv.size(),
+                                 cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(ps.data(), plan->prep_status.as<int32_t>() + j0, sizeof(int32_t) * ps.size(),
+                                 cudaMemcpyDeviceToHost, st));
+  NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+  const int max_n = prepare_fp64_max_n();
+  for (int64_t J = j0; J < j1; ++J) {
+    const int32_t s = stv[(size_t)(J - j0)];
+    if (s != kSubNotConv && s != kSubNonFinite) continue;
+    if (ps[(size_t)(J - j0)] == kSubNotSpd) continue;   // an indefinite overlap stays reported
+    if (plan->h_sub_n[(size_t)J] <= max_n) out->push_back((int32_t)J);
+  }
+  return NOLSM_OK;
+}
+
 // The solve of nolsm_solve_batch, restricted to the device list[0, count) of submatrices of the range
 // when `list` is set (the others keep their previous results; the trace sums cover the whole range).
 static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options* opts, cudaStream_t st,
@@ -307,7 +400,10 @@ static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options*
     spec.count = count;
   }
   mark(plan, 1, st);
+  std::vector<int32_t> handed;
+  if (!fp64 && cls != kPrepSym) NOLSM_TRY(ill_conditioned_list(plan, *opts, cls, j0, j1, list, count, st, &handed));
   NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, spec, st) : solve_tc(plan, mu, *opts, j0, j1, spec, st));
+  NOLSM_TRY(solve_on_fp64(plan, mu, *opts, j0, j1, handed, st));
   // submatrices that failed the convergence test under learned bounds are solved again with power
   // bounds, under power bounds with the Gershgorin interval
   while (level > NOLSM_BOUND_GERSHGORIN) {
@@ -326,6 +422,11 @@ static nolsm_status solve_impl(nolsm_plan* plan, double mu, const nolsm_options*
     }
     NOLSM_TRY(fp64 ? solve_fp64(plan, mu, *opts, j0, j1, rs, st) : solve_tc(plan, mu, *opts, j0, j1, rs, st));
     plan->stats.reruns += count;
+  }
+  // no submatrix is accepted unconverged: what the low-precision solve left failed goes to the FP64 path
+  if (!fp64 && cls != kPrepSym) {
+    NOLSM_TRY(failed_fp64_list(plan, j0, j1, st, &handed));
+    NOLSM_TRY(solve_on_fp64(plan, mu, *opts, j0, j1, handed, st));
   }
   mark(plan, 2, st);
   double tS = 0, tH = 0;
@@ -410,7 +511,7 @@ nolsm_status nolsm_scatter_density(nolsm_plan* plan, double* D_vals, nolsm_strea
 }
 
 nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
-                                     double* Q, int32_t* prep_status) {
+                                     double* Q, int32_t* prep_status, float* cond_est) {
   if (!plan) { set_error("nolsm_plan_get_prepared: NULL plan"); return NOLSM_ERR_ARG; }
   int64_t j0, j1;
   NOLSM_TRY(check_options(plan, opts, &j0, &j1));
@@ -431,6 +532,9 @@ nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts
   if (prep_status)
     NOLSM_CUDA_TRY(cudaMemcpyAsync(prep_status + j0, plan->prep_status.as<int32_t>() + j0,
                                    sizeof(int32_t) * (size_t)(j1 - j0), cudaMemcpyDeviceToDevice, st));
+  if (cond_est && P.cond.p)
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(cond_est + j0, P.cond.as<float>() + j0, sizeof(float) * (size_t)(j1 - j0),
+                                   cudaMemcpyDeviceToDevice, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
   return NOLSM_OK;
 }

@@ -46,7 +46,20 @@ struct Prepared {
   bool fp64 = false;          // true: A held in FP64 (plain path); false: FP32 (tensor-core paths)
   DevBuf A;                   // A_J = T_J(S)^-1 T_J(H0), n_J x n_J row-major at a_off[J]
   std::vector<uint8_t> done;  // host flag per submatrix: prepared
+  // tensor-core preparations: a lower estimate of cond(T_J(S)), (max_i L_ii / min_i L_ii)^2 from the FP32
+  // Cholesky factor, max_i S_ii (T_J(S)^-1)_ii from the inverse square root (float per submatrix, device
+  // and host copies; huge when the FP32 preparation failed)
+  DevBuf cond;
+  std::vector<float> h_cond;
 };
+
+// Above this estimate the overlap is too ill-conditioned for the mode: A_J = T_J(S)^-1 T_J(H0) is then far
+// from normal (its eigenvectors are T_J(S)-orthogonal, with condition number about sqrt(cond)), and the
+// low-precision products' rounding, amplified by it, keeps the sign from the mode's accuracy (or from
+// converging at all); such a submatrix is prepared and solved on the FP64 path instead. The FP32 mode
+// (1e-6 target) takes cond <= 10, the other modes (1e-4) cond <= 30; the synthetic water overlaps have
+// 1.06 to 1.3.
+inline float cond_max(int precision) { return precision == NOLSM_FP32 ? 10.0f : 30.0f; }
 
 }  // namespace nolsm
 
@@ -66,6 +79,11 @@ struct nolsm_plan {
   nolsm::DevBuf d_slot;                     // int32 [d_nnzb]: slot of block (nb_idx[p], J) in D
   nolsm::DevBuf a_off, c_off;               // int64 [n_mol+1]: offsets of n^2 and n*b arrays
   nolsm::DevBuf flag;                       // int32 scratch flag
+
+  // elements generated on the device from the geometry (nolsm_plan_set_elements) instead of read
+  bool gen = false;
+  nolsm_element_model model{};
+  nolsm::DevBuf onsite_off;                 // int64 [n_mol+1]: offsets of each molecule's on-site energies
 
   // host copies
   std::vector<int32_t> h_sub_n, h_nbf, h_nb_ptr;
@@ -91,6 +109,7 @@ struct nolsm_plan {
   nolsm::DevBuf lam_m;              // float64 [2*n_mol]: learned interval
   nolsm::DevBuf budget;             // int32 [n_mol]: learned step budget
   nolsm::DevBuf rerun;              // int32 [n_mol + 1]: failed submatrices, then their count
+  nolsm::DevBuf ill_list;           // int32 [n_mol]: submatrices a tensor-core solve hands to the FP64 path
   const nolsm_mlp* mlp = nullptr;   // network used by NOLSM_BOUND_MLP (caller-owned)
 
   // per-mu results

@@ -29,6 +29,7 @@ struct PrepArgs {
   int32_t sym = 0;
   float* Ysym = nullptr;      // L^-1 T_J(H0), same offsets as ws
   double* Wc = nullptr;       // W_c = L^-1 E_c, n x b at c_off (plan-wide)
+  float* cond = nullptr;      // estimate of cond(T_J(S)) per submatrix (nullable), see Prepared::cond
 };
 
 // The symmetric form's finishing step: D_c = L^-T U (U left in Dc by the sign kernel), traces.

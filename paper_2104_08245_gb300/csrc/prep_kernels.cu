@@ -35,6 +35,7 @@ constexpr int kThreads = 128;   // several CTAs (submatrices) per SM overlap eac
 constexpr int kMaxB = 64;
 constexpr int kRefineMax = 4;   // refinement steps of Q before a submatrix falls back to the FP64 factor
 constexpr double kRefineTol = 1e-6;
+constexpr double kNsOneStep = 3e-6;   // k_ns_qrefine: a first correction below this ends the refinement
 
 // Row stride of panels and tiles in shared memory: FP64 rows padded by one element (bank spread),
 // FP32 rows by four so that every row starts on a 16-byte boundary (vector loads).
@@ -1016,6 +1017,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   if (tid == 0) s_bad = 0;
   __syncthreads();
   bool ok = cholesky32(L, S, n, Pf, Xs, &s_bad);
+  if (ok && g.cond) {
+    // cond(T_J(S)) >= (max_i L_ii / min_i L_ii)^2; the factor keeps 1 / L_ii on its diagonal, whose ratio is
+    // the same
+    float mn = INFINITY, mx = 0.0f;
+    for (int i = tid; i < n; i += kThreads) {
+      const float d = L[(size_t)i * n + i];
+      mn = fminf(mn, d);
+      mx = fmaxf(mx, d);
+    }
+    rlo[tid] = mn;
+    rhi[tid] = mx;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        rlo[tid] = fminf(rlo[tid], rlo[tid + s]);
+        rhi[tid] = fmaxf(rhi[tid], rhi[tid + s]);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) g.cond[J] = (rhi[0] / rlo[0]) * (rhi[0] / rlo[0]);
+    __syncthreads();
+  }
   if (ok) {
     // A_J = L^-T L^-1 T_J(H0) in FP32, and the FP32 first solve of Q when its b columns fit in the
     // last column batch
@@ -1116,6 +1139,17 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
     const int i = e / bJ, c = e - i * bJ;
     q[e] = (double)X[(size_t)i * n + c0 + c];
   }
+  if (g.cond) {   // cond(T_J(S)) >= max_i S_ii (T_J(S)^-1)_ii
+    float mx = 0.0f;
+    for (int i = tid; i < n; i += kThreads) mx = fmaxf(mx, (float)S[(size_t)i * n + i] * X[(size_t)i * n + i]);
+    rhi[tid] = mx;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+      if (tid < s) rhi[tid] = fmaxf(rhi[tid], rhi[tid + s]);
+      __syncthreads();
+    }
+    if (tid == 0) g.cond[J] = rhi[0];
+  }
   __syncthreads();
   bool conv = false;
   for (int it = 0; it < kRefineMax && !conv; ++it) {
@@ -1155,7 +1189,10 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
       dm = fmaxf(dm, red_d[w2]);
       qm = fmax(qm, red_q[w2]);
     }
-    conv = (double)dm <= kRefineTol * qm;   // the same shared values in every thread
+    // converged when the correction is below 1e-6 of q, or after the first step when that correction (the
+    // error of X's columns, about the contraction factor ||I - X T_J(S)|| too) is below 3e-6 of q: the error
+    // left is then about its square, below 1e-11 of q
+    conv = (double)dm <= kRefineTol * qm || (it == 0 && (double)dm <= kNsOneStep * qm);
     __syncthreads();
   }
   if (conv) gershgorin(Acache + g.a_off[J], n, g.lam + 2 * J, rlo, rhi);

@@ -27,10 +27,11 @@
 // and Z_0 = I, V_k = Z_k Y_k, Y_{k+1} = 1/2 Y_k (3I - V_k), Z_{k+1} = 1/2 (3I - V_k) Z_k, Z_k tends to
 // (T_J(S)/c)^-1/2, so T_J(S)^-1 = Z^2 / c (Eq. inv3) and A_J = (Z^2 / c) T_J(H0). Every product is a
 // three-term FP16 split. The step whose V_k has ||I - V_k||_F / sqrt(n) <= tol_inv is the last (its Y
-// update is skipped, Z alone is needed); c is the midpoint of T_J(S)'s Gershgorin interval (its upper
-// end when the lower one is not positive), so the eigenvalues of Y_0 lie in (0, 2), where the iteration
-// converges. X = T_J(S)^-1 is also written in FP32 for the refinement of the centre columns of
-// T_J(S)^-1; a submatrix whose iteration does not converge is flagged for the FP64 preparation.
+// update is skipped, Z alone is needed); c = Tr T_J(S) / n, the mean eigenvalue, so that the eigenvalues
+// of Y_0 average 1 and lie in (0, 2), where the iteration converges, unless the largest eigenvalue of
+// T_J(S) exceeds twice the mean (then the defect grows, and the submatrix, like any whose iteration does
+// not reach tol_inv within max_inv steps, is flagged for the FP64 preparation). X = T_J(S)^-1 is also
+// written in FP32 for the refinement of the centre columns of T_J(S)^-1.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -57,7 +58,7 @@ constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
 constexpr uint32_t kStgBytes = 128 * 64;                // 8 KB; the epilogue's staging is 4 kStgBytes
 constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + a 4 KB hi/lo buffer per epilogue warp
 constexpr int kPlanes = 6;
-constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait; one product takes < 1 ms
+constexpr uint64_t kWaitNs = 2000000000ull;        // default limit per wait (2 s); one product takes < 1 ms
 
 enum : int { FMT_F16 = 0, FMT_BF16 = 1, FMT_E4M3 = 2 };
 
@@ -95,6 +96,10 @@ struct TcArgs {
   int32_t* err;               // global error flag (timeouts)
   double* Dc; double* tS; double* tH; int32_t* iters; int32_t* status; int32_t* rsteps;
   int32_t* nbelow;            // eigenvalues below mu, (n - Tr X) / 2 (nullable)
+  uint64_t wait_ns;           // limit of every wait on another role (the teardown's own waits: 50 ms)
+  const float* cond;          // preparation's cond(T_J(S)) estimate (nullable): above cond_max the submatrix
+  float cond_max;             // is left to the FP64 path (its status stays as it is) when it has at most
+  int32_t ill_max_n;          // ill_max_n rows (what the FP64 preparation takes)
   // inverse-square-root mode: the chunk's gathered T_J(S), T_J(H0) (FP64, at a_off[J] - a_base and
   // chunk_n2 further), the outputs and the iteration's stopping rule
   const double* ws;
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int pick = -1;
       while (!sh.err && (alive[0] || alive[1])) {
         if (alive[s]) {
-          if (!tc::mbar_wait(&sh.epi_done[s], epar[s], tc::globaltimer() + 4 * kWaitNs)) { sh.err = 1; break; }
+          if (!tc::mbar_wait(&sh.epi_done[s], epar[s], tc::globaltimer() + 4 * g.wait_ns)) { sh.err = 1; break; }
           epar[s] ^= 1;
           tc::fence_proxy_async_global();   // the epilogue's plane writes, before TMA reads them
           if (sh.slot[s].job >= 0) { pick = s; break; }
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
-            if (!tc::mbar_wait(&sh.empty[st], ph ^ 1, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+            if (!tc::mbar_wait(&sh.empty[st], ph ^ 1, tc::globaltimer() + g.wait_ns)) { sh.err = 1; break; }
             uint8_t* sm = stage_mem + st * kStageBytes;
             tc::mbar_arrive_expect_tx(&sh.full[st], bytes);
             armed[st] = true;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ MMA issuer: the products in the scheduler's order
     uint32_t kcount = 0, tcount = 0;
     for (uint32_t i = 0; !sh.err; ++i) {
-      if (!tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * kWaitNs)) {
+      if (!tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * g.wait_ns)) {
         sh.err = 1;
         break;
       }
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // kind::f16: A K-major, B MN-major; kind::f8f6f4 (E4M3 = 0): both K-major
           const uint32_t id = f8 ? tc::idesc(0, 0, 0, 0, 128, nt) : tc::idesc(d.f.fmt, d.f.fmt, 0, 1, 128, nt);
           const int buf = tcount & 1;
-          if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + kWaitNs)) {
+          if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + g.wait_ns)) {
             sh.err = 1;
             break;
           }
@@ -411,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
-            if (!tc::mbar_wait(&sh.full[st], ph, tc::globaltimer() + kWaitNs)) { sh.err = 1; break; }
+            if (!tc::mbar_wait(&sh.full[st], ph, tc::globaltimer() + g.wait_ns)) { sh.err = 1; break; }
             tc::tc_fence_after();
             const uint32_t a0 = tc::smem_u32(stage_mem + st * kStageBytes);
             const uint32_t b0 = a0 + 2 * kABytes;
@@ -473,38 +478,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
 
-    // inverse mode, a new submatrix J in slot s: c from the Gershgorin interval of T_J(S), Y_0 = T_J(S) / c,
-    // Z_0 = I (zero on the padding), T_J(H0) into pair 5
+    // inverse mode, a new submatrix J in slot s: c = Tr T_J(S) / n, Y_0 = T_J(S) / c, Z_0 = I (zero on the
+    // padding), T_J(H0) into pair 5
     auto start_inverse = [&](int s, int J) {
       SlotState& st = sh.slot[s];
       const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
       const double* S = g.ws + (g.a_off[J] - g.a_base);
       const double* H = S + g.chunk_n2;
-      double glo = INFINITY, ghi = -INFINITY;
-      for (int i = warp - 4; i < n; i += 8) {
-        double r = 0.0, dg = 0.0;
-        for (int j = lane; j < n; j += 32) {
-          const double v = S[(size_t)i * n + j];
-          if (j == i) dg = v; else r += fabs(v);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          r += __shfl_xor_sync(0xffffffffu, r, o);
-          dg += __shfl_xor_sync(0xffffffffu, dg, o);
-        }
-        glo = fmin(glo, dg - r);
-        ghi = fmax(ghi, dg + r);
-      }
-      if (lane == 0) {
-        sh.dred[0][warp - 4] = glo;
-        sh.dred[1][warp - 4] = ghi;
-      }
-      epi_bar();
-      double lo = INFINITY, hi = -INFINITY;
-      for (int w = 0; w < 8; ++w) {
-        lo = fmin(lo, sh.dred[0][w]);
-        hi = fmax(hi, sh.dred[1][w]);
-      }
-      const double c = lo > 0.0 ? 0.5 * (lo + hi) : hi;
+      // the trace of T_J(S) (every warp sums it alike, lanes along the diagonal)
+      double tr = 0.0;
+      for (int i = lane; i < n; i += 32) tr += S[(size_t)i * n + i];
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      const double c = tr / n;
       const float inv = (float)(1.0 / c);
       uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
       fill_pair(base, n, n64, [&](int i, int j) { return (float)S[(size_t)i * n + j] * inv; });
@@ -521,7 +506,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // reject a dimension or scale the planes cannot hold
         if (!(c > 0.0) || !isfinite(c)) st.status = kSubRefine;
       }
-      epi_bar();   // dred free again
     };
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
@@ -543,6 +527,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           start_inverse(s, J);
           break;
         }
+        if (g.cond && g.prep_status[J] == kSubOk && g.cond[J] > g.cond_max && g.sub_n[J] <= g.ill_max_n) continue;
         if (g.prep_status[J] != kSubOk) {
           if (tid == 128) {
             g.status[J] = g.prep_status[J];
@@ -736,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     start_slot(1);
     for (uint32_t i = 0;; ++i) {
       // every epilogue thread waits for the descriptor; a wait that ran out in any of them ends all
-      const bool got = tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * kWaitNs);
+      const bool got = tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * g.wait_ns);
       if (epi_bar_or(!got || sh.err)) {
         if (tid == 128) sh.err = 1;
         break;
@@ -754,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int cb = 0; cb < d.ncb; ++cb) {
           const int nt = min(256, n64 - 256 * cb);
           const int buf = tcount & 1;
-          if (!bad) bad = !tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + kWaitNs);
+          if (!bad) bad = !tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + g.wait_ns);
           bad = __any_sync(0xffffffffu, bad);   // tcgen05.ld needs the whole warp
           tc::tc_fence_after();
           const int row = 128 * mb + 32 * q + lane;
@@ -1095,7 +1080,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   }
   NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
   NOLSM_CUDA_TRY(cudaMemsetAsync(S->err.p, 0, sizeof(int32_t), st));
-  TcArgs g;
+  TcArgs g{};
   if (spec.list) {   // an explicit work list (reruns): in list order
     g.j0 = 0; g.j1 = spec.count;
     g.order = spec.list;
@@ -1126,6 +1111,10 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.iters = plan->iters.as<int32_t>(); g.status = plan->status.as<int32_t>();
   g.rsteps = plan->rsteps.as<int32_t>();
   g.nbelow = plan->nbelow.as<int32_t>();
+  g.wait_ns = o.wait_ns > 0 ? (uint64_t)o.wait_ns : kWaitNs;
+  g.cond = sym ? nullptr : prepared(plan, prep_class(o)).cond.as<float>();
+  g.cond_max = cond_max(o.precision);
+  g.ill_max_n = prepare_fp64_max_n();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   // one-byte views of the same planes (rows of 2 LD bytes) for E4M3 operands, both loaded K-major
   CUtensorMap mA8, mB8;
@@ -1206,6 +1195,7 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   g.ws = a.ws; g.a_base = a.a_base; g.chunk_n2 = a.chunk_n2;
   g.Aout = a.Aout; g.Xout = a.Xout; g.prep_out = a.prep_out;
   g.tol_inv = a.tol_inv; g.max_inv = a.max_inv;
+  g.wait_ns = kWaitNs;
   g.flops = S->inv_flops.as<double>();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   k_ns_tc<1><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
@@ -1326,7 +1316,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   }
   k_noalloc_reset<<<(count + 255) / 256, 256, 0, st>>>(base, count, status);
   NOLSM_LAUNCH_CHECK();
-  TcArgs g;
+  TcArgs g{};
   g.j0 = 0; g.j1 = count;
   g.order = ints;
   g.sub_n = sub_n; g.nbf = nbf; g.a_off = a_off; g.c_off = c_off;
@@ -1344,6 +1334,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.Dc = Dc; g.tS = t_S; g.tH = t_H; g.iters = iters; g.status = status;
   g.rsteps = ints + 2 * kNaMaxSub;
   g.nbelow = nullptr;
+  g.wait_ns = opts->wait_ns > 0 ? (uint64_t)opts->wait_ns : kWaitNs;
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
   NOLSM_LAUNCH_CHECK();

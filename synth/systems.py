@@ -61,6 +61,8 @@ class SystemSpec:
     hop: float = -0.2
     hop_len: float = 1.5
     occ_per_mol: int = 4        # occupied orbitals of a 6-function molecule
+    basis_mix: float = 0.0      # beta of the per-molecule basis transform B = I - beta v v^T (0: none)
+    basis_mix_every: int = 1    # transform molecules 0, k, 2k, ... (k = basis_mix_every)
     seed: int = 0
 
     @property
@@ -99,6 +101,7 @@ class System:
         return int(self.nbf.sum())
 
     occ: Optional[np.ndarray] = None   # int32 [n_mol], occupied orbitals per molecule
+    dirs: Optional[np.ndarray] = None  # float64 [2, 23, 3], direction vectors of the anisotropic modulation
 
     @property
     def n_occ(self) -> float:
@@ -277,7 +280,38 @@ def make_system(spec: SystemSpec) -> System:
                       lambda i, b: np.eye(b), n)
     H = _build_blocks(I[sel_h], J[sel_h], d[sel_h], nbf, onsite, dirs, h_val,
                       lambda i, b: np.diag(onsite[i]), n)
-    return System(spec=spec, pos=pos, cell=cell, nbf=nbf, onsite=onsite, S=S, H=H, occ=occ)
+    if spec.basis_mix != 0.0:
+        _mix_basis(S, nbf, spec)
+        _mix_basis(H, nbf, spec)
+    return System(spec=spec, pos=pos, cell=cell, nbf=nbf, onsite=onsite, S=S, H=H, occ=occ, dirs=dirs)
+
+
+def _mix_basis(M: BlockCSR, nbf: np.ndarray, spec: SystemSpec) -> None:
+    """Replaces the basis of every basis_mix_every-th molecule I by a linear combination of its functions,
+    B_I = I - beta v v^T with v = (1, 2, ..., b_I) / |(1, 2, ..., b_I)|, in place: block (I, J) becomes
+    B_I M_IJ B_J (B symmetric, identity for untouched molecules). The same congruence of S and H leaves the
+    generalized eigenvalues, hence the gap and mu, unchanged, while the overlap's condition number grows
+    like 1 / (1 - beta)^2: a non-orthogonal basis with nearly dependent functions."""
+    def B(I):
+        b = int(nbf[I])
+        if I % spec.basis_mix_every != 0:
+            return None
+        v = np.arange(1.0, b + 1.0)
+        v /= np.linalg.norm(v)
+        return np.eye(b) - spec.basis_mix * np.outer(v, v)
+    n = nbf.shape[0]
+    Bs = [B(I) for I in range(n)]
+    for I in range(n):
+        for p in range(int(M.row_ptr[I]), int(M.row_ptr[I + 1])):
+            J = int(M.col_idx[p])
+            if Bs[I] is None and Bs[J] is None:
+                continue
+            blk = M.vals[M.blk_off[p]:M.blk_off[p + 1]].reshape(int(nbf[I]), int(nbf[J]))
+            if Bs[I] is not None:
+                blk = Bs[I] @ blk
+            if Bs[J] is not None:
+                blk = blk @ Bs[J]
+            M.vals[M.blk_off[p]:M.blk_off[p + 1]] = blk.ravel()
 
 
 # ------------------------------------------------------------------------------------ named workloads

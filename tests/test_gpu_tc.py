@@ -3,7 +3,9 @@
 Tolerances come from the workload targets: the FP32 mode (three-term FP16 split, about 22 bits)
 max|dD| <= 1e-6; the BF16X3 and plain FP16 modes max|dD| <= 1e-4 with relative Tr(DH) error <= 1e-5. The plain BF16
 and FP8 modes cannot reach 1e-4 (a rounding error made in any step persists in the occupied-virtual
-block of the sign), so for them the measured error is checked against a loose bound and reported."""
+block of the sign, and their 8 and 4 significant bits leave too much of it: the CPU pin of
+tests/test_precision_readings.py): their measured errors are held to about twice the values measured on
+GB300 (regressions fail), and the 1e-4 target itself is a strict expected failure for them."""
 import numpy as np
 import pytest
 
@@ -75,7 +77,7 @@ def test_plain_bf16_is_reported_not_hidden(nl, small_ref):
     D = plan.scatter().cpu().numpy()
     err = d_error(None, ref, D)
     print(f"bf16 + 2 refinement steps: max|dD| = {err:.3e}")
-    assert 1e-6 < err < 5e-3
+    assert 1e-6 < err < 3e-4          # measured on GB300: 1.2e-4
     assert np.all(r.sub_status.cpu().numpy() == 0)
 
 
@@ -98,8 +100,8 @@ def test_fp8_mode_is_reported_not_hidden(nl, small_ref):
     rel = abs(r.trace_DH - ref.trace_DH) / abs(ref.trace_DH)
     print(f"fp8e4m3 + 3 refinement steps: max|dD| = {err:.3e}, rel Tr(DH) = {rel:.3e}, "
           f"steps {it.min()}..{it.max()}")
-    assert 1e-6 < err < 2e-2
-    assert rel < 1e-3
+    assert 1e-6 < err < 1e-2          # measured on GB300: 4.9e-3
+    assert rel < 5e-5                 # measured: 1.7e-5
     steps = np.array([ref.subs[J].steps for J in range(sysm.n_mol)])
     assert np.all(it <= steps + 3)
 
@@ -130,8 +132,28 @@ def test_fp8_mode_full_size_sampled(nl):
     print(f"full size fp8e4m3: sampled max|dD| = {err:.3e}, max rel t_H = {rel:.3e}, "
           f"mean steps {it.mean():.2f}")
     # measured on GB300: 2.9e-2 and 3.4e-3 (the E4M3 floor, amplified by the overlap's conditioning)
-    assert err < 1e-1
-    assert rel < 2e-2
+    assert err < 6e-2
+    assert rel < 7e-3
+
+
+@pytest.mark.xfail(strict=True, reason="out of reach by the analysis pinned in test_precision_readings.py: "
+                   "measured max|dD| 1.7e-4 (plain BF16) and 1.6e-2 (E4M3) on 96 sampled submatrices of the "
+                   "262,144-molecule workload")
+@pytest.mark.parametrize("prec", ["bf16", "fp8e4m3"])
+def test_the_1e4_target_is_out_of_reach_for(nl, prec):
+    """The workload's max|dD| <= 1e-4 target for the single-product 8-bit-mantissa modes, on 64 sampled
+    submatrices of the 4,096-molecule uneven system: expected to fail (strict)."""
+    from synth import spec_batched_uneven_4096
+    sysm = make_system(spec_batched_uneven_4096())
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    rng = np.random.default_rng(21)
+    subs = sorted(int(j) for j in rng.choice(sysm.n_mol, size=64, replace=False))
+    ref = orc.solve(sysm, -0.35, subs=subs, plan=po)
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    nl.nolsm_solve_batch(plan, -0.35, nl.options(prec))
+    err = d_error(po, ref, plan.scatter().cpu().numpy(), subs)
+    print(f"{prec}: sampled max|dD| = {err:.3e} against the 1e-4 target")
+    assert err <= 1e-4
 
 
 def test_fp8_needs_refinement_and_symmetric_form(nl, small_ref):
@@ -282,13 +304,41 @@ def test_split_valence_sampled(nl):
                   set(int(j) for j in rng.choice(sysm.n_mol, size=4, replace=False)))
     ref = orc.solve(sysm, m.mu, subs=subs, plan=po)
     n_max = int(po.sub_n.max())
-    for prec, tol in (("fp32", 1e-6 * np.sqrt(n_max / 300.0)), ("bf16x3", 1e-4), ("fp8e4m3", 1e-1)):
+    for prec, tol in (("fp32", 1e-6 * np.sqrt(n_max / 300.0)), ("bf16x3", 1e-4), ("fp8e4m3", 1e-2)):
         r = nl.nolsm_solve_batch(plan, m.mu, nl.options(prec))
         D = plan.scatter().cpu().numpy()
         err = d_error(po, ref, D, subs)
         it = r.iters.cpu().numpy()
         print(f"23 functions, n {po.sub_n.min()}..{n_max}, mu {m.mu:.4f}: {prec} sampled max|dD| = {err:.3e}, "
               f"steps {it.min()}..{it.max()}")
+        assert err <= tol
+        assert np.all(r.sub_status.cpu().numpy() == 0)
+
+
+def test_split_valence_n_above_900(nl):
+    """23 functions per molecule with a 6.8 A cutoff: n = 805..1058 (the 700-1000 span of the split-valence
+    workload and past it): up to nine row blocks, five column tiles, seventeen K slices. mu from the GPU
+    bisection; the smallest, the largest and two random submatrices against the oracle at that mu, in the
+    FP32, BF16X3 and FP16 modes and in BF16X3 with the tensor-core inverse square root."""
+    sysm = make_system(SystemSpec(8, 8, 8, nbf="23", cutoff=6.8, seed=1104))
+    plan = nl.nolsm_build_submatrices(nl.DeviceSystem(sysm))
+    po = orc.build_plan(sysm.nbf, sysm.S.row_ptr, sysm.S.col_idx, sysm.H.row_ptr, sysm.H.col_idx)
+    assert po.sub_n.max() >= 1000 and po.sub_n.min() >= 700
+    m = plan.find_mu(float(np.sum(sysm.occ)), 0.0, 0.0, nl.options("bf16x3"))
+    assert m.status == 0
+    rng = np.random.default_rng(12)
+    subs = sorted({int(np.argmin(po.sub_n)), int(np.argmax(po.sub_n))} |
+                  set(int(j) for j in rng.choice(sysm.n_mol, size=2, replace=False)))
+    ref = orc.solve(sysm, m.mu, subs=subs, plan=po)
+    n_max = int(po.sub_n.max())
+    for prec, inv, tol in (("fp32", 0, 1e-6 * np.sqrt(n_max / 300.0)), ("bf16x3", 0, 1e-4), ("fp16", 0, 1e-4),
+                           ("bf16x3", 1, 1e-4)):
+        r = nl.nolsm_solve_batch(plan, m.mu, nl.options(prec, inverse=inv))
+        D = plan.scatter().cpu().numpy()
+        err = d_error(po, ref, D, subs)
+        it = r.iters.cpu().numpy()
+        print(f"23 functions, n {po.sub_n.min()}..{n_max}, mu {m.mu:.4f}: {prec} (inverse {inv}) sampled "
+              f"max|dD| = {err:.3e}, steps {it.min()}..{it.max()}")
         assert err <= tol
         assert np.all(r.sub_status.cpu().numpy() == 0)
 
