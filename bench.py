@@ -388,8 +388,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3")
     ap.add_argument("--workload", default="streamed_bf16", choices=list(WORKLOADS))
-    ap.add_argument("--inverse", default="cholesky", choices=["cholesky", "ns"],
-                    help="preparation of A_J: FP32 Cholesky, or the tensor-core Newton-Schulz inverse square root")
+    ap.add_argument("--inverse", default="ns", choices=["cholesky", "ns"],
+                    help="preparation of A_J: the tensor-core Newton-Schulz inverse square root (Eqs. inv1-inv3), "
+                         "or the FP32 Cholesky factor")
     ap.add_argument("--batches", type=int, default=8, help="molecule batches the errors are reported for")
     ap.add_argument("--sample", type=int, default=640, help="oracle submatrices (errors and CPU baseline)")
     ap.add_argument("--ref-sample", type=int, default=96, help="submatrices per reference-arm step")
@@ -584,18 +585,35 @@ def main():
                                                 "steps, unpadded n",
                  "achieved_padded": tf(fl_padded, ms_sign),
                  "achieved_padded_note": "split products on the padded tiles the kernel executes"}
-    if not fp64_path and ms_factor > ms_sign:
+    roof_prep = None
+    ms_prep_kernel = 0.0
+    if not fp64_path and args.inverse == "ns":
+        ms_prep_kernel = mean("ms_prep_tensor")
+        fl_prep = mean("flops_prep_tensor")
+        roof_prep = {"bound": "tensor", "kernel": "k_ns_tc<1> (inverse square root of T_J(S), Eqs. inv1-inv3, "
+                                                  "and A_J)",
+                     "achieved": tf(fl_prep, ms_prep_kernel), "peak": peak, "unit": "TFLOP/s",
+                     "frac": tf(fl_prep, ms_prep_kernel) / peak if peak else None,
+                     "traffic": kernel_traffic("k_ns_tc_inv", (j1 - j0) / chunks), "launches_per_step": chunks,
+                     "peak_source": peaks["source"] + " bf16 sustained (FP16 operands run at the BF16 rate)",
+                     "algorithmic": "2 n^3 flops per product on the unpadded n, 3 k + 1 products per submatrix "
+                                    "(k coupled steps of 3 products, the last without its Y update, then "
+                                    "T_J(S)^-1 = Z^2 / c and A_J = T_J(S)^-1 T_J(H0))",
+                     "achieved_tensor_issued": tf(mean("flops_prep_tensor_issued"), ms_prep_kernel),
+                     "achieved_tensor_issued_note": "x3 for the three-term FP16 split"}
+    elif not fp64_path:
+        ms_prep_kernel = ms_factor
         ach_f = tf(fl_fp32, ms_factor)
-        roofline = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, double-FP32 "
-                                              "refinement of Q)",
-                    "achieved": ach_f, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
-                    "traffic": kernel_traffic("k_prepare_mixed", (j1 - j0) / chunks), "launches_per_step": chunks,
-                    "peak_source": "FP32 SIMT peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
-                    "algorithmic": "FP32 flops 2 (n^3/3 + n^3 + 3 n^2 b) per submatrix: Cholesky, the two "
-                                   "triangular solves for A, the Q solve, its residual and correction"}
-    else:
-        roofline = roof_sign
+        roof_prep = {"bound": "alu", "kernel": "k_prepare_mixed (FP32 factorisation and solves, double-FP32 "
+                                               "refinement of Q)",
+                     "achieved": ach_f, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach_f / FP32_ALU_PEAK_TFLOPS,
+                     "traffic": kernel_traffic("k_prepare_mixed", (j1 - j0) / chunks), "launches_per_step": chunks,
+                     "peak_source": "FP32 SIMT peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                     "algorithmic": "FP32 flops 2 (n^3/3 + n^3 + 3 n^2 b) per submatrix: Cholesky, the two "
+                                    "triangular solves for A, the Q solve, its residual and correction"}
+    # the headline roofline is the step's dominant kernel
+    roofline = roof_prep if (roof_prep is not None and ms_prep_kernel > ms_sign) else roof_sign
 
     extra = {"mu": mu_star, "trace_DS": r.trace_DS, "n_occ": n_occ, "bisection_points": evals,
              "ms_phases": {k: mean(k) for k in ("ms_plan", "ms_prepare", "ms_gather", "ms_factor", "ms_prep_tensor",
@@ -640,7 +658,8 @@ def main():
         plan = nl.nolsm_build_submatrices(dsys)
         fp64_range = (0, min(n_mol, 2 * 152 * 4))
         for prec in ["fp32", "bf16x3", "fp16", "bf16", "fp8e4m3", "fp64"]:
-            o = nl.options(prec)
+            # the FP32 mode's 1e-6 target is the Cholesky preparation's; the other modes use the bench's
+            o = nl.options(prec, inverse=nl._abi.INVERSE_CHOLESKY if prec == "fp32" else inverse)
             if prec == "fp64":
                 o.sub_begin, o.sub_end = fp64_range
             nl.nolsm_solve_batch(plan, mu_star, o, check=False)      # prepares the geometry caches
@@ -652,6 +671,7 @@ def main():
             s2 = plan.stats()
             cnt = (o.sub_end or n_mol) - o.sub_begin
             pth = {"submatrices_per_s_one_mu": cnt / dt, "ms_sign": s2["ms_sign"], "status": rr.status,
+                   "inverse": "cholesky" if o.inverse == nl._abi.INVERSE_CHOLESKY else "ns",
                    "sign_tflops_paper": tf(s2["flops_paper"], s2["ms_sign"]),
                    "tensor_tflops_issued": tf(s2["flops_tensor"], s2["ms_sign"]) if prec != "fp64" else None}
             if ref:
@@ -726,7 +746,7 @@ def main():
                                                                                            args.precision),
         "data": "synthetic",
         "config": {"workload": desc if world == 1 else f"{desc}; lattice {world}x longer along x, one slab per GPU",
-                   "precision": args.precision, "molecules": n_mol, "molecules_per_gpu": n_mol // world,
+                   "precision": args.precision, "inverse": args.inverse, "molecules": n_mol, "molecules_per_gpu": n_mol // world,
                    "l2": "inputs larger than L2 (block-CSR S and H, %.0f MB each)" % (sysm.S.vals.nbytes / 1e6),
                    "bracket": "Gershgorin interval of all submatrices",
                    "batches": f"{nb} contiguous molecule ranges, errors reported per range"},
@@ -740,6 +760,7 @@ def main():
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "roofline_sign": roof_sign,
+        "roofline_prep": roof_prep,
         "cpu_baseline": {"value": cpu_subs_per_s, "unit": "submatrices/s", "cores": workers, "kind": "oracle",
                          "sample": f"{len(sample)} submatrices ({per} per batch) gathered and solved once at the "
                                    f"final mu, divided by the {evals} bisection points of a step"},

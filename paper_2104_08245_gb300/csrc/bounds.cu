@@ -666,15 +666,16 @@ nolsm_status power_bounds(nolsm_plan* plan, int cls, int64_t j0, int64_t j1, con
 nolsm_status features(nolsm_plan* plan, double mu, int64_t j0, int64_t j1, cudaStream_t st) {
   const size_t n = (size_t)plan->n_mol;
   NOLSM_TRY(ensure_buf(plan, plan->feat, sizeof(float) * kFeatures * n));
-  if (!plan->onsite_done) {
-    NOLSM_TRY(ensure_buf(plan, plan->onsite, sizeof(double) * 2 * n));
+  if (!plan->onsite_done) {   // per molecule of the input system (a grouped plan has fewer submatrices)
+    const int32_t nm = plan->sys.n_mol;
+    NOLSM_TRY(ensure_buf(plan, plan->onsite, sizeof(double) * 2 * (size_t)nm));
     if (plan->gen)
-      k_onsite_model<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(plan->n_mol, plan->onsite_off.as<int64_t>(),
-                                                                  plan->model.onsite, plan->onsite.as<double>());
+      k_onsite_model<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, plan->onsite_off.as<int64_t>(),
+                                                                   plan->model.onsite, plan->onsite.as<double>());
     else
-      k_onsite<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(plan->n_mol, plan->sys.nbf, plan->sys.h_row_ptr,
-                                                            plan->sys.h_col_idx, plan->h_blk_off.as<int64_t>(),
-                                                            plan->sys.h_vals, plan->onsite.as<double>());
+      k_onsite<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, plan->sys.nbf, plan->sys.h_row_ptr,
+                                                             plan->sys.h_col_idx, plan->h_blk_off.as<int64_t>(),
+                                                             plan->sys.h_vals, plan->onsite.as<double>());
     NOLSM_LAUNCH_CHECK();
     plan->stats.launches += 1;
     plan->onsite_done = true;

@@ -208,7 +208,7 @@ nolsm_status energy_weighted(nolsm_plan* plan, cudaStream_t st, double* W_vals, 
   EwArgs g;
   g.j0 = (int32_t)j0;
   g.sub_n = plan->sub_n.as<int32_t>();
-  g.nbf = plan->sys.nbf;
+  g.nbf = plan->sub_b.as<int32_t>();   // centre columns per submatrix
   g.a_off = plan->a_off.as<int64_t>();
   g.c_off = plan->c_off.as<int64_t>();
   g.Dc = plan->Dc.as<double>();

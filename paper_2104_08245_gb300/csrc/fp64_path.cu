@@ -40,7 +40,8 @@ __device__ __forceinline__ int find_sorted(const int32_t* __restrict__ a, int lo
 // Also writes the centre columns of T_J(S) and T_J(H0) into the geometry caches.
 struct GatherArgs {
   int32_t n_mol;
-  const int32_t* nbf;
+  const int32_t* nbf;   // per molecule
+  const int32_t* sub_b; // centre columns per submatrix
   const int32_t* srp; const int32_t* sci; const int64_t* soff; const double* sval;
   const int32_t* hrp; const int32_t* hci; const int64_t* hoff; const double* hval;
   const int32_t* nb_ptr; const int32_t* nb_idx; const int32_t* nb_off;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
   }
   __syncwarp();
   const int c0 = g.sub_c0[J];
-  const int bJ = g.nbf[J];
+  const int bJ = g.sub_b[J];
   double* TS = g.ws + (g.a_off[J] - g.a_base);
   double* TH = TS + g.chunk_n2;
   double* Sc = g.Sc + g.c_off[J];
@@ -468,6 +469,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     GatherArgs g{};
     g.n_mol = n_mol;
     g.nbf = plan->sys.nbf;
+    g.sub_b = plan->sub_b.as<int32_t>();
     g.srp = plan->sys.s_row_ptr; g.sci = plan->sys.s_col_idx; g.soff = plan->s_blk_off.as<int64_t>();
     g.sval = plan->sys.s_vals;
     g.hrp = plan->sys.h_row_ptr; g.hci = plan->sys.h_col_idx; g.hoff = plan->h_blk_off.as<int64_t>();
@@ -507,7 +509,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       NOLSM_CUDA_TRY(cudaMemsetAsync(pa.cond + J, 0x7F, sizeof(float) * (size_t)(e - J), st));
     }
     pa.j0 = (int32_t)J;
-    pa.sub_n = plan->sub_n.as<int32_t>(); pa.sub_c0 = plan->sub_c0.as<int32_t>(); pa.nbf = plan->sys.nbf;
+    pa.sub_n = plan->sub_n.as<int32_t>(); pa.sub_c0 = plan->sub_c0.as<int32_t>(); pa.nbf = plan->sub_b.as<int32_t>();
     pa.a_off = plan->a_off.as<int64_t>(); pa.c_off = plan->c_off.as<int64_t>();
     pa.a_base = g.a_base; pa.chunk_n2 = n2; pa.ws = g.ws;
     pa.Q = plan->Q.as<double>(); pa.lam = plan->lam.as<double>(); pa.prep_status = plan->prep_status.as<int32_t>();
@@ -588,7 +590,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
     pmark(plan, st);
     plan->stats.factor_launches += 1;
     for (int64_t k = J; k < e; ++k) {
-      const double m = plan->h_sub_n[k], b = plan->h_nbf[k];
+      const double m = plan->h_sub_n[k], b = plan->h_sub_b[k];
       // algorithmic flops (2 per FMA): Cholesky m^3/3 FMAs; two triangular solves with m right-hand sides
       // m^3 FMAs (A = L^-T L^-1 H, or M = L^-1 (L^-1 H)^T); the Q solves m^2 b FMAs each (FP64 path: one;
       // mixed: the first solve and one correction, plus m^2 b / 2 for W_c in the symmetric form); the
@@ -645,7 +647,7 @@ nolsm_status solve_fp64(nolsm_plan* plan, double mu, const nolsm_options& o, int
   NOLSM_CUDA_TRY(cudaMemsetAsync(plan->counter.p, 0, sizeof(int32_t), st));
   NsArgs g;
   g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
-  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sub_b.as<int32_t>();
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
   g.A = plan->prep64.A.as<double>(); g.Q = plan->Q.as<double>(); g.Sc = plan->Sc.as<double>();
   g.Hc = plan->Hc.as<double>(); g.lam = spec.lam ? spec.lam : plan->lam.as<double>();

@@ -244,7 +244,7 @@ nolsm_status nolsm_plan_set_elements(nolsm_plan* plan, const nolsm_element_model
     set_error("nolsm_plan_set_elements: NULL array or invalid model parameter");
     return NOLSM_ERR_ARG;
   }
-  const int32_t n = plan->n_mol;
+  const int32_t n = plan->sys.n_mol;   // molecules of the input system
   std::vector<int64_t> off((size_t)n + 1, 0);
   for (int32_t I = 0; I < n; ++I) off[(size_t)I + 1] = off[(size_t)I] + plan->h_nbf[(size_t)I];
   if (!plan->onsite_off.p) NOLSM_TRY(dev_alloc(plan, plan->onsite_off, sizeof(int64_t) * off.size()));

@@ -75,6 +75,8 @@ struct nolsm_plan {
   nolsm::DevBuf s_blk_off, h_blk_off;       // int64 [nnzb+1]
   nolsm::DevBuf nb_ptr, nb_idx, nb_off;     // int32
   nolsm::DevBuf sub_n, sub_c0;              // int32 [n_mol]
+  nolsm::DevBuf sub_b;                      // int32 [n_mol]: centre columns of each submatrix (b_J; a group's
+                                            // members' functions in a grouped plan)
   nolsm::DevBuf d_blk_off;                  // int64 [d_nnzb+1]
   nolsm::DevBuf d_slot;                     // int32 [d_nnzb]: slot of block (nb_idx[p], J) in D
   nolsm::DevBuf a_off, c_off;               // int64 [n_mol+1]: offsets of n^2 and n*b arrays
@@ -86,7 +88,8 @@ struct nolsm_plan {
   nolsm::DevBuf onsite_off;                 // int64 [n_mol+1]: offsets of each molecule's on-site energies
 
   // host copies
-  std::vector<int32_t> h_sub_n, h_nbf, h_nb_ptr;
+  std::vector<int32_t> h_sub_n, h_nbf, h_nb_ptr;   // h_nbf: per molecule of the input system
+  std::vector<int32_t> h_sub_b;                    // per submatrix
   std::vector<int64_t> h_a_off, h_c_off;
 
   // geometry caches shared by all precisions (device), n_J x b_J row-major at c_off[J]

@@ -369,6 +369,8 @@ nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st) {
   plan->h_c_off.resize(n + 1);
   NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->h_sub_n.data(), plan->sub_n.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
   NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->h_nbf.data(), s.nbf, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  NOLSM_TRY(dev_alloc(plan, plan->sub_b, sizeof(int32_t) * (size_t)n));   // one submatrix per molecule: b_J
+  NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->sub_b.p, s.nbf, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
   NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->h_nb_ptr.data(), plan->nb_ptr.p, sizeof(int32_t) * (n + 1),
                                  cudaMemcpyDeviceToHost, st));
   NOLSM_CUDA_TRY(cudaMemcpyAsync(plan->h_a_off.data(), plan->a_off.p, sizeof(int64_t) * (n + 1),
@@ -395,6 +397,7 @@ nolsm_status build_plan_device(nolsm_plan* plan, cudaStream_t st) {
     plan->max_n = std::max(plan->max_n, m);
     plan->min_n = std::min(plan->min_n, m);
     plan->max_b = std::max(plan->max_b, plan->h_nbf[J]);
+    plan->h_sub_b.push_back(plan->h_nbf[J]);
     plan->sum_n3 += (double)m * m * m;
   }
   return NOLSM_OK;

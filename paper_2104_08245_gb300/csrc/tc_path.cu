@@ -1088,7 +1088,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     g.j0 = (int32_t)j0; g.j1 = (int32_t)j1;
     g.order = S->order.as<int32_t>();
   }
-  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sub_b.as<int32_t>();
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
   // the symmetric form iterates on M and its centre-column phase uses W_c = L^-1 E_c in place of Q
   const bool sym = prep_class(o) == kPrepSym;
@@ -1133,7 +1133,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     SymArgs a;
     a.j0 = (int32_t)j0;
     a.list = spec.list;
-    a.sub_n = plan->sub_n.as<int32_t>(); a.nbf = plan->sys.nbf;
+    a.sub_n = plan->sub_n.as<int32_t>(); a.nbf = plan->sub_b.as<int32_t>();
     a.a_off = plan->a_off.as<int64_t>(); a.c_off = plan->c_off.as<int64_t>();
     a.prep_status = plan->prep_status.as<int32_t>();
     a.L = plan->Lsym.as<float>();
@@ -1185,7 +1185,7 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   TcArgs g{};
   g.j0 = 0; g.j1 = a.count;
   g.order = a.order;
-  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sys.nbf;
+  g.sub_n = plan->sub_n.as<int32_t>(); g.nbf = plan->sub_b.as<int32_t>();
   g.a_off = plan->a_off.as<int64_t>(); g.c_off = plan->c_off.as<int64_t>();
   g.main_fmt = Fmt{FMT_F16, 3}; g.refine_fmt = g.main_fmt;
   g.planes = S->inv_planes.as<uint16_t>();

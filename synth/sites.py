@@ -98,3 +98,39 @@ def spec_ions_in_water(**kw) -> SiteSpec:
 def spec_ions_in_water_small(**kw) -> SiteSpec:
     """216 lattice sites (6x6x6), 3 % ions: about 630 atom sites (fast enough for the plain oracle)."""
     return SiteSpec(6, 6, 6, **{"ion_fraction": 0.03, "seed": 1302, **kw})
+
+
+# on-site energies (Ha) of the site species' functions: O (4), H (2), ion (4)
+ONSITE_SITE = {0: np.array([-1.0, -0.5, -0.5, -0.5]), 1: np.array([-0.4, 0.3]), 2: np.array([-1.2, 0.2, 0.2, 0.2])}
+
+
+def site_system(sp: SitePattern, s_exp: float = 0.5, hop: float = -0.2, hop_len: float = 1.5):
+    """S and H0 on an atom-resolved pattern: the blocks of the pattern's pairs filled by the element model of
+    systems.py (S = exp(-s_exp r^2) / sqrt(b_a b_b), H0 = hop exp(-r / hop_len) / sqrt(b_a b_b) between
+    different sites, S = identity and H0 = diag(on-site energies of the species) on a site), so that S is
+    positive definite for every geometry as in the molecule systems. Returns a systems.System whose
+    "molecules" are the sites (spec carries the model's parameters; functions of other species than the
+    molecule systems' have other on-site energies, ONSITE_SITE)."""
+    from .systems import System, SystemSpec, _build_blocks, _min_image
+    n = sp.n_sites
+    J = np.repeat(np.arange(n), np.diff(sp.nb_ptr))          # column molecule of every (row, column) pair
+    I = sp.nb_idx.astype(np.int64)
+    key = np.lexsort((J, I))                                 # rows I ascending, then columns
+    I, J = I[key], J[key].astype(np.int64)
+    d = _min_image(sp.pos[J] - sp.pos[I], sp.cell)
+    onsite = [ONSITE_SITE[int(s)] for s in sp.species]
+    spec = SystemSpec(sp.spec.nx, sp.spec.ny, sp.spec.nz, s_exp=s_exp, hop=hop, hop_len=hop_len, seed=sp.spec.seed)
+
+    def s_val(r, dhat, b1, b2, dirs):
+        base = (1.0 / np.sqrt(b1 * b2)) * np.exp(-s_exp * r * r)[:, None, None]
+        return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
+
+    def h_val(r, dhat, b1, b2, dirs):
+        base = (1.0 / np.sqrt(b1 * b2)) * (hop * np.exp(-r / hop_len))[:, None, None]
+        return np.broadcast_to(base, (r.shape[0], b1, b2)).copy()
+
+    S = _build_blocks(I, J, d, sp.nbf, onsite, None, s_val, lambda i, b: np.eye(b), n)
+    H = _build_blocks(I, J, d, sp.nbf, onsite, None, h_val, lambda i, b: np.diag(onsite[i]), n)
+    occ = np.choose(sp.species, [2, 1, 2]).astype(np.int32)    # O 2, H 1, ion 2 occupied orbitals
+    return System(spec=spec, pos=sp.pos, cell=sp.cell, nbf=sp.nbf.astype(np.int32), onsite=onsite, S=S, H=H,
+                  occ=occ)
