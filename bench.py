@@ -421,6 +421,8 @@ def main():
     n_mol = sysm.n_mol
     n_occ = sysm.n_occ
     workers = max(1, os.cpu_count() or 1)
+    if world > 1:   # the side measurements and the oracle's accuracy check are single-GPU legs
+        args.no_extra = args.no_oracle = True
     # the oracle's worker pool (spawned) and plan, before the first GPU call
     ora = OracleSample(sysm, workers) if (rank == 0 and not args.no_oracle) else None
 
@@ -434,6 +436,19 @@ def main():
     inverse = nl._abi.INVERSE_NEWTON_SCHULZ if args.inverse == "ns" else nl._abi.INVERSE_CHOLESKY
     opts = nl.options(args.precision, inverse=inverse)
 
+    # shard molecules over ranks (independent submatrices; one scalar all-reduce per bisection point); with
+    # several ranks each holds only its halo: the block rows of its molecules' neighbourhoods
+    j0 = (n_mol * rank) // world
+    j1 = (n_mol * (rank + 1)) // world
+    full = sysm
+    if world > 1:
+        from paper_2104_08245_gb300.sharded import extract_halo
+        halo = extract_halo(sysm, j0, j1)
+        sysm = halo.system
+        opts.sub_begin, opts.sub_end = halo.l0, halo.l1
+    else:
+        opts.sub_begin, opts.sub_end = j0, j1
+
     # host copies (pinned) for the e2e leg; device copies for the resident leg
     host = {"nbf": torch.from_numpy(sysm.nbf).pin_memory(),
             "s_row_ptr": torch.from_numpy(sysm.S.row_ptr).pin_memory(),
@@ -443,12 +458,9 @@ def main():
             "h_col_idx": torch.from_numpy(sysm.H.col_idx).pin_memory(),
             "h_vals": torch.from_numpy(sysm.H.vals).pin_memory()}
     dsys = nl.DeviceSystem(sysm, dev)
+    n_local = dsys.n_mol      # molecules this rank holds (its halo with several ranks)
     stream = torch.cuda.current_stream(dev)
 
-    # shard molecules over ranks (independent submatrices; one scalar all-reduce per bisection point)
-    j0 = (n_mol * rank) // world
-    j1 = (n_mol * (rank + 1)) // world
-    opts.sub_begin, opts.sub_end = j0, j1
 
     def find_mu(plan):
         if world == 1:
@@ -504,7 +516,7 @@ def main():
         e = _Sys()
         for k, t in host.items():
             setattr(e, k, t.to(dev, non_blocking=True))
-        e.n_mol, e.n_occ = n_mol, n_occ
+        e.n_mol, e.n_occ = n_local, n_occ
         e.struct = lambda: nl.DeviceSystem.struct(e)
         plan = nl.nolsm_build_submatrices(e)
         r_ = find_mu(plan)
@@ -536,7 +548,7 @@ def main():
         for k in ("nbf", "s_row_ptr", "s_col_idx", "h_row_ptr", "h_col_idx"):
             setattr(e, k, dv[k])
         e.s_vals = e.h_vals = None
-        e.n_mol, e.n_occ = n_mol, n_occ
+        e.n_mol, e.n_occ = n_local, n_occ
         e.struct = lambda: nl.DeviceSystem.struct(e)
         m = nl.ElementModel.__new__(nl.ElementModel)
         m.pos, m.onsite, m.dirs, m.cell, m.params = dv["pos"], dv["onsite"], mdl.dirs, mdl.cell, mdl.params
@@ -730,6 +742,44 @@ def main():
                        "sum_n3_reduction": cr.sum_n3_before / cr.sum_n3_after,
                        "sum_n2_reduction": cr.sum_n2_before / cr.sum_n2_after,
                        "host_s": dt_c, "host_threads": os.cpu_count()}
+        # the merged submatrices solved on the device: a step (plan, one solve at the per-site mu*, write-back)
+        # with one submatrix per site against one per group
+        ssys = synth.site_system(sp)
+        dss = nl.DeviceSystem(ssys, dev)
+        o_s = nl.options(args.precision, inverse=inverse)
+        mp = nl.nolsm_build_submatrices(dss)
+        mu_s = mp.find_mu(float(np.sum(ssys.occ)), 0.0, 0.0, o_s).mu
+        Ds = torch.zeros(mp.info().d_nvals, dtype=torch.float64, device=dev)
+        mp.close()
+
+        def site_step(grouped):
+            p_ = nl.nolsm_build_submatrices(dss)
+            q_ = nl.nolsm_build_grouped(p_, cr.group_of) if grouped else p_
+            r_ = nl.nolsm_solve_batch(q_, mu_s, o_s, check=False)
+            q_.scatter(Ds)
+            st_ = q_.stats()
+            if grouped:
+                q_.close()
+            p_.close()
+            return r_, st_
+
+        timing = {}
+        for grouped in (False, True):
+            site_step(grouped)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(3):
+                r_s, st_s = site_step(grouped)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            timing["grouped" if grouped else "per_site"] = {
+                "ms_step": ev0.elapsed_time(ev1) / 3, "ms_prepare": st_s["ms_prepare"], "ms_sign": st_s["ms_sign"],
+                "status": r_s.status, "trace_DS": r_s.trace_DS}
+        combination["device_solve"] = {
+            **timing, "mu": mu_s, "precision": args.precision,
+            "step_time_ratio": timing["per_site"]["ms_step"] / timing["grouped"]["ms_step"],
+            "note": "step = plan (plus the grouped plan's host construction), preparation and one solve at the "
+                    "per-site plan's mu*, and the write-back into the per-site pattern of D"}
 
     bounds = {}
     if not args.no_extra and not fp64_path and ora is not None:

@@ -163,6 +163,9 @@ typedef struct {
   int32_t min_n;       /* smallest n_J */
   double sum_n3;       /* sum over J of n_J^3 (work metric) */
   int64_t device_bytes;/* device memory currently held by the plan */
+  int64_t nb_entries;  /* entries of nb_idx / nb_off (nolsm_plan_get_maps): d_nnzb, or for a grouped plan the
+                          total length of its groups' row lists */
+  int32_t grouped;     /* 1 for a plan from nolsm_build_grouped (n_mol then counts its groups) */
 } nolsm_plan_info;
 
 /* a0: submatrix construction plan (Sec. "The Non-Orthogonal Local Submatrix Method", merged pattern;
@@ -205,9 +208,10 @@ typedef struct {
 nolsm_status nolsm_plan_set_elements(nolsm_plan* plan, const nolsm_element_model* model);
 
 /* Copies the plan's integer maps into caller device buffers (any pointer may be NULL):
- * nb_ptr [n_mol+1], nb_idx [d_nnzb], nb_off [d_nnzb], sub_n [n_mol], sub_c0 [n_mol],
+ * nb_ptr [n_mol+1], nb_idx [nb_entries], nb_off [nb_entries], sub_n [n_mol], sub_c0 [n_mol],
  * d_blk_off [d_nnzb+1] (int64 element offsets of the D blocks). The merged pattern of D is
- * block row I = nb_idx[nb_ptr[I] .. nb_ptr[I+1]). */
+ * block row I = nb_idx[nb_ptr[I] .. nb_ptr[I+1]) of a per-molecule plan. For a grouped plan the first five
+ * describe its groups (rows of T_G in order, members first) and d_blk_off the per-molecule pattern of D. */
 nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_t* nb_idx, int32_t* nb_off,
                                  int32_t* sub_n, int32_t* sub_c0, int64_t* d_blk_off, nolsm_stream_t stream);
 
@@ -227,6 +231,21 @@ nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_
  * handed over. Synchronises the stream. */
 nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
                                      double* Q, int32_t* prep_status, float* cond_est);
+
+/* Merged submatrices on the device (Sec. "Submatrix Combination Heuristics"): a new plan whose submatrices
+ * are groups of molecules, e.g. the groups of nolsm_combine_submatrices. group_of (host, [n_mol] of the
+ * per-molecule plan mp): a label per molecule, molecules with equal labels forming one group (any labels in
+ * 0 .. n_mol-1; groups are numbered in the order of their smallest member). The submatrix of group G has the
+ * rows of N(G), the union of its members' N(J): the members first (ascending), then the other molecules
+ * (ascending); its centre columns are the members' functions (sub_c0 = 0, width the sum of their b_J).
+ * Everything that works on submatrices then works on the groups (nolsm_solve_batch, nolsm_find_mu with its
+ * options' range counting groups, bound sources, nolsm_energy_weighted); nolsm_scatter_density writes member
+ * J's columns of T_G(D) on the rows of its own N(J), so that D keeps mp's pattern (d_blk_off, d_nvals). The
+ * new plan shares mp's input arrays (and its element model, if set) and owns its own maps; mp may be
+ * destroyed afterwards. Host work O(sum over groups of |N(G)| log |N(G)|); synchronises the stream.
+ * NOLSM_ERR_ARG for a label outside 0 .. n_mol-1 or a grouped mp; NOLSM_ERR_UNSUPPORTED when a group has more
+ * than 64 centre columns (the preparation's column tiles; split such a group). */
+nolsm_status nolsm_build_grouped(const nolsm_plan* mp, const int32_t* group_of, nolsm_stream_t stream, nolsm_plan** out);
 
 /* a1-a7: every submatrix J in [sub_begin, sub_end) at chemical potential mu:
  *   T_J(S), T_J(H0) gathered (a1); T_J(S) = L L^T in FP64 (a2); A_J = T_J(S)^-1 T_J(H0) (a3);

@@ -128,18 +128,22 @@ class GroupedResult:
     D_vals: np.ndarray     # D in the merged pattern (block (I, J) for I in N(J), as the per-molecule solve)
 
 
-def solve_grouped(system, mu: float, group_of, plan, tol: float = 1e-9) -> GroupedResult:
+def solve_grouped(system, mu: float, group_of, plan, tol: float = 1e-9, only=None) -> GroupedResult:
     """The density matrix from merged submatrices (Sec. "Submatrix Combination Heuristics": the columns of
     all molecules of a group share one submatrix T_G over the union of their rows):
     T_G(D) = 1/2 (I - sign(T_G(S)^-1 T_G(H0) - mu I)) T_G(S)^-1 (Eq. purification_submatrix), and the
     columns of each member J are written back on the rows of N(J), so that D keeps the merged pattern of S
-    and H0 (reading: the paper notes that merging could keep a denser D; this keeps the output format)."""
+    and H0 (reading: the paper notes that merging could keep a denser D; this keeps the output format).
+    only: solve just the groups with these labels (their members' columns and traces; no written-back D)."""
     from .nolsm_oracle import submatrix_density, write_back_cols
     nbf = plan.nbf
     group_of = np.asarray(group_of)
     cols, tS = {}, {}
     total = 0.0
-    for g in sorted(set(int(x) for x in group_of)):
+    labels = sorted(set(int(x) for x in group_of))
+    if only is not None:
+        labels = [g for g in labels if g in set(int(x) for x in only)]
+    for g in labels:
         members = [int(J) for J in np.nonzero(group_of == g)[0]]
         rows = sorted(set(int(m) for J in members for m in plan.nb_idx[plan.nb_ptr[J]:plan.nb_ptr[J + 1]]))
         offs = dict(zip(rows, np.concatenate([[0], np.cumsum([int(nbf[m]) for m in rows])])[:-1].tolist()))
@@ -157,4 +161,4 @@ def solve_grouped(system, mu: float, group_of, plan, tol: float = 1e-9) -> Group
                     t += r.D_sub[i, j] * S[i, j]
             tS[J] = t
             total += t
-    return GroupedResult(cols, tS, total, write_back_cols(plan, cols))
+    return GroupedResult(cols, tS, total, write_back_cols(plan, cols) if only is None else None)

@@ -18,7 +18,7 @@ from ._abi import (BF16, BF16X3, BOUND_GERSHGORIN, BOUND_MLP, BOUND_POWER, FP8E4
 __all__ = ["DeviceSystem", "nolsm_build_submatrices", "nolsm_solve_batch", "nolsm_scatter_density",
            "nolsm_energy_weighted", "nolsm_combine_submatrices",
            "nolsm_find_mu", "nolsm_plan_query", "nolsm_plan_get_maps", "nolsm_plan_stats", "nolsm_plan_stats_reset",
-           "nolsm_spectral_bracket", "nolsm_plan_get_prepared", "nolsm_plan_set_elements", "ElementModel",
+           "nolsm_spectral_bracket", "nolsm_plan_get_prepared", "nolsm_plan_set_elements", "ElementModel", "nolsm_build_grouped",
            "nolsm_features", "nolsm_power_bounds", "nolsm_training_data",
            "nolsm_plan_set_mlp", "Mlp", "MLP_PARAMS",
            "options", "NolsmError", "Plan", "SolveResult", "MuResult"]
@@ -138,6 +138,20 @@ def nolsm_plan_set_elements(plan: "Plan", model: ElementModel) -> None:
     plan.model = model   # keeps the device arrays alive while the plan may use them
 
 
+def nolsm_build_grouped(plan: "Plan", group_of, stream=None) -> "Plan":
+    """A plan whose submatrices are the groups of molecules given by group_of (one label per molecule, e.g.
+    nolsm_combine_submatrices(...).group_of)."""
+    import numpy as np
+    g = np.ascontiguousarray(np.asarray(group_of.cpu() if hasattr(group_of, "cpu") else group_of), dtype=np.int32)
+    out = ctypes.c_void_p()
+    rc = _abi.load().nolsm_build_grouped(plan.handle, g.ctypes.data, _stream(stream), ctypes.byref(out))
+    if rc != 0:
+        raise NolsmError(rc, "nolsm_build_grouped")
+    gp = Plan(out, plan.dsys)
+    gp.model = getattr(plan, "model", None)
+    return gp
+
+
 def nolsm_plan_query(plan: "Plan") -> NolsmPlanInfo:
     info = NolsmPlanInfo()
     rc = _abi.load().nolsm_plan_query(plan.handle, ctypes.byref(info))
@@ -149,11 +163,11 @@ def nolsm_plan_query(plan: "Plan") -> NolsmPlanInfo:
 def nolsm_plan_get_maps(plan: "Plan", stream=None) -> dict:
     torch = _torch()
     info = nolsm_plan_query(plan)
-    n, m = info.n_mol, info.d_nnzb
+    n, m, q = info.n_mol, info.d_nnzb, info.nb_entries
     dev = plan.dsys.nbf.device
     out = {"nb_ptr": torch.empty(n + 1, dtype=torch.int32, device=dev),
-           "nb_idx": torch.empty(m, dtype=torch.int32, device=dev),
-           "nb_off": torch.empty(m, dtype=torch.int32, device=dev),
+           "nb_idx": torch.empty(q, dtype=torch.int32, device=dev),
+           "nb_off": torch.empty(q, dtype=torch.int32, device=dev),
            "sub_n": torch.empty(n, dtype=torch.int32, device=dev),
            "sub_c0": torch.empty(n, dtype=torch.int32, device=dev),
            "d_blk_off": torch.empty(m + 1, dtype=torch.int64, device=dev)}

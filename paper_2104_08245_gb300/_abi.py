@@ -49,7 +49,8 @@ class NolsmElementModel(ctypes.Structure):
 
 class NolsmPlanInfo(ctypes.Structure):
     _fields_ = [("n_mol", c_int32), ("d_nnzb", c_int64), ("d_nvals", c_int64), ("max_n", c_int32),
-                ("min_n", c_int32), ("sum_n3", c_double), ("device_bytes", c_int64)]
+                ("min_n", c_int32), ("sum_n3", c_double), ("device_bytes", c_int64), ("nb_entries", c_int64),
+                ("grouped", c_int32)]
 
 
 class NolsmStats(ctypes.Structure):
@@ -71,6 +72,7 @@ SIGNATURES = [
     ("nolsm_build_submatrices", c_int32, [ctypes.POINTER(NolsmSystem), c_void_p, ctypes.POINTER(c_void_p)]),
     ("nolsm_plan_query", c_int32, [c_void_p, ctypes.POINTER(NolsmPlanInfo)]),
     ("nolsm_plan_set_elements", c_int32, [c_void_p, ctypes.POINTER(NolsmElementModel)]),
+    ("nolsm_build_grouped", c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]),
     ("nolsm_plan_get_maps", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
     ("nolsm_solve_batch", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p,

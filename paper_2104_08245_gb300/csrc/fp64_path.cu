@@ -689,6 +689,7 @@ nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_m
 }
 
 nolsm_status scatter(nolsm_plan* plan, double* D, int64_t j0, int64_t j1, cudaStream_t st, const double* src) {
+  if (plan->grouped) return scatter_grouped(plan, D, j0, j1, st, src);
   const int64_t p0 = plan->h_nb_ptr[j0], p1 = plan->h_nb_ptr[j1];
   if (p1 <= p0) return NOLSM_OK;
   const int64_t threads = (p1 - p0) * 32;

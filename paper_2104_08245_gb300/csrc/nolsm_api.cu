@@ -148,7 +148,8 @@ nolsm_plan::~nolsm_plan() {
                    &a_off, &c_off, &flag, &Q, &Sc, &Hc, &lam, &prep_status, &prep64.A, &prep32.A, &prep_sym.A, &prep_ns.A, &Lsym, &Wc, &Dc,
                    &t_S, &t_H, &iters, &status, &rsteps, &nbelow, &nb_lo, &nb_hi, &active, &sums, &counter, &ws_dense, &ws_l32, &ws_refine, &prep_order, &ws_ns,
                    &lam_p, &onsite, &feat, &mlp_y, &lam_m, &budget, &rerun, &ws_ysym, &Wd, &tW,
-                   &prep32.cond, &prep_ns.cond, &ill_list, &onsite_off};
+                   &prep32.cond, &prep_ns.cond, &ill_list, &onsite_off,
+                   &sub_b, &m_nb_ptr, &m_nb_idx, &g_of, &g_col, &g_row};
   for (DevBuf* b : all) dev_free(this, *b);
   tc_release(this);
   if (ev_ok)
@@ -234,6 +235,8 @@ nolsm_status nolsm_plan_query(const nolsm_plan* plan, nolsm_plan_info* info) {
   info->min_n = plan->min_n;
   info->sum_n3 = plan->sum_n3;
   info->device_bytes = plan->bytes;
+  info->nb_entries = plan->h_nb_ptr.empty() ? 0 : plan->h_nb_ptr.back();
+  info->grouped = plan->grouped ? 1 : 0;
   return NOLSM_OK;
 }
 
@@ -263,10 +266,10 @@ nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_
                                  int32_t* sub_n, int32_t* sub_c0, int64_t* d_blk_off, nolsm_stream_t stream) {
   if (!plan) { set_error("nolsm_plan_get_maps: NULL plan"); return NOLSM_ERR_ARG; }
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t n = (size_t)plan->n_mol, m = (size_t)plan->d_nnzb;
+  const size_t n = (size_t)plan->n_mol, m = (size_t)plan->d_nnzb, q = (size_t)plan->h_nb_ptr[n];
   if (nb_ptr) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_ptr, plan->nb_ptr.p, 4 * (n + 1), cudaMemcpyDeviceToDevice, st));
-  if (nb_idx) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_idx, plan->nb_idx.p, 4 * m, cudaMemcpyDeviceToDevice, st));
-  if (nb_off) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_off, plan->nb_off.p, 4 * m, cudaMemcpyDeviceToDevice, st));
+  if (nb_idx) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_idx, plan->nb_idx.p, 4 * q, cudaMemcpyDeviceToDevice, st));
+  if (nb_off) NOLSM_CUDA_TRY(cudaMemcpyAsync(nb_off, plan->nb_off.p, 4 * q, cudaMemcpyDeviceToDevice, st));
   if (sub_n) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_n, plan->sub_n.p, 4 * n, cudaMemcpyDeviceToDevice, st));
   if (sub_c0) NOLSM_CUDA_TRY(cudaMemcpyAsync(sub_c0, plan->sub_c0.p, 4 * n, cudaMemcpyDeviceToDevice, st));
   if (d_blk_off) NOLSM_CUDA_TRY(cudaMemcpyAsync(d_blk_off, plan->d_blk_off.p, 8 * (m + 1), cudaMemcpyDeviceToDevice, st));

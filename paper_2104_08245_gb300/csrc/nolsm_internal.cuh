@@ -82,6 +82,13 @@ struct nolsm_plan {
   nolsm::DevBuf a_off, c_off;               // int64 [n_mol+1]: offsets of n^2 and n*b arrays
   nolsm::DevBuf flag;                       // int32 scratch flag
 
+  // grouped plans (nolsm_build_grouped): the submatrices are groups of molecules; n_mol counts the groups,
+  // sys.n_mol the molecules; D keeps the per-molecule pattern (d_slot, d_blk_off, d_nnzb of that plan)
+  bool grouped = false;
+  nolsm::DevBuf m_nb_ptr, m_nb_idx;         // int32: the per-molecule plan's N(J)
+  nolsm::DevBuf g_of, g_col;                // int32 [molecules]: group of J, offset of J's columns in it
+  nolsm::DevBuf g_row;                      // int32 [molecule pairs]: offset of the rows of I in T_G, G of J
+
   // elements generated on the device from the geometry (nolsm_plan_set_elements) instead of read
   bool gen = false;
   nolsm_element_model model{};
@@ -217,6 +224,9 @@ nolsm_status reduce_traces(nolsm_plan* plan, int64_t j0, int64_t j1, int terms_m
 // write-back of centre columns (default: those of T_J(D)) into the merged pattern
 nolsm_status scatter(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st,
                      const double* src = nullptr);
+// the same for a grouped plan: each member's columns of T_G(D) on the rows of its own N(J) (grouped.cu)
+nolsm_status scatter_grouped(nolsm_plan* plan, double* D_vals, int64_t j0, int64_t j1, cudaStream_t st,
+                             const double* src);
 // centre columns of the energy-weighted T_J(W) at the plan's solution (energy_weighted.cu)
 nolsm_status energy_weighted(nolsm_plan* plan, cudaStream_t st, double* W_vals, double* trace_WS);
 

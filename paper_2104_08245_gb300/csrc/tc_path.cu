@@ -135,6 +135,7 @@ struct SlotState {
   float dprev;                   // defect of the previous step (E4M3 stagnation test)
   Fmt fcur, fnxt;
   int yc, zc;                    // inverse mode: plane pairs of the current Y and Z
+  int zdone;                     // inverse mode: this step's Z update was made at the start (step 0)
   float cinv;                    // inverse mode: 1 / c
 };
 
@@ -478,8 +479,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
 
-    // inverse mode, a new submatrix J in slot s: c = Tr T_J(S) / n, Y_0 = T_J(S) / c, Z_0 = I (zero on the
-    // padding), T_J(H0) into pair 5
+    // inverse mode, a new submatrix J in slot s: c = Tr T_J(S) / n and step 0 without products, since Z_0 = I:
+    // V_0 = Y_0 = T_J(S) / c, T_0 = 3I - Y_0 and Z_1 = T_0 / 2 are written directly (pairs 0, 2, 1), with the
+    // defect ||I - Y_0||_F / sqrt(n); only Y_1 = Y_0 T_0 / 2 needs the tensor cores. T_J(H0) into pair 5.
     auto start_inverse = [&](int s, int J) {
       SlotState& st = sh.slot[s];
       const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
@@ -492,20 +494,38 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double c = tr / n;
       const float inv = (float)(1.0 / c);
       uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
-      fill_pair(base, n, n64, [&](int i, int j) { return (float)S[(size_t)i * n + j] * inv; });
-      fill_pair(base + 2 * plane_elems, n, n64, [&](int i, int j) { return i == j ? 1.0f : 0.0f; });
+      float dpart = 0.0f;   // this thread's share of ||I - Y_0||_F^2
+      fill_pair(base, n, n64, [&](int i, int j) {
+        const float y = (float)S[(size_t)i * n + j] * inv;
+        const float e = (i == j ? 1.0f : 0.0f) - y;
+        dpart += e * e;
+        return y;
+      });
+      fill_pair(base + 4 * plane_elems, n, n64,
+                [&](int i, int j) { return (i == j ? 3.0f : 0.0f) - (float)S[(size_t)i * n + j] * inv; });
+      fill_pair(base + 2 * plane_elems, n, n64,
+                [&](int i, int j) { return 0.5f * ((i == j ? 3.0f : 0.0f) - (float)S[(size_t)i * n + j] * inv); });
       fill_pair(base + 10 * plane_elems, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
+      for (int o = 16; o > 0; o >>= 1) dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
+      if (lane == 0) sh.dred[0][warp - 4] = dpart;
+      epi_bar();
       if (tid == 128) {
+        float dsum = 0.0f;
+        for (int w = 0; w < 8; ++w) dsum += (float)sh.dred[0][w];
+        const float d0 = sqrtf(dsum / (float)n);
         st.job = J;
         st.n = n; st.n64 = n64; st.R = R;
         st.nrb = R / 128; st.ncb = (n64 + 255) / 256; st.nks = n64 / 64;
-        st.kind = 0; st.yc = 0; st.zc = 1; st.cinv = inv;
-        st.steps = 0; st.rsteps = 0; st.status = kSubOk; st.last = 0;
+        st.yc = 0; st.zc = 1; st.cinv = inv;
+        st.steps = 1; st.rsteps = 0; st.status = kSubOk;
         st.fcur = Fmt{FMT_F16, 3}; st.fnxt = st.fcur;
         st.dprev = INFINITY;
-        // reject a dimension or scale the planes cannot hold
-        if (!(c > 0.0) || !isfinite(c)) st.status = kSubRefine;
+        if (!(c > 0.0) || !isfinite(c) || !isfinite(d0)) st.status = kSubRefine;   // the FP64 preparation takes it
+        st.last = d0 <= g.tol_inv ? 1 : 0;
+        st.kind = st.last ? 3 : 1;     // step 0 the last: X = Z_1 Z_1 / c next; else Y_1 = Y_0 T_0 / 2
+        st.zdone = 1;
       }
+      epi_bar();   // dred free again
     };
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
@@ -855,7 +875,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             st.kind = st.last ? 2 : 1;
             break;
           }
-          case 1: st.yc = st.yc == 0 ? 3 : 0; st.kind = 2; break;
+          case 1:   // after Y's update: Z's, unless the step's Z update was made at the start
+            st.yc = st.yc == 0 ? 3 : 0;
+            st.kind = st.zdone ? 0 : 2;
+            st.zdone = 0;
+            break;
           case 2: st.zc = st.zc == 1 ? 4 : 1; st.kind = st.last ? 3 : 0; break;
           case 3: st.kind = 4; break;
           default: break;
@@ -923,7 +947,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const SlotState& sf = sh.slot[d.slot];
             g.prep_out[sf.job] = sf.status;
             const double n3 = (double)sf.n * sf.n * sf.n;
-            const double prods = 3.0 * sf.steps + 1.0;   // the last step skips its Y update; X and A follow
+            // step 0 needs one product (Y_1), every further step three but the last two (no Y update); then X, A
+            const double prods = 3.0 * sf.steps - 1.0;
             atomicAdd(&g.flops[0], 2.0 * n3 * prods);
             atomicAdd(&g.flops[1], 6.0 * n3 * prods);
           }

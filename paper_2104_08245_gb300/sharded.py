@@ -74,3 +74,64 @@ def sharded_find_mu(plan, n_occ: float, opts, group=None) -> ShardedMu:
         nl.nolsm_bisect_side(plan, opts, raises_lo)
 
     return bisect_allreduce(count, (lo, hi), n_occ, opts, group, side)
+
+
+@dataclasses.dataclass
+class Halo:
+    """The part of the input one rank needs for its molecules [j0, j1): the molecules of the union of their
+    neighbourhoods N(J) (the halo, ascending global ids), the block rows of S and H0 of those molecules
+    restricted to columns in the halo, renumbered 0 .. len(mols)-1; the rank's molecules are the local range
+    [l0, l1)."""
+    mols: "object"           # int32 [m]: global id of every local molecule
+    l0: int
+    l1: int
+    system: "object"         # a synth-like object with nbf, S, H (BlockCSR-like), n_occ, occ, and the
+                             # geometry of the halo's molecules (pos, onsite, cell, spec, dirs) when known
+
+
+def extract_halo(system, j0: int, j1: int) -> Halo:
+    """Host-side extraction of a rank's halo (once per geometry): N(J) is the merged pattern of S and H0 in
+    block column J (the submatrix's rows, Sec. "The Non-Orthogonal Local Submatrix Method"); every submatrix
+    of the rank needs the blocks (I, K) with I, K in N(J), which are among the halo's rows and columns. The
+    pattern stays structurally symmetric (it is the full one restricted to the halo on both sides), so the
+    plan built from it reproduces N(J), T_J(S) and T_J(H0) of every owned J exactly."""
+    import numpy as np
+
+    n = int(system.nbf.shape[0])
+    # N(J) of the owned molecules from the symmetric patterns: block column J = block row J
+    mols = np.unique(np.concatenate([system.S.col_idx[system.S.row_ptr[j0]:system.S.row_ptr[j1]],
+                                     system.H.col_idx[system.H.row_ptr[j0]:system.H.row_ptr[j1]]])).astype(np.int32)
+    loc = np.full(n, -1, dtype=np.int64)
+    loc[mols] = np.arange(mols.shape[0])
+
+    def ranges(starts, counts):
+        """Concatenation of [starts[k], starts[k] + counts[k]) over k."""
+        tot = int(np.sum(counts))
+        if tot == 0:
+            return np.zeros(0, dtype=np.int64)
+        base = np.repeat(starts - np.concatenate([[0], np.cumsum(counts)[:-1]]), counts)
+        return base + np.arange(tot, dtype=np.int64)
+
+    def restrict(M):
+        rp = M.row_ptr.astype(np.int64)
+        ps = ranges(rp[mols], rp[mols + 1] - rp[mols])                  # the halo's block rows
+        keep = ps[loc[M.col_idx[ps]] >= 0]                               # restricted to halo columns
+        row_of = np.repeat(np.arange(mols.shape[0]), (rp[mols + 1] - rp[mols]))[loc[M.col_idx[ps]] >= 0]
+        row_ptr = np.zeros(mols.shape[0] + 1, dtype=np.int64)
+        np.cumsum(np.bincount(row_of, minlength=mols.shape[0]), out=row_ptr[1:])
+        sizes = M.blk_off[keep + 1] - M.blk_off[keep]
+        blk = np.zeros(keep.shape[0] + 1, dtype=np.int64)
+        np.cumsum(sizes, out=blk[1:])
+        vals = M.vals[ranges(M.blk_off[keep], sizes)]
+        return type(M)(row_ptr.astype(np.int32), loc[M.col_idx[keep]].astype(np.int32), blk, vals)
+
+    S, H = restrict(system.S), restrict(system.H)
+    get = lambda k: getattr(system, k, None)
+    sub = dataclasses.make_dataclass("HaloSystem", ["nbf", "S", "H", "occ", "n_occ", "pos", "onsite", "cell", "spec",
+                                                    "dirs"])(
+        system.nbf[mols].astype(np.int32), S, H, system.occ[mols] if get("occ") is not None else None,
+        float(np.sum(system.occ[j0:j1])) if get("occ") is not None else 0.0,
+        system.pos[mols] if get("pos") is not None else None,
+        [system.onsite[int(g)] for g in mols] if get("onsite") is not None else None,
+        get("cell"), get("spec"), get("dirs"))
+    return Halo(mols, int(loc[j0]), int(loc[j1 - 1]) + 1, sub)
