@@ -608,9 +608,10 @@ def main():
                      "frac": tf(fl_prep, ms_prep_kernel) / peak if peak else None,
                      "traffic": kernel_traffic("k_ns_tc_inv", (j1 - j0) / chunks), "launches_per_step": chunks,
                      "peak_source": peaks["source"] + " bf16 sustained (FP16 operands run at the BF16 rate)",
-                     "algorithmic": "2 n^3 flops per product on the unpadded n, 3 k + 1 products per submatrix "
-                                    "(k coupled steps of 3 products, the last without its Y update, then "
-                                    "T_J(S)^-1 = Z^2 / c and A_J = T_J(S)^-1 T_J(H0))",
+                     "algorithmic": "2 n^3 flops per product on the unpadded n, 3 k - 1 products per submatrix "
+                                    "(k coupled steps: step 0 one product since Z_0 = I, the middle ones "
+                                    "three, the last two as it needs no Y update; then T_J(S)^-1 = Z^2 / c "
+                                    "and A_J = T_J(S)^-1 T_J(H0))",
                      "achieved_tensor_issued": tf(mean("flops_prep_tensor_issued"), ms_prep_kernel),
                      "achieved_tensor_issued_note": "x3 for the three-term FP16 split"}
     elif not fp64_path:

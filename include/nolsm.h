@@ -228,7 +228,8 @@ nolsm_status nolsm_plan_get_maps(const nolsm_plan* plan, int32_t* nb_ptr, int32_
  * 10 (NOLSM_FP32) or 30 (the other tensor-core modes) to the FP64 path before its own solve, and after it
  * every submatrix that failed the low-precision accept test or turned non-finite; nolsm_stats.ill_conditioned
  * counts them. Only submatrices of at most 775 rows (the FP64 factorisation's shared-memory panel) are
- * handed over. Synchronises the stream. */
+ * handed over; larger ones above the limit stay in the requested mode and nolsm_stats.ill_conditioned_kept
+ * counts them. Synchronises the stream. */
 nolsm_status nolsm_plan_get_prepared(nolsm_plan* plan, const nolsm_options* opts, nolsm_stream_t stream, void* A,
                                      double* Q, int32_t* prep_status, float* cond_est);
 
@@ -398,6 +399,9 @@ typedef struct {
   double flops_prep_tensor_issued; /* the same x3 (three-term split products) */
   int64_t ill_conditioned;     /* submatrices of tensor-core solves that were solved on the FP64 path: overlap
                                   too ill-conditioned for the mode, or the low-precision solve failed */
+  int64_t ill_conditioned_kept; /* submatrices whose overlap is too ill-conditioned for the mode but larger
+                                  than the FP64 path takes (n > 775): solved in the requested mode, whose
+                                  accuracy target then does not hold for them */
 } nolsm_stats;
 
 nolsm_status nolsm_plan_stats(const nolsm_plan* plan, nolsm_stats* stats);

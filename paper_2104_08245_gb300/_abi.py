@@ -60,7 +60,8 @@ class NolsmStats(ctypes.Structure):
                 ("flops_fp64", c_double), ("launches", c_int64), ("reruns", c_int64), ("ms_gather", c_double),
                 ("ms_factor", c_double), ("flops_fp32", c_double), ("factor_launches", c_int64),
                 ("ms_energy_weighted", c_double), ("ms_prep_tensor", c_double), ("flops_prep_tensor", c_double),
-                ("flops_prep_tensor_issued", c_double), ("ill_conditioned", c_int64)]
+                ("flops_prep_tensor_issued", c_double), ("ill_conditioned", c_int64),
+                ("ill_conditioned_kept", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

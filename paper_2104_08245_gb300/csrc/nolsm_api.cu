@@ -350,7 +350,11 @@ static nolsm_status ill_conditioned_list(nolsm_plan* plan, const nolsm_options& 
   const float lim = cond_max(o.precision);
   const int max_n = prepare_fp64_max_n();   // larger submatrices stay on the tensor path
   auto take = [&](int32_t J) {
-    if (P.h_cond[(size_t)J] > lim && plan->h_sub_n[(size_t)J] <= max_n) out->push_back(J);
+    if (P.h_cond[(size_t)J] <= lim) return;
+    if (plan->h_sub_n[(size_t)J] <= max_n)
+      out->push_back(J);
+    else
+      plan->stats.ill_conditioned_kept += 1;
   };
   if (list) {
     std::vector<int32_t> cand((size_t)count);

@@ -1132,7 +1132,6 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
   const int n = g.sub_n[J], bJ = g.nbf[J], c0 = g.sub_c0[J], nbc = n * bJ;
   const double* S = g.ws + (g.a_off[J] - g.a_base);
   const float* X = g.L32 + (g.a_off[J] - g.a_base);
-  float* w = g.W32 + (g.c_off[J] - g.c_base);
   float2* qp = g.Qp + (g.c_off[J] - g.c_base);
   double* q = g.Q + g.c_off[J];
   for (int e = tid; e < nbc; e += kThreads) {
@@ -1152,26 +1151,86 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
   }
   __syncthreads();
   bool conv = false;
+  constexpr int kWarps = kThreads / 32;
   for (int it = 0; it < kRefineMax && !conv; ++it) {
     for (int e = tid; e < nbc; e += kThreads) qp[e] = split_f64(q[e]);
     __syncthreads();
-    residual_df(S, n, c0, bJ, qp, w);
+    // R = E_c - T_J(S) q, one warp per row, lanes along it (coalesced), 8 columns of q per sweep, in
+    // double-FP32 arithmetic (as residual_df); the lanes' (hi, lo) sums are combined with TwoSum
+    for (int i = warp; i < n; i += kWarps) {
+      const double* Si = S + (size_t)i * n;
+      for (int cg = 0; cg < bJ; cg += 8) {
+        const int cn = min(8, bJ - cg);
+        float sh[8], sl[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) sh[c] = sl[c] = 0.0f;
+        for (int k = lane; k < n; k += 32) {
+          const float2 a = split_f64(Si[k]);
+          const float2* qk = qp + (size_t)k * bJ + cg;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c < cn) {
+              const float2 v = qk[c];
+              const float pr = a.x * v.x;
+              sl[c] += fmaf(a.x, v.x, -pr);
+              two_sum(sh[c], sl[c], pr);
+              sl[c] = fmaf(a.x, v.y, fmaf(a.y, v.x, sl[c]));
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
+            two_sum(sh[c], sl[c], oh);
+            sl[c] += ol;
+          }
+        }
+        if (lane < cn) {
+          float hv = sh[0], lv = sl[0];
+#pragma unroll
+          for (int c = 1; c < 8; ++c)
+            if (lane == c) { hv = sh[c]; lv = sl[c]; }
+          Wsh[i * bJ + cg + lane] = ((i == c0 + cg + lane ? 1.0f : 0.0f) - hv) - lv;
+        }
+      }
+    }
     __syncthreads();
-    for (int e = tid; e < nbc; e += kThreads) Wsh[e] = w[e];
-    __syncthreads();
+    // q <- q + X R, one warp per row of X (coalesced), R from shared memory
     float dmax = 0.0f;
     double qmax = 0.0;
     bool finite = true;
-    for (int e = tid; e < nbc; e += kThreads) {
-      const int i = e / bJ, c = e - i * bJ;
+    for (int i = warp; i < n; i += kWarps) {
       const float* xi = X + (size_t)i * n;
-      float d = 0.0f;
-      for (int k = 0; k < n; ++k) d = fmaf(xi[k], Wsh[k * bJ + c], d);
-      const double qe = q[e] + (double)d;
-      q[e] = qe;
-      finite = finite && isfinite(d) && isfinite(qe);
-      dmax = fmaxf(dmax, fabsf(d));
-      qmax = fmax(qmax, fabs(qe));
+      for (int cg = 0; cg < bJ; cg += 8) {
+        const int cn = min(8, bJ - cg);
+        float acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+        for (int k = lane; k < n; k += 32) {
+          const float x = xi[k];
+          const float* rk = Wsh + k * bJ + cg;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < cn) acc[c] = fmaf(x, rk[c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if (lane < cn) {
+          float d = acc[0];
+#pragma unroll
+          for (int c = 1; c < 8; ++c)
+            if (lane == c) d = acc[c];
+          const size_t e = (size_t)i * bJ + cg + lane;
+          const double qe = q[e] + (double)d;
+          q[e] = qe;
+          finite = finite && isfinite(d) && isfinite(qe);
+          dmax = fmaxf(dmax, fabsf(d));
+          qmax = fmax(qmax, fabs(qe));
+        }
+      }
     }
     if (!finite) dmax = INFINITY;
     for (int o = 16; o > 0; o >>= 1) {
@@ -1185,7 +1244,7 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
     __syncthreads();
     float dm = 0.0f;
     double qm = 0.0;
-    for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+    for (int w2 = 0; w2 < kWarps; ++w2) {
       dm = fmaxf(dm, red_d[w2]);
       qm = fmax(qm, red_q[w2]);
     }

@@ -495,16 +495,41 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float inv = (float)(1.0 / c);
       uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
       float dpart = 0.0f;   // this thread's share of ||I - Y_0||_F^2
-      fill_pair(base, n, n64, [&](int i, int j) {
-        const float y = (float)S[(size_t)i * n + j] * inv;
-        const float e = (i == j ? 1.0f : 0.0f) - y;
-        dpart += e * e;
-        return y;
-      });
-      fill_pair(base + 4 * plane_elems, n, n64,
-                [&](int i, int j) { return (i == j ? 3.0f : 0.0f) - (float)S[(size_t)i * n + j] * inv; });
-      fill_pair(base + 2 * plane_elems, n, n64,
-                [&](int i, int j) { return 0.5f * ((i == j ? 3.0f : 0.0f) - (float)S[(size_t)i * n + j] * inv); });
+      // Y_0, T_0 and Z_1 from one read of T_J(S): the same pass pattern as fill_pair, three pairs out
+      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+        for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+            if (i >= n64) break;
+            float y[8], t[8], z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int j = j0 + u;
+              const bool in = i < n && j < n;
+              y[u] = in ? (float)S[(size_t)i * n + j] * inv : 0.0f;
+              const float e = (i == j && in ? 1.0f : 0.0f) - y[u];
+              dpart += e * e;
+              t[u] = in ? (i == j ? 3.0f : 0.0f) - y[u] : 0.0f;
+              z[u] = 0.5f * t[u];
+            }
+            uint32_t h[4], l[4];
+            const size_t off = (size_t)i * g.LD + j0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split2(y[2 * u], y[2 * u + 1], FMT_F16, h[u], l[u]);
+            *reinterpret_cast<uint4*>(base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(base + plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split2(t[2 * u], t[2 * u + 1], FMT_F16, h[u], l[u]);
+            *reinterpret_cast<uint4*>(base + 4 * plane_elems + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(base + 5 * plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split2(z[2 * u], z[2 * u + 1], FMT_F16, h[u], l[u]);
+            *reinterpret_cast<uint4*>(base + 2 * plane_elems + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(base + 3 * plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
+          }
+        }
+      }
       fill_pair(base + 10 * plane_elems, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
       for (int o = 16; o > 0; o >>= 1) dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
       if (lane == 0) sh.dred[0][warp - 4] = dpart;

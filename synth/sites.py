@@ -131,6 +131,8 @@ def site_system(sp: SitePattern, s_exp: float = 0.5, hop: float = -0.2, hop_len:
 
     S = _build_blocks(I, J, d, sp.nbf, onsite, None, s_val, lambda i, b: np.eye(b), n)
     H = _build_blocks(I, J, d, sp.nbf, onsite, None, h_val, lambda i, b: np.diag(onsite[i]), n)
-    occ = np.choose(sp.species, [2, 1, 2]).astype(np.int32)    # O 2, H 1, ion 2 occupied orbitals
+    # occupied orbitals: every O function, the lower H and ion functions (a gap of 0.45 Ha on the 632-site
+    # system between -0.29 and +0.16 Ha; two per O would put the Fermi level inside O's threefold level)
+    occ = np.choose(sp.species, [4, 1, 1]).astype(np.int32)
     return System(spec=spec, pos=sp.pos, cell=sp.cell, nbf=sp.nbf.astype(np.int32), onsite=onsite, S=S, H=H,
                   occ=occ)
