@@ -252,12 +252,19 @@ __device__ __forceinline__ bool epi_bar_or(bool p) {
   return r != 0;
 }
 
+// Whether row tile mb of a product is an M = 64 tile: the last one of a kind::f16 product whose n64 is an odd
+// multiple of 64 (n = 129..192 runs as 128 + 64 rows instead of 2 x 128). Its accumulator rows r sit in TMEM
+// lanes 32 (r / 16) + r % 16, the first 16 lanes of each warp's quarter.
+__device__ __forceinline__ bool tail64(const Desc& d, int mb) {
+  return d.f.fmt != FMT_E4M3 && d.fo.fmt != FMT_E4M3 && mb == d.nrb - 1 && (d.n64 & 127) == 64;
+}
+
 // kMode 0: the sign iteration (a4-a7); kMode 1: the inverse square root of T_J(S) and A_J (a2-a3)
 template <int kMode>
 __global__ void __launch_bounds__(kThreads, 1)
     k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
             const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapA8,
-            const __grid_constant__ CUtensorMap mapB8, TcArgs g) {
+            const __grid_constant__ CUtensorMap mapB8, const __grid_constant__ CUtensorMap mapS16, TcArgs g) {
   constexpr int kPps = kMode == 0 ? kPlanes : kPlanesInv;   // planes per slot
   extern __shared__ uint8_t smraw[];
   uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -283,6 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::prefetch_tmap(&mapS);
     tc::prefetch_tmap(&mapA8);
     tc::prefetch_tmap(&mapB8);
+    tc::prefetch_tmap(&mapS16);
   }
   if (warp == 0) {
     tc::tmem_alloc(&sh.tmem, 512);
@@ -363,9 +371,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
           const int nt = min(256, d.n64 - 256 * cb);
+          // an M = 64 tile loads 64 rows of A (the B map's 64 x 64 box)
+          const bool m64 = tail64(d, mb);
+          const uint32_t abytes = m64 ? kABytes / 2 : kABytes;
           // E4M3: both operands K-major (the symmetric iterate is its own transpose); the B box is always
           // 256 rows (rows past R are zero-filled by the copy)
-          const uint32_t bytes = f8 ? kABytes + 256u * 128u : (uint32_t)two * (kABytes + (uint32_t)nt * 128u);
+          const uint32_t bytes = f8 ? kABytes + 256u * 128u : (uint32_t)two * (abytes + (uint32_t)nt * 128u);
           for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc::tma_load_3d(sm + 2 * kABytes, &mapB8, &sh.full[st], 128 * ks, 256 * cb, d.zb);
             } else {
               for (int z = 0; z < two; ++z) {
-                tc::tma_load_3d(sm + z * kABytes, &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
+                tc::tma_load_3d(sm + z * kABytes, m64 ? &mapB : &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
                 uint8_t* bdst = sm + 2 * kABytes + z * kBBytes;
                 for (int c = 0; c < nt / 64; ++c)
                   tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], 256 * cb + 64 * c, 64 * ks, d.zb + z);
@@ -402,11 +413,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (d.term) break;
       const bool f8 = d.f.fmt == FMT_E4M3;
       const int nks = f8 ? k8_extent(d.n64) / 128 : d.nks;
+      // kind::f16 products run over n16 = n rounded up to 16 in N and K (the loads stay whole 64-wide slices):
+      // the operands' rows and columns past n are zero, so the entries the trimmed product leaves out are 0
+      const int n16 = (d.n + 15) & ~15;
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
           const int nt = min(256, d.n64 - 256 * cb);
+          const int ntu = min(nt, n16 - 256 * cb);
           // kind::f16: A K-major, B MN-major; kind::f8f6f4 (E4M3 = 0): both K-major
-          const uint32_t id = f8 ? tc::idesc(0, 0, 0, 0, 128, nt) : tc::idesc(d.f.fmt, d.f.fmt, 0, 1, 128, nt);
+          const uint32_t id = f8 ? tc::idesc(0, 0, 0, 0, 128, nt)
+                                 : tc::idesc(d.f.fmt, d.f.fmt, 0, 1, tail64(d, mb) ? 64 : 128, ntu);
           const int buf = tcount & 1;
           if (!tc::mbar_wait(&sh.acce[buf], ((tcount >> 1) & 1) ^ 1, tc::globaltimer() + g.wait_ns)) {
             sh.err = 1;
@@ -430,8 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               ++kcount;
               continue;
             }
+            const int kku = min(4, (n16 - 64 * ks) / 16);   // K = 16 steps below n16 (at least one)
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
+              if (kk >= kku) break;
               const uint64_t ah = tc::sdesc_sw128(a0 + kk * 32, 16, 1024);
               const uint64_t bh = tc::sdesc_sw128(b0 + kk * 2048, 8192, 1024);
               tc::mma_f16(dt, ah, bh, id, (ks > 0 || kk > 0) ? 1u : 0u);
@@ -787,8 +805,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!bad) bad = !tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + g.wait_ns);
           bad = __any_sync(0xffffffffu, bad);   // tcgen05.ld needs the whole warp
           tc::tc_fence_after();
-          const int row = 128 * mb + 32 * q + lane;
-          const bool live = 128 * mb + 32 * q < n64 && !bad;   // rows >= n64 are never read back
+          // an M = 64 tile: 16 rows per warp quarter, in its lanes 0-15
+          const bool m64 = tail64(d, mb);
+          const int rbase = 128 * mb + (m64 ? 16 : 32) * q;
+          const int row = rbase + lane;
+          const bool rok = !m64 || lane < 16;
+          const bool live = rbase < n64 && !bad;   // rows >= n64 are never read back
           const int nch = nt / 32;
           const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
           uint32_t r[32];
@@ -799,22 +821,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             float v[32];
             if (live) {
               tc::tmem_wait_ld();
+              // entries past n are written as zeros: the trimmed products leave the accumulator's columns
+              // past n16 as they were, and the next products' K and N never reach past n16
               if (epi == kEpiT) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   const int col = col0 + j;
+                  const bool in = rok && row < n && col < n;
                   const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - P)_ij
-                  if (row < n && col < n) part += e * e;
-                  v[j] = e + (row == col ? 2.0f : 0.0f);                              // (3I - P)_ij
+                  if (in) part += e * e;
+                  v[j] = in ? e + (row == col ? 2.0f : 0.0f) : 0.0f;                 // (3I - P)_ij
                 }
               } else {
                 const float m = escale * sc;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = m * __uint_as_float(r[j]);
+                for (int j = 0; j < 32; ++j) v[j] = (rok && row < n && col0 + j < n) ? m * __uint_as_float(r[j]) : 0.0f;
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
-            if (kMode == 1 && live && epi >= kEpiX && row < n) {
+            if (kMode == 1 && live && rok && epi >= kEpiX && row < n) {
               // inverse mode: X or A_J in FP32, row-major n x n
               const int J = sh.slot[d.slot].job;
               float* dst = (epi == kEpiX ? g.Xout + (g.a_off[J] - g.a_base) : g.Aout + g.a_off[J]) + (size_t)row * n;
@@ -863,9 +888,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               tc::fence_proxy_async_smem();
               __syncwarp();
-              if (lane == 0) {
-                tc::tma_store_3d(&mapS, wb, col0, 128 * mb + 32 * q, d.zo);
-                if (d.fo.terms > 1) tc::tma_store_3d(&mapS, wb + 2048, col0, 128 * mb + 32 * q, d.zo + 1);
+              if (lane == 0) {   // an M = 64 tile stores the first 16 rows of the staging (16-row box)
+                const CUtensorMap* ms = m64 ? &mapS16 : &mapS;
+                tc::tma_store_3d(ms, wb, col0, rbase, d.zo);
+                if (d.fo.terms > 1) tc::tma_store_3d(ms, wb + 2048, col0, rbase, d.zo + 1);
                 tc::bulk_commit();
               }
             }
@@ -1120,8 +1146,10 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     S->ord_j0 = j0;
     S->ord_j1 = j1;
   }
-  CUtensorMap mA, mB, mS;
-  if (!tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
+  CUtensorMap mA, mB, mS, mS16;
+  if (!tmap::make_3d(&mS16, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 16,
+                     CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64) ||
       !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 32,
                      CU_TENSOR_MAP_SWIZZLE_64B)) {
@@ -1176,7 +1204,7 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   k_status_pending<<<(unsigned)std::min<int64_t>(1024, (work + 255) / 256), 256, 0, st>>>(
       (int32_t)j0, (int32_t)work, spec.list, plan->status.as<int32_t>());
   NOLSM_LAUNCH_CHECK();
-  k_ns_tc<0><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, g);
+  k_ns_tc<0><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, mS16, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 2;
   if (sym) {   // D_c = L^-T U and the traces
@@ -1218,8 +1246,10 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   if (!S->err.p) NOLSM_TRY(dev_alloc(plan, S->err, sizeof(int32_t) * 4));
   if (!S->inv_flops.p) NOLSM_TRY(dev_alloc(plan, S->inv_flops, sizeof(double) * 2));
   const uint64_t depth = (uint64_t)S->islots * kPlanesInv;
-  CUtensorMap mA, mB, mS;
-  if (!tmap::make_3d(&mA, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 128) ||
+  CUtensorMap mA, mB, mS, mS16;
+  if (!tmap::make_3d(&mS16, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 16,
+                     CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mA, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 128) ||
       !tmap::make_3d(&mB, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 64) ||
       !tmap::make_3d(&mS, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 32,
                      CU_TENSOR_MAP_SWIZZLE_64B)) {
@@ -1248,7 +1278,7 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   g.wait_ns = kWaitNs;
   g.flops = S->inv_flops.as<double>();
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<1><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
+  k_ns_tc<1><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, g);
   NOLSM_LAUNCH_CHECK();
   double fl[2];
   NOLSM_CUDA_TRY(cudaMemcpyAsync(fl, S->inv_flops.p, sizeof(fl), cudaMemcpyDeviceToHost, st));
@@ -1357,8 +1387,9 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   unsigned char* base = static_cast<unsigned char*>(addr);
   int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
 
-  CUtensorMap mA, mB, mS;
-  if (!tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
+  CUtensorMap mA, mB, mS, mS16;
+  if (!tmap::make_3d(&mS16, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 16, CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64) ||
       !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B)) {
     set_error("nolsm_sign_noalloc: cuTensorMapEncodeTiled rejected the static scratch layout");
@@ -1386,7 +1417,7 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.nbelow = nullptr;
   g.wait_ns = opts->wait_ns > 0 ? (uint64_t)opts->wait_ns : kWaitNs;
   NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, g);
+  k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, g);
   NOLSM_LAUNCH_CHECK();
   return NOLSM_OK;
 }

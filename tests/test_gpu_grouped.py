@@ -132,7 +132,7 @@ def test_grouped_solve_matches_the_oracle(nl, name):
         gplan.stats_reset()
         r = nl.nolsm_solve_batch(gplan, mu, nl.options(prec))
         if large and prec == "fp32":
-            kept = gplan.stats().ill_conditioned_kept
+            kept = gplan.stats()["ill_conditioned_kept"]
             print(f"{name}: condition numbers of the sampled groups' overlaps {kappa.min():.1f}..{kappa.max():.1f}; "
                   f"{kept} groups above 775 rows counted as kept in FP32 mode")
         D = gplan.scatter().cpu().numpy()
