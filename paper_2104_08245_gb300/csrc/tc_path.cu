@@ -119,7 +119,7 @@ enum : int {
   kEpiX = 2,      // scale * P to the planes and in FP32 to Xout
   kEpiA = 3       // P in FP32 to Aout (no planes)
 };
-constexpr int kPlanesInv = 12;   // inverse mode: plane pairs Y, Z, T (then X), Y', Z', T_J(H0)
+constexpr int kPlanesInv = 10;   // inverse mode: plane pairs Y (then T_J(H0)), Z, T (then X), Y', Z'
 
 constexpr int kSlots = 2;   // submatrices in flight per CTA (their products interleave)
 constexpr int kRing = 4;    // product descriptors between the scheduler and the MMA / epilogue warps
@@ -192,10 +192,31 @@ __device__ __forceinline__ void two_sum(float& s, float& c, float p) {
   s = t;
 }
 
-// 32 consecutive values of one row as packed hi (and lo) pairs.
-__device__ __forceinline__ void split_pack(const float (&v)[32], Fmt f, uint32_t (&h)[16], uint32_t (&l)[16]) {
+// 32 consecutive values of one row as packed hi (and lo) pairs; the format a template parameter (one
+// branch per chunk, none per pair), the lo parts only when the format has them.
+template <int kFmt, bool kLo>
+__device__ __forceinline__ void split_pack_t(const float (&v)[32], uint32_t (&h)[16], uint32_t (&l)[16]) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) split2(v[2 * j], v[2 * j + 1], f.fmt, h[j], l[j]);
+  for (int j = 0; j < 16; ++j) {
+    if (kLo) {
+      split2(v[2 * j], v[2 * j + 1], kFmt, h[j], l[j]);
+    } else if (kFmt == FMT_BF16) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      h[j] = *reinterpret_cast<const uint32_t*>(&b);
+    } else {
+      const __half2 b = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+      h[j] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+  }
+}
+__device__ __forceinline__ void split_pack(const float (&v)[32], Fmt f, uint32_t (&h)[16], uint32_t (&l)[16]) {
+  if (f.fmt == FMT_BF16) {
+    if (f.terms > 1) split_pack_t<FMT_BF16, true>(v, h, l);
+    else split_pack_t<FMT_BF16, false>(v, h, l);
+  } else {
+    if (f.terms > 1) split_pack_t<FMT_F16, true>(v, h, l);
+    else split_pack_t<FMT_F16, false>(v, h, l);
+  }
 }
 
 // One row of X (2-byte hi and, with kLo, lo planes; n64 columns, zero padded) times 8 columns of Q in
@@ -344,21 +365,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           // (as the A operand) only by tile (mb, 0), whose loads have completed before its epilogue writes
           d.zo = st.kind == 0 ? zb + 4 : (st.ncb == 1 ? d.za : zb + 2 * (st.cur ^ 1));
         } else {
-          // pairs: Y in 0 or 3, Z in 1 or 4 (ping-pong), T and then X in 2, T_J(H0) in 5
+          // pairs: Y in 0 (updated in place when one column tile covers the matrix, else ping-pong with 3),
+          // Z in 1 or 4 (ping-pong: every row tile of T Z reads all of Z), T and then X in 2; T_J(H0) goes
+          // into Y's pair once Y is no longer needed
           d.last = st.kind == 4;
           d.scale = 0.5f;
           d.fo = st.fcur;
           switch (st.kind) {
             case 0:  // V = Z Y -> T = 3I - V
               d.za = zb + 2 * st.zc; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiT; break;
-            case 1:  // Y' = 1/2 Y T
-              d.za = zb + 2 * st.yc; d.zb = zb + 4; d.zo = zb + 2 * (st.yc == 0 ? 3 : 0); d.epi = kEpiScale; break;
+            case 1:  // Y' = 1/2 Y T (row block mb of Y is read only by tile (mb, 0), as for X X T)
+              d.za = zb + 2 * st.yc; d.zb = zb + 4; d.zo = st.ncb == 1 ? d.za : zb + 2 * (st.yc == 0 ? 3 : 0);
+              d.epi = kEpiScale; break;
             case 2:  // Z' = 1/2 T Z
               d.za = zb + 4; d.zb = zb + 2 * st.zc; d.zo = zb + 2 * (st.zc == 1 ? 4 : 1); d.epi = kEpiScale; break;
             case 3:  // X = Z Z / c = T_J(S)^-1
               d.za = zb + 2 * st.zc; d.zb = d.za; d.zo = zb + 4; d.epi = kEpiX; d.scale = st.cinv; break;
             default:  // A_J = X T_J(H0)
-              d.za = zb + 4; d.zb = zb + 10; d.zo = zb + 4; d.epi = kEpiA; break;
+              d.za = zb + 4; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiA; break;
           }
         }
       }
@@ -499,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // inverse mode, a new submatrix J in slot s: c = Tr T_J(S) / n and step 0 without products, since Z_0 = I:
     // V_0 = Y_0 = T_J(S) / c, T_0 = 3I - Y_0 and Z_1 = T_0 / 2 are written directly (pairs 0, 2, 1), with the
-    // defect ||I - Y_0||_F / sqrt(n); only Y_1 = Y_0 T_0 / 2 needs the tensor cores. T_J(H0) into pair 5.
+    // defect ||I - Y_0||_F / sqrt(n); only Y_1 = Y_0 T_0 / 2 needs the tensor cores.
     auto start_inverse = [&](int s, int J) {
       SlotState& st = sh.slot[s];
       const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
@@ -548,7 +572,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      fill_pair(base + 10 * plane_elems, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
       for (int o = 16; o > 0; o >>= 1) dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
       if (lane == 0) sh.dred[0][warp - 4] = dpart;
       epi_bar();
@@ -568,7 +591,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         st.kind = st.last ? 3 : 1;     // step 0 the last: X = Z_1 Z_1 / c next; else Y_1 = Y_0 T_0 / 2
         st.zdone = 1;
       }
-      epi_bar();   // dred free again
+      epi_bar();   // dred free again; st.last visible to every epilogue thread
+      // step 0 the last: Y_0 is not needed, T_J(H0) takes its pair now (else after the last Z update)
+      if (st.last) fill_pair(base, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
     };
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
@@ -823,19 +848,39 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc::tmem_wait_ld();
               // entries past n are written as zeros: the trimmed products leave the accumulator's columns
               // past n16 as they were, and the next products' K and N never reach past n16
+              // a chunk inside the n columns that holds none of the warp's diagonal entries takes the short
+              // path (warp-uniform test): rows past n through a zero factor, no test per entry
+              const bool rin = rok && row < n;
+              const bool inner = col0 + 32 <= n && col0 != (rbase & ~31);
               if (epi == kEpiT) {
+                if (inner) {
+                  const float s = rin ? sc : 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int col = col0 + j;
-                  const bool in = rok && row < n && col < n;
-                  const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - P)_ij
-                  if (in) part += e * e;
-                  v[j] = in ? e + (row == col ? 2.0f : 0.0f) : 0.0f;                 // (3I - P)_ij
+                  for (int j = 0; j < 32; ++j) {
+                    const float p = s * __uint_as_float(r[j]);   // P_ij, off the diagonal: (I - P)_ij = -p
+                    part = fmaf(p, p, part);
+                    v[j] = -p;                                   // (3I - P)_ij
+                  }
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) {
+                    const int col = col0 + j;
+                    const bool in = rin && col < n;
+                    const float e = (row == col ? 1.0f : 0.0f) - sc * __uint_as_float(r[j]);  // (I - P)_ij
+                    if (in) part += e * e;
+                    v[j] = in ? e + (row == col ? 2.0f : 0.0f) : 0.0f;                 // (3I - P)_ij
+                  }
                 }
               } else {
                 const float m = escale * sc;
+                if (col0 + 32 <= n) {
+                  const float mr = rin ? m : 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = (rok && row < n && col0 + j < n) ? m * __uint_as_float(r[j]) : 0.0f;
+                  for (int j = 0; j < 32; ++j) v[j] = mr * __uint_as_float(r[j]);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 32; ++j) v[j] = (rin && col0 + j < n) ? m * __uint_as_float(r[j]) : 0.0f;
+                }
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
@@ -927,7 +972,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           case 1:   // after Y's update: Z's, unless the step's Z update was made at the start
-            st.yc = st.yc == 0 ? 3 : 0;
+            if (st.ncb != 1) st.yc = st.yc == 0 ? 3 : 0;
             st.kind = st.zdone ? 0 : 2;
             st.zdone = 0;
             break;
@@ -935,7 +980,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           case 3: st.kind = 4; break;
           default: break;
         }
-      } else if (tid == 128) {
+      }
+      if (kMode == 1 && d.kind == 2 && st.last) {
+        // the iteration's last Z update is done: T_J(H0) into Y's pair (Y was last read by this step's
+        // V = Z Y) for A_J = X T_J(H0), written now so that it is not held through the iteration
+        const int J = st.job;
+        const double* H = g.ws + (g.a_off[J] - g.a_base) + g.chunk_n2;
+        uint16_t* yp = g.planes + ((size_t)(sub0 + d.slot) * kPps + 2 * st.yc) * plane_elems;
+        fill_pair(yp, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
+      }
+      if (kMode == 0 && tid == 128) {
         if (d.kind == 0) {
           // defect of X_step and the decision about the following steps
           float dsum = 0.0f;
