@@ -884,13 +884,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
             }
-            if (kMode == 1 && live && rok && epi >= kEpiX && row < n) {
-              // inverse mode: X or A_J in FP32, row-major n x n
+            if (kMode == 1 && live && epi >= kEpiX) {
+              // inverse mode: X or A_J in FP32, row-major n x n. The chunk goes through the warp's staging
+              // buffer (row = lane, entry j at j ^ lane: no bank conflicts either way) so that each store
+              // instruction writes 32 consecutive entries of one row
               const int J = sh.slot[d.slot].job;
-              float* dst = (epi == kEpiX ? g.Xout + (g.a_off[J] - g.a_base) : g.Aout + g.a_off[J]) + (size_t)row * n;
+              float* dst = epi == kEpiX ? g.Xout + (g.a_off[J] - g.a_base) : g.Aout + g.a_off[J];
+              float* wf = reinterpret_cast<float*>(stg + (size_t)(warp - 4) * 4096);
+              if (lane == 0) tc::bulk_wait_read<0>();   // this warp's previous store has read the buffer
+              __syncwarp();
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (col0 + j < n) dst[col0 + j] = v[j];
+              for (int j = 0; j < 32; ++j) wf[lane * 32 + (j ^ lane)] = v[j];
+              __syncwarp();
+              const int nr = m64 ? 16 : 32;
+              for (int rr = 0; rr < nr; ++rr) {
+                const int orow = rbase + rr;
+                if (orow < n && col0 + lane < n) dst[(size_t)orow * n + col0 + lane] = wf[rr * 32 + (lane ^ rr)];
+              }
+              __syncwarp();   // the staging is free again
             }
             if (kMode == 1 && epi == kEpiA) {
               // no operand to write
