@@ -498,19 +498,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
     uint32_t tcount = 0;
 
-    // One n64 x n64 operand (zero padded) into the 3-term FP16 planes hi, lo (hi + plane_elems): four rows
-    // per warp pass, 8 consecutive columns per lane, 16-byte stores; value(i, j) for i, j < n.
-    auto fill_pair = [&](uint16_t* hi, int n, int n64, auto value) {
+    // One FP64 n x n matrix M (row-major) as an n64 x n64 operand (zero padded) into the 3-term FP16 planes
+    // hi, lo (hi + plane_elems): four rows per warp pass, 8 consecutive columns per lane, the pass's 32 loads
+    // all issued before its first store, then 16-byte stores.
+    auto fill_pair = [&](uint16_t* hi, int n, int n64, const double* __restrict__ M) {
       uint16_t* lo = hi + plane_elems;
       for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
         for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
+          float vv[4][8];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vv[r][u] = (i < n && j0 + u < n) ? (float)__ldg(M + (size_t)i * n + j0 + u) : 0.0f;
+          }
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int i = i0 + r;
             if (i >= n64) break;
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (i < n && j0 + u < n) ? value(i, j0 + u) : 0.0f;
+            const float (&v)[8] = vv[r];
             uint32_t h[4], l[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) split2(v[2 * u], v[2 * u + 1], FMT_F16, h[u], l[u]);
@@ -540,6 +546,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       // Y_0, T_0 and Z_1 from one read of T_J(S): the same pass pattern as fill_pair, three pairs out
       for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
         for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
+          float sv[4][8];   // the pass's 32 loads, all issued before its first store
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int i = i0 + r;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[r][u] = (i < n && j0 + u < n) ? (float)__ldg(S + (size_t)i * n + j0 + u) : 0.0f;
+          }
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int i = i0 + r;
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int u = 0; u < 8; ++u) {
               const int j = j0 + u;
               const bool in = i < n && j < n;
-              y[u] = in ? (float)S[(size_t)i * n + j] * inv : 0.0f;
+              y[u] = sv[r][u] * inv;
               const float e = (i == j && in ? 1.0f : 0.0f) - y[u];
               dpart += e * e;
               t[u] = in ? (i == j ? 3.0f : 0.0f) - y[u] : 0.0f;
@@ -593,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       epi_bar();   // dred free again; st.last visible to every epilogue thread
       // step 0 the last: Y_0 is not needed, T_J(H0) takes its pair now (else after the last Z update)
-      if (st.last) fill_pair(base, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
+      if (st.last) fill_pair(base, n, n64, H);
     };
 
     // a4 for a new submatrix of slot s: X_0 = (A - mu I) / alpha in the main format, zero padded
@@ -998,7 +1011,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int J = st.job;
         const double* H = g.ws + (g.a_off[J] - g.a_base) + g.chunk_n2;
         uint16_t* yp = g.planes + ((size_t)(sub0 + d.slot) * kPps + 2 * st.yc) * plane_elems;
-        fill_pair(yp, n, n64, [&](int i, int j) { return (float)H[(size_t)i * n + j]; });
+        fill_pair(yp, n, n64, H);
       }
       if (kMode == 0 && tid == 128) {
         if (d.kind == 0) {
