@@ -32,6 +32,9 @@
 // T_J(S) exceeds twice the mean (then the defect grows, and the submatrix, like any whose iteration does
 // not reach tol_inv within max_inv steps, is flagged for the FP64 preparation). X = T_J(S)^-1 is also
 // written in FP32 for the refinement of the centre columns of T_J(S)^-1.
+// This mode runs 512 threads: three epilogue groups (warps 4-15, every third chunk each), since the start
+// of a submatrix (three operand pairs from T_J(S)) and T_J(H0) weigh more against its few products; its
+// tiles are 128 x up to 192 columns, and the TMA / MMA warpgroup hands registers to the epilogue (setmaxnreg).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -50,13 +53,37 @@ namespace nolsm {
 
 namespace {
 
-constexpr int kThreads = 384;   // warp 0 TMA, warp 1 MMA, warps 4-11 two epilogue groups
 constexpr int kStages = 2;
 constexpr uint32_t kABytes = 128 * 64 * 2;        // one A plane slice: 128 rows x 64 K
-constexpr uint32_t kBBytes = 64 * 256 * 2;        // one B plane slice: 64 K x up to 256 columns
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr uint32_t kStgBytes = 128 * 64;                // 8 KB; the epilogue's staging is 4 kStgBytes
-constexpr int kSmemBytes = kStages * kStageBytes + 4 * kStgBytes + 1024;   // + a 4 KB hi/lo buffer per epilogue warp
+constexpr int kMaxEpiWarps = 12;
+
+// Launch shape per mode. Warp 0 issues the TMA loads, warp 1 the MMAs; the epilogue warps from warp 4 on
+// come in groups of four (each group covers the 128 TMEM lanes) and deal a tile's 32-column chunks round
+// robin. The sign iteration (mode 0): 384 threads, two groups, tiles of 128 x up to 256 columns. The inverse
+// square root (mode 1), whose per-submatrix start (three operand pairs from T_J(S)) and T_J(H0) weigh more
+// against its few products: 512 threads, three groups, tiles of 128 x up to 192 columns (so that the twelve
+// 4 KB staging buffers fit beside the two operand stages), with a register split (below).
+template <int kMode>
+struct Shape {
+  static constexpr int kThreads = kMode == 0 ? 384 : 512;
+  static constexpr int kEpiWarps = kThreads / 32 - 4;
+  static constexpr int kEpiThreads = 32 * kEpiWarps;
+  static constexpr int kGroups = kEpiWarps / 4;
+  static constexpr int kTileN = kMode == 0 ? 256 : 192;        // N of one MMA
+  static constexpr uint32_t kBBytes = 64 * kTileN * 2;        // one B plane slice: 64 K x up to kTileN columns
+  static constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+  static constexpr uint32_t kStgTotal = 4096 * kEpiWarps;    // a 4 KB hi/lo staging buffer per epilogue warp
+  static constexpr int kSmemBytes = kStages * kStageBytes + kStgTotal + 1024;
+};
+static_assert(Shape<1>::kEpiWarps <= kMaxEpiWarps && Shape<0>::kEpiWarps <= kMaxEpiWarps, "epilogue warps");
+static_assert(Shape<0>::kSmemBytes <= 227 * 1024 && Shape<1>::kSmemBytes <= 227 * 1024, "shared memory");
+// Register split of the 512-thread shape: the launch gives every thread kRegsLaunch registers (512 x 128 = the
+// SM's 65,536); the first warpgroup (TMA and MMA threads) releases down to kRegsLow and the three epilogue
+// warpgroups take kRegsEpi: 128 x 56 + 384 x 152 = 65,536, so the increase never waits on registers that do
+// not exist.
+constexpr int kRegsLaunch = 128, kRegsLow = 56, kRegsEpi = 152;
+static_assert(128 * kRegsLow + Shape<1>::kEpiThreads * kRegsEpi <= Shape<1>::kThreads * kRegsLaunch,
+              "register split above the launch");
 constexpr int kPlanes = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;        // default limit per wait (2 s); one product takes < 1 ms
 
@@ -158,8 +185,8 @@ struct Shared {
   int fetch;
   SlotState slot[kSlots];
   Desc ring[kRing];
-  float red[2][8];               // defect partial sums, by product parity
-  double dred[3][8];
+  float red[2][kMaxEpiWarps];    // defect partial sums, by product parity
+  double dred[3][kMaxEpiWarps];
 };
 
 __device__ __forceinline__ float from_bits(uint16_t b, int fmt) {
@@ -260,15 +287,17 @@ __device__ __forceinline__ void xq_row(const uint16_t* __restrict__ xh, const ui
   }
 }
 
-// named barrier 3 for the 256 epilogue threads
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 3, 256;" ::: "memory"); }
-// barrier 3 with an OR over the 256 epilogue threads' predicates
+// named barrier 3 for the N epilogue threads
+template <int N>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 3, %0;" ::"n"(N) : "memory"); }
+// barrier 3 with an OR over the N epilogue threads' predicates
+template <int N>
 __device__ __forceinline__ bool epi_bar_or(bool p) {
   uint32_t r;
   asm volatile(
-      "{\n\t.reg .pred P, Q;\n\tsetp.ne.u32 P, %1, 0;\n\tbar.red.or.pred Q, 3, 256, P;\n\tselp.u32 %0, 1, 0, Q;\n\t}"
+      "{\n\t.reg .pred P, Q;\n\tsetp.ne.u32 P, %1, 0;\n\tbar.red.or.pred Q, 3, %2, P;\n\tselp.u32 %0, 1, 0, Q;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)p)
+      : "r"((uint32_t)p), "n"(N)
       : "memory");
   return r != 0;
 }
@@ -282,11 +311,16 @@ __device__ __forceinline__ bool tail64(const Desc& d, int mb) {
 
 // kMode 0: the sign iteration (a4-a7); kMode 1: the inverse square root of T_J(S) and A_J (a2-a3)
 template <int kMode>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
     k_ns_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
             const __grid_constant__ CUtensorMap mapS, const __grid_constant__ CUtensorMap mapA8,
-            const __grid_constant__ CUtensorMap mapB8, const __grid_constant__ CUtensorMap mapS16, TcArgs g) {
+            const __grid_constant__ CUtensorMap mapB8, const __grid_constant__ CUtensorMap mapS16,
+            const __grid_constant__ CUtensorMap mapS2, const __grid_constant__ CUtensorMap mapS16x2, TcArgs g) {
   constexpr int kPps = kMode == 0 ? kPlanes : kPlanesInv;   // planes per slot
+  constexpr int kEpiWarps = Shape<kMode>::kEpiWarps, kEpiThreads = Shape<kMode>::kEpiThreads;
+  constexpr int kGroups = Shape<kMode>::kGroups, kTileN = Shape<kMode>::kTileN;
+  constexpr uint32_t kBBytes = Shape<kMode>::kBBytes, kStageBytes = Shape<kMode>::kStageBytes;
+  constexpr uint32_t kStgTotal = Shape<kMode>::kStgTotal;
   extern __shared__ uint8_t smraw[];
   uint8_t* stage_mem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Shared sh;
@@ -299,9 +333,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sh.accf[b], 1);
-      tc::mbar_init(&sh.acce[b], 256);
+      tc::mbar_init(&sh.acce[b], kEpiThreads);
     }
-    for (int s = 0; s < kSlots; ++s) tc::mbar_init(&sh.epi_done[s], 256);
+    for (int s = 0; s < kSlots; ++s) tc::mbar_init(&sh.epi_done[s], kEpiThreads);
     for (int r = 0; r < kRing; ++r) tc::mbar_init(&sh.desc_full[r], 1);
     tc::mbar_init(&sh.idle, 1);
     tc::fence_mbar_init();
@@ -312,6 +346,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::prefetch_tmap(&mapA8);
     tc::prefetch_tmap(&mapB8);
     tc::prefetch_tmap(&mapS16);
+    tc::prefetch_tmap(&mapS2);
+    tc::prefetch_tmap(&mapS16x2);
   }
   if (warp == 0) {
     tc::tmem_alloc(&sh.tmem, 512);
@@ -327,6 +363,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t arm_phase[kStages] = {0, 0};                      // producer: parity of the last load armed per stage
   bool armed[kStages] = {false, false};
 
+  if (warp < 4) {
+  if constexpr (kMode == 1) tc::setmaxnreg_dec<kRegsLow>();   // the TMA / MMA warpgroup gives registers up
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ producer: schedules the products of both slots
     // round robin over live slots; a slot's next product is issued once the epilogue of its previous
@@ -394,13 +432,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nks = f8 ? k8_extent(d.n64) / 128 : d.nks;   // E4M3: 128-byte K slices
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
-          const int nt = min(256, d.n64 - 256 * cb);
+          const int nt = min(kTileN, d.n64 - kTileN * cb);
           // an M = 64 tile loads 64 rows of A (the B map's 64 x 64 box)
           const bool m64 = tail64(d, mb);
           const uint32_t abytes = m64 ? kABytes / 2 : kABytes;
           // E4M3: both operands K-major (the symmetric iterate is its own transpose); the B box is always
-          // 256 rows (rows past R are zero-filled by the copy)
-          const uint32_t bytes = f8 ? kABytes + 256u * 128u : (uint32_t)two * (abytes + (uint32_t)nt * 128u);
+          // kTileN rows (rows past R are zero-filled by the copy)
+          const uint32_t bytes = f8 ? kABytes + (uint32_t)kTileN * 128u : (uint32_t)two * (abytes + (uint32_t)nt * 128u);
           for (int ks = 0; ks < nks; ++ks) {
             const int st = kcount % kStages;
             const uint32_t ph = (kcount / kStages) & 1;
@@ -411,13 +449,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             arm_phase[st] = ph;
             if (f8) {
               tc::tma_load_3d(sm, &mapA8, &sh.full[st], 128 * ks, 128 * mb, d.za);
-              tc::tma_load_3d(sm + 2 * kABytes, &mapB8, &sh.full[st], 128 * ks, 256 * cb, d.zb);
+              tc::tma_load_3d(sm + 2 * kABytes, &mapB8, &sh.full[st], 128 * ks, kTileN * cb, d.zb);
             } else {
               for (int z = 0; z < two; ++z) {
                 tc::tma_load_3d(sm + z * kABytes, m64 ? &mapB : &mapA, &sh.full[st], 64 * ks, 128 * mb, d.za + z);
                 uint8_t* bdst = sm + 2 * kABytes + z * kBBytes;
                 for (int c = 0; c < nt / 64; ++c)
-                  tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], 256 * cb + 64 * c, 64 * ks, d.zb + z);
+                  tc::tma_load_3d(bdst + c * 8192, &mapB, &sh.full[st], kTileN * cb + 64 * c, 64 * ks, d.zb + z);
               }
             }
             ++kcount;
@@ -442,8 +480,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int n16 = (d.n + 15) & ~15;
       for (int mb = 0; mb < d.nrb && !sh.err; ++mb)
         for (int cb = 0; cb < d.ncb && !sh.err; ++cb) {
-          const int nt = min(256, d.n64 - 256 * cb);
-          const int ntu = min(nt, n16 - 256 * cb);
+          const int nt = min(kTileN, d.n64 - kTileN * cb);
+          const int ntu = min(nt, n16 - kTileN * cb);
           // kind::f16: A K-major, B MN-major; kind::f8f6f4 (E4M3 = 0): both K-major
           const uint32_t id = f8 ? tc::idesc(0, 0, 0, 0, 128, nt)
                                  : tc::idesc(d.f.fmt, d.f.fmt, 0, 1, tail64(d, mb) ? 64 : 128, ntu);
@@ -491,11 +529,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++tcount;
         }
     }
-  } else if (warp >= 4) {
+  }
+  } else {
+  if constexpr (kMode == 1) tc::setmaxnreg_inc<kRegsEpi>();   // to the epilogue groups
+  {
     // ------------------------------------------------ epilogue: drains products, decides, finishes and starts slots
     const int etid = tid - 128;              // 0..255
     const int q = warp & 3;                  // TMEM lane quarter of this warp
-    const int grp = (warp - 4) >> 2;         // epilogue group: even or odd 32-column chunks
+    const int grp = (warp - 4) >> 2;         // epilogue group: chunks grp, grp + 3, ... of a tile
     uint32_t tcount = 0;
 
     // One FP64 n x n matrix M (row-major) as an n64 x n64 operand (zero padded) into the 3-term FP16 planes
@@ -503,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // all issued before its first store, then 16-byte stores.
     auto fill_pair = [&](uint16_t* hi, int n, int n64, const double* __restrict__ M) {
       uint16_t* lo = hi + plane_elems;
-      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 4 * kEpiWarps) {
         for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
           float vv[4][8];
 #pragma unroll
@@ -544,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
       float dpart = 0.0f;   // this thread's share of ||I - Y_0||_F^2
       // Y_0, T_0 and Z_1 from one read of T_J(S): the same pass pattern as fill_pair, three pairs out
-      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+      for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 4 * kEpiWarps) {
         for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
           float sv[4][8];   // the pass's 32 loads, all issued before its first store
 #pragma unroll
@@ -587,14 +628,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       for (int o = 16; o > 0; o >>= 1) dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
       if (lane == 0) sh.dred[0][warp - 4] = dpart;
-      epi_bar();
+      epi_bar<kEpiThreads>();
       if (tid == 128) {
         float dsum = 0.0f;
-        for (int w = 0; w < 8; ++w) dsum += (float)sh.dred[0][w];
+        for (int w = 0; w < kEpiWarps; ++w) dsum += (float)sh.dred[0][w];
         const float d0 = sqrtf(dsum / (float)n);
         st.job = J;
         st.n = n; st.n64 = n64; st.R = R;
-        st.nrb = R / 128; st.ncb = (n64 + 255) / 256; st.nks = n64 / 64;
+        st.nrb = R / 128; st.ncb = (n64 + kTileN - 1) / kTileN; st.nks = n64 / 64;
         st.yc = 0; st.zc = 1; st.cinv = inv;
         st.steps = 1; st.rsteps = 0; st.status = kSubOk;
         st.fcur = Fmt{FMT_F16, 3}; st.fnxt = st.fcur;
@@ -604,7 +645,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         st.kind = st.last ? 3 : 1;     // step 0 the last: X = Z_1 Z_1 / c next; else Y_1 = Y_0 T_0 / 2
         st.zdone = 1;
       }
-      epi_bar();   // dred free again; st.last visible to every epilogue thread
+      epi_bar<kEpiThreads>();   // dred free again; st.last visible to every epilogue thread
       // step 0 the last: Y_0 is not needed, T_J(H0) takes its pair now (else after the last Z update)
       if (st.last) fill_pair(base, n, n64, H);
     };
@@ -617,9 +658,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int k = atomicAdd(g.next, 1);
           sh.fetch = (k < g.j1 - g.j0 && !sh.err) ? g.order[k] : -1;
         }
-        epi_bar();
+        epi_bar<kEpiThreads>();
         const int J = sh.fetch;
-        epi_bar();
+        epi_bar<kEpiThreads>();
         if (J < 0) {
           if (tid == 128) st.job = -1;
           break;
@@ -651,7 +692,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the other X plane and of T (their products write only the first n64 columns)
           const int k8 = k8_extent(n64);
           uint8_t* p8 = reinterpret_cast<uint8_t*>(hi);
-          for (int e = etid; e < R * k8; e += 256) {
+          for (int e = etid; e < R * k8; e += kEpiThreads) {
             const int i = e / k8, j = e - i * k8;
             float x = 0.0f;
             if (i < n && j < n) x = (A[(size_t)i * n + j] - (i == j ? fmu : 0.0f)) * inv;
@@ -665,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // four rows per warp pass, 8 consecutive columns per lane (all 32 loads in flight together, then
           // 16-byte stores of hi and lo); rows and columns n..n64 are the zero padding; rows from n64 on
           // only feed product rows that are never read back
-          for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 32) {
+          for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 4 * kEpiWarps) {
             for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
               float v[4][8];
 #pragma unroll
@@ -694,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (tid == 128) {
           st.job = J;
           st.n = n; st.n64 = n64; st.R = R;
-          st.nrb = R / 128; st.ncb = (n64 + 255) / 256; st.nks = n64 / 64;
+          st.nrb = R / 128; st.ncb = (n64 + kTileN - 1) / kTileN; st.nks = n64 / 64;
           st.kind = 0; st.cur = 0;
           st.phase = 0; st.refine_left = g.refine_steps; st.steps = 0; st.rsteps = 0;
           st.status = kSubNotConv; st.last = 0;
@@ -710,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // a7 for the finished submatrix of slot s: centre columns of T_J(D) = 1/2 (I - X) T_J(S)^-1 and the
     // FP64 partial traces
     auto finish_slot = [&](int s) {
-      epi_bar();   // the slot state written by thread 128 and the final X of both groups are visible
+      epi_bar<kEpiThreads>();   // the slot state written by thread 128 and the final X of every group are visible
       SlotState& st = sh.slot[s];
       const int J = st.job, n = st.n, b = g.nbf[J];
       // the final X_k, hi (+ lo) in the last product's output format
@@ -728,16 +769,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int n64 = st.n64, bp = (b + 7) & ~7;
       float* Qs = reinterpret_cast<float*>(stg);
       const size_t qs_bytes = (size_t)n64 * bp * sizeof(float);
-      const bool fast = qs_bytes + (size_t)n * b * sizeof(float2) <= 4 * kStgBytes;
+      const bool fast = qs_bytes + (size_t)n * b * sizeof(float2) <= kStgTotal;
       float2* Ps = reinterpret_cast<float2*>(stg + qs_bytes);
       double ps = 0.0, ph = 0.0;
       if (fast) {
-        for (int e = etid; e < n64 * bp; e += 256) {
+        for (int e = etid; e < n64 * bp; e += kEpiThreads) {
           const int k = e / bp, c = e - k * bp;
           Qs[e] = (k < n && c < b) ? (float)Q[(size_t)k * b + c] : 0.0f;
         }
-        epi_bar();
-        for (int i0 = 32 * (warp - 4); i0 < n; i0 += 256) {
+        epi_bar<kEpiThreads>();
+        for (int i0 = 32 * (warp - 4); i0 < n; i0 += kEpiThreads) {
           const int i = i0 + lane;
           const size_t ro = (size_t)(i < n ? i : 0) * g.LD;
           for (int cg = 0; cg < b; cg += 8) {
@@ -756,8 +797,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        epi_bar();
-        for (int e = etid; e < n * b; e += 256) {
+        epi_bar<kEpiThreads>();
+        for (int e = etid; e < n * b; e += kEpiThreads) {
           const float2 p = Ps[e];
           const double dv = 0.5 * (Q[e] - ((double)p.x + (double)p.y));
           Dc[e] = dv;
@@ -765,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ph += dv * Hc[e];
         }
       } else {
-        for (int e = etid; e < n * b; e += 256) {
+        for (int e = etid; e < n * b; e += kEpiThreads) {
           const int i = e / b, c = e - i * b;
           float sum = 0.0f, cmp = 0.0f;
           for (int k = 0; k < n; ++k) {
@@ -783,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       double px = 0.0;   // the trace of the final X: (n - Tr X) / 2 eigenvalues lie below mu
-      for (int i = etid; i < n; i += 256) {
+      for (int i = etid; i < n; i += kEpiThreads) {
         float x = from_bits(xh[(size_t)i * g.LD + i], xfmt.fmt);
         if (xfmt.terms > 1) x += from_bits(xl[(size_t)i * g.LD + i], xfmt.fmt);
         px += x;
@@ -798,10 +839,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         sh.dred[1][warp - 4] = ph;
         sh.dred[2][warp - 4] = px;
       }
-      epi_bar();
+      epi_bar<kEpiThreads>();
       if (tid == 128) {
         double ts = 0.0, th = 0.0, tx = 0.0;
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < kEpiWarps; ++w) {
           ts += sh.dred[0][w];
           th += sh.dred[1][w];
           tx += sh.dred[2][w];
@@ -815,7 +856,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         g.rsteps[J] = st.rsteps;
         g.status[J] = stt;
       }
-      epi_bar();   // staging and dred free again
+      epi_bar<kEpiThreads>();   // staging and dred free again
     };
 
     start_slot(0);
@@ -823,7 +864,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (uint32_t i = 0;; ++i) {
       // every epilogue thread waits for the descriptor; a wait that ran out in any of them ends all
       const bool got = tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * g.wait_ns);
-      if (epi_bar_or(!got || sh.err)) {
+      if (epi_bar_or<kEpiThreads>(!got || sh.err)) {
         if (tid == 128) sh.err = 1;
         break;
       }
@@ -838,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool bad = false;   // a wait of this warp ran out: keep the barrier schedule, skip the work
       for (int mb = 0; mb < d.nrb; ++mb)
         for (int cb = 0; cb < d.ncb; ++cb) {
-          const int nt = min(256, n64 - 256 * cb);
+          const int nt = min(kTileN, n64 - kTileN * cb);
           const int buf = tcount & 1;
           if (!bad) bad = !tc::mbar_wait(&sh.accf[buf], (tcount >> 1) & 1, tc::globaltimer() + g.wait_ns);
           bad = __any_sync(0xffffffffu, bad);   // tcgen05.ld needs the whole warp
@@ -854,8 +895,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           uint32_t r[32];
           if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
           const float sc = d.f.fmt == FMT_E4M3 ? kF8Down : 1.0f;   // E4M3 operand scales
-          for (int c0 = grp; c0 < nch; c0 += 2) {
-            const int col0 = 256 * cb + 32 * c0;
+          for (int c0 = grp; c0 < nch; c0 += kGroups) {
+            const int col0 = kTileN * cb + 32 * c0;
             float v[32];
             if (live) {
               tc::tmem_wait_ld();
@@ -895,7 +936,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   for (int j = 0; j < 32; ++j) v[j] = (rin && col0 + j < n) ? m * __uint_as_float(r[j]) : 0.0f;
                 }
               }
-              if (c0 + 2 < nch) tc::tmem_ld32(taddr + 32 * (c0 + 2), r);   // overlaps this chunk's work
+              if (c0 + kGroups < nch) tc::tmem_ld32(taddr + 32 * (c0 + kGroups), r);   // overlaps this chunk's work
             }
             if (kMode == 1 && live && epi >= kEpiX) {
               // inverse mode: X or A_J in FP32, row-major n x n. The chunk goes through the warp's staging
@@ -937,30 +978,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 reinterpret_cast<uint4*>(dst)[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
               }
             } else if (live) {
-              // each warp stores its own 32 rows x 32 columns through its own 4 KB staging buffer (hi 2 KB,
-              // lo 2 KB; 64-byte swizzle: 16-byte unit c of row r at unit c ^ ((r >> 1) & 3)), with TMA
-              // tensor stores issued by its lane 0: no barrier between warps, and one store per plane
-              // and chunk (fewer, larger TMA operations measured faster than double-buffered halves)
+              // each warp stores its own 32 rows x 32 columns through its own 4 KB staging buffer (hi rows, then
+              // lo rows; 64-byte swizzle: 16-byte unit c of row r at unit c ^ ((r >> 1) & 3)), with one TMA
+              // tensor store issued by its lane 0 for both planes (a box two planes deep): no barrier between
+              // warps, one store per chunk. An M = 64 tile has 16 rows per warp: its lo rows follow its 16 hi
+              // rows, and the 16-row box reads them there.
               uint32_t h[16], l[16];
               split_pack(v, d.fo, h, l);
               uint8_t* wb = stg + (size_t)(warp - 4) * 4096;
               if (lane == 0) tc::bulk_wait_read<0>();   // this warp's previous store has read the buffer
               __syncwarp();
-              uint4* dh = reinterpret_cast<uint4*>(wb + lane * 64);
-#pragma unroll
-              for (int c = 0; c < 4; ++c) dh[c ^ ((lane >> 1) & 3)] = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
-              if (d.fo.terms > 1) {
-                uint4* dl = reinterpret_cast<uint4*>(wb + 2048 + lane * 64);
+              if (rok) {
+                uint4* dh = reinterpret_cast<uint4*>(wb + lane * 64);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                  dl[c ^ ((lane >> 1) & 3)] = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                  dh[c ^ ((lane >> 1) & 3)] = make_uint4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                if (d.fo.terms > 1) {
+                  uint4* dl = reinterpret_cast<uint4*>(wb + (m64 ? 1024 : 2048) + lane * 64);
+#pragma unroll
+                  for (int c = 0; c < 4; ++c)
+                    dl[c ^ ((lane >> 1) & 3)] = make_uint4(l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                }
               }
               tc::fence_proxy_async_smem();
               __syncwarp();
-              if (lane == 0) {   // an M = 64 tile stores the first 16 rows of the staging (16-row box)
-                const CUtensorMap* ms = m64 ? &mapS16 : &mapS;
+              if (lane == 0) {
+                const CUtensorMap* ms = d.fo.terms > 1 ? (m64 ? &mapS16x2 : &mapS2) : (m64 ? &mapS16 : &mapS);
                 tc::tma_store_3d(ms, wb, col0, rbase, d.zo);
-                if (d.fo.terms > 1) tc::tma_store_3d(ms, wb + 2048, col0, rbase, d.zo + 1);
                 tc::bulk_commit();
               }
             }
@@ -974,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- end of the product: one uniform error decision, then the slot's next state
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
       if (lane == 0) sh.red[i & 1][warp - 4] = part;
-      if (epi_bar_or(bad)) {
+      if (epi_bar_or<kEpiThreads>(bad)) {
         if (tid == 128) sh.err = 1;
         break;
       }
@@ -983,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         switch (d.kind) {
           case 0: {
             float dsum = 0.0f;
-            for (int w = 0; w < 8; ++w) dsum += sh.red[i & 1][w];
+            for (int w = 0; w < kEpiWarps; ++w) dsum += sh.red[i & 1][w];
             const float dd = sqrtf(dsum / (float)n);
             st.steps += 1;
             if (!isfinite(dd) || (dd > g.tol_inv && st.steps >= g.max_inv)) {
@@ -1017,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (d.kind == 0) {
           // defect of X_step and the decision about the following steps
           float dsum = 0.0f;
-          for (int w = 0; w < 8; ++w) dsum += sh.red[i & 1][w];
+          for (int w = 0; w < kEpiWarps; ++w) dsum += sh.red[i & 1][w];
           const float dd = sqrtf(dsum / (float)n);
           const int steps = st.steps + 1;
           if (st.phase == 1) st.rsteps += 1;   // this step ran in the refinement format
@@ -1106,6 +1150,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       atomicExch(g.err, 1);
     }
   }
+  }
 
   // every role has left its loop, so sh.err is final; after a timeout wait (bounded) for this CTA's
   // TMA loads and MMAs still in flight before the shared and tensor memory are released
@@ -1178,6 +1223,20 @@ static bool formats(int precision, Fmt* main_fmt, Fmt* refine_fmt) {
   }
 }
 
+// The inverse kernel's register split (setmaxnreg) assumes the launch gives each of its 512 threads
+// kRegsLaunch registers; with fewer, the epilogue warpgroups' increase could never be granted, so the launch
+// is refused.
+static nolsm_status check_register_split(const void* fn) {
+  cudaFuncAttributes at{};
+  NOLSM_CUDA_TRY(cudaFuncGetAttributes(&at, fn));
+  if (at.numRegs != kRegsLaunch) {
+    set_error("k_ns_tc was built with %d registers per thread; its register split needs exactly %d", at.numRegs,
+              kRegsLaunch);
+    return NOLSM_ERR_UNSUPPORTED;
+  }
+  return NOLSM_OK;
+}
+
 nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64_t j0, int64_t j1, const SolveSpec& spec,
                       cudaStream_t st) {
   Fmt mf, rf;
@@ -1224,9 +1283,13 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
     S->ord_j0 = j0;
     S->ord_j1 = j1;
   }
-  CUtensorMap mA, mB, mS, mS16;
+  CUtensorMap mA, mB, mS, mS16, mS2, mS16x2;
   if (!tmap::make_3d(&mS16, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 16,
                      CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mS16x2, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 16,
+                     CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
+      !tmap::make_3d(&mS2, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 32,
+                     CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
       !tmap::make_3d(&mA, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 64, 64) ||
       !tmap::make_3d(&mS, S->planes.p, 2, (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 32, 32,
@@ -1271,18 +1334,18 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   g.cond = sym ? nullptr : prepared(plan, prep_class(o)).cond.as<float>();
   g.cond_max = cond_max(o.precision);
   g.ill_max_n = prepare_fp64_max_n();
-  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<0>::kSmemBytes));
   // one-byte views of the same planes (rows of 2 LD bytes) for E4M3 operands, both loaded K-major
   CUtensorMap mA8, mB8;
   if (!tmap::make_3d(&mA8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, 128) ||
-      !tmap::make_3d(&mB8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, 256)) {
+      !tmap::make_3d(&mB8, S->planes.p, 1, 2 * (uint64_t)S->LD, (uint64_t)S->R, (uint64_t)S->slots * kPlanes, 128, Shape<0>::kTileN)) {
     set_error("cuTensorMapEncodeTiled rejected the one-byte scratch layout");
     return NOLSM_ERR_CUDA;
   }
   k_status_pending<<<(unsigned)std::min<int64_t>(1024, (work + 255) / 256), 256, 0, st>>>(
       (int32_t)j0, (int32_t)work, spec.list, plan->status.as<int32_t>());
   NOLSM_LAUNCH_CHECK();
-  k_ns_tc<0><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, mS16, g);
+  k_ns_tc<0><<<ctas, Shape<0>::kThreads, Shape<0>::kSmemBytes, st>>>(mA, mB, mS, mA8, mB8, mS16, mS2, mS16x2, g);
   NOLSM_LAUNCH_CHECK();
   plan->stats.launches += 2;
   if (sym) {   // D_c = L^-T U and the traces
@@ -1324,9 +1387,13 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   if (!S->err.p) NOLSM_TRY(dev_alloc(plan, S->err, sizeof(int32_t) * 4));
   if (!S->inv_flops.p) NOLSM_TRY(dev_alloc(plan, S->inv_flops, sizeof(double) * 2));
   const uint64_t depth = (uint64_t)S->islots * kPlanesInv;
-  CUtensorMap mA, mB, mS, mS16;
+  CUtensorMap mA, mB, mS, mS16, mS2, mS16x2;
   if (!tmap::make_3d(&mS16, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 16,
                      CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mS16x2, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 16,
+                     CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
+      !tmap::make_3d(&mS2, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 32,
+                     CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
       !tmap::make_3d(&mA, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 128) ||
       !tmap::make_3d(&mB, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 64, 64) ||
       !tmap::make_3d(&mS, S->inv_planes.p, 2, (uint64_t)S->iLD, (uint64_t)S->iR, depth, 32, 32,
@@ -1355,8 +1422,9 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   g.tol_inv = a.tol_inv; g.max_inv = a.max_inv;
   g.wait_ns = kWaitNs;
   g.flops = S->inv_flops.as<double>();
-  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<1><<<ctas, kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, g);
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<1>::kSmemBytes));
+  NOLSM_TRY(check_register_split(reinterpret_cast<const void*>(k_ns_tc<1>)));
+  k_ns_tc<1><<<ctas, Shape<1>::kThreads, Shape<1>::kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, mS2, mS16x2, g);
   NOLSM_LAUNCH_CHECK();
   double fl[2];
   NOLSM_CUDA_TRY(cudaMemcpyAsync(fl, S->inv_flops.p, sizeof(fl), cudaMemcpyDeviceToHost, st));
@@ -1465,8 +1533,10 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   unsigned char* base = static_cast<unsigned char*>(addr);
   int32_t* ints = reinterpret_cast<int32_t*>(base + kNaPlanesBytes);
 
-  CUtensorMap mA, mB, mS, mS16;
+  CUtensorMap mA, mB, mS, mS16, mS2, mS16x2;
   if (!tmap::make_3d(&mS16, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 16, CU_TENSOR_MAP_SWIZZLE_64B) ||
+      !tmap::make_3d(&mS16x2, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 16, CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
+      !tmap::make_3d(&mS2, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B, 2) ||
       !tmap::make_3d(&mA, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 128) ||
       !tmap::make_3d(&mB, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 64, 64) ||
       !tmap::make_3d(&mS, base, 2, kNaLD, kNaR, (uint64_t)kNaSlots * kPlanes, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B)) {
@@ -1494,8 +1564,8 @@ extern "C" nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, 
   g.rsteps = ints + 2 * kNaMaxSub;
   g.nbelow = nullptr;
   g.wait_ns = opts->wait_ns > 0 ? (uint64_t)opts->wait_ns : kWaitNs;
-  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-  k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), kThreads, kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, g);
+  NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_ns_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<0>::kSmemBytes));
+  k_ns_tc<0><<<std::min(kNaSlots / kSlots, (count + kSlots - 1) / kSlots), Shape<0>::kThreads, Shape<0>::kSmemBytes, st>>>(mA, mB, mS, mA, mB, mS16, mS2, mS16x2, g);
   NOLSM_LAUNCH_CHECK();
   return NOLSM_OK;
 }

@@ -23,10 +23,11 @@ inline EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over [dim2][dim1][dim0] elements of `esize` bytes (dim0 contiguous), box {box0, box1, 1},
+// 3-D map over [dim2][dim1][dim0] elements of `esize` bytes (dim0 contiguous), box {box0, box1, box2},
 // 128-byte swizzle unless another is given. Returns false if the driver rejects it (alignment, sizes).
 inline bool make_3d(CUtensorMap* map, void* base, int esize, uint64_t dim0, uint64_t dim1, uint64_t dim2,
-                    uint32_t box0, uint32_t box1, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+                    uint32_t box0, uint32_t box1, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B,
+                    uint32_t box2 = 1) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const CUtensorMapDataType dt = esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
@@ -34,7 +35,7 @@ inline bool make_3d(CUtensorMap* map, void* base, int esize, uint64_t dim0, uint
                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   cuuint64_t dims[3] = {dim0, dim1, dim2};
   cuuint64_t strides[2] = {dim0 * esize, dim0 * dim1 * esize};
-  cuuint32_t box[3] = {box0, box1, 1};
+  cuuint32_t box[3] = {box0, box1, box2};
   cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
