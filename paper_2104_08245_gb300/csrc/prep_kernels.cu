@@ -35,7 +35,7 @@ constexpr int kThreads = 128;   // several CTAs (submatrices) per SM overlap eac
 constexpr int kMaxB = 64;
 constexpr int kRefineMax = 4;   // refinement steps of Q before a submatrix falls back to the FP64 factor
 constexpr double kRefineTol = 1e-6;
-constexpr double kNsOneStep = 3e-6;   // k_ns_qrefine: a first correction below this ends the refinement
+constexpr double kNsOneStep = 1e-5;   // k_ns_qrefine: a first correction below this ends the refinement
 
 // Row stride of panels and tiles in shared memory: FP64 rows padded by one element (bank spread),
 // FP32 rows by four so that every row starts on a 16-byte boundary (vector loads).
@@ -1115,6 +1115,64 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   if (tid == 0) g.prep_status[J] = ok ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
 }
 
+// One row of R = E_c - T_J(S) q for CN centre columns: S_i (FP64 row of T_J(S)) against q (float2 hi/lo
+// pairs, rows of stride bJ), products and sums in double-FP32 arithmetic (each product's rounding error by FMA,
+// each sum's by TwoSum); column c is on the diagonal of E_c when c == ce. Writes w[c] (FP32) when rv.
+template <int CN>
+__device__ __forceinline__ void residual_row(const double* __restrict__ Si, const float2* __restrict__ q, int n,
+                                             int bJ, bool rv, int ce, float* __restrict__ w) {
+  float sh[CN], sl[CN];
+#pragma unroll
+  for (int c = 0; c < CN; ++c) sh[c] = sl[c] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const float2 a = split_f64(Si[k]);
+    const float2* qk = q + (size_t)k * bJ;
+#pragma unroll
+    for (int c = 0; c < CN; ++c) {
+      const float2 v = qk[c];
+      const float pr = a.x * v.x;
+      sl[c] += fmaf(a.x, v.x, -pr);
+      two_sum(sh[c], sl[c], pr);
+      sl[c] = fmaf(a.x, v.y, fmaf(a.y, v.x, sl[c]));
+    }
+  }
+  if (rv) {
+#pragma unroll
+    for (int c = 0; c < CN; ++c) w[c] = ((c == ce ? 1.0f : 0.0f) - sh[c]) - sl[c];
+  }
+}
+
+// One row of the correction X R for CN columns of R (FP32, rows of stride bJ): four interleaved FP32 partial
+// sums along k per column, added at the end; d[c] for c < CN.
+template <int CN>
+__device__ __forceinline__ void update_row(const float* __restrict__ xi, const float* __restrict__ R, int n, int bJ,
+                                           float (&d)[8]) {
+  float acc[4][CN];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < CN; ++c) acc[u][c] = 0.0f;
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float x = xi[k + u];
+      const float* rk = R + (size_t)(k + u) * bJ;
+#pragma unroll
+      for (int c = 0; c < CN; ++c) acc[u][c] = fmaf(x, rk[c], acc[u][c]);
+    }
+  }
+  for (; k < n; ++k) {
+    const float x = xi[k];
+    const float* rk = R + (size_t)k * bJ;
+#pragma unroll
+    for (int c = 0; c < CN; ++c) acc[0][c] = fmaf(x, rk[c], acc[0][c]);
+  }
+#pragma unroll
+  for (int c = 0; c < CN; ++c) d[c] = (acc[0][c] + acc[1][c]) + (acc[2][c] + acc[3][c]);
+}
+
 // After the tensor-core inverse square root (Eqs. inv1-inv3), which leaves X = T_J(S)^-1 in FP32 (in g.L32,
 // accurate to about 1e-6 of its norm) and A_J in Acache: the centre columns of T_J(S)^-1 by iterative
 // refinement with X as the approximate inverse, q <- q + X (E_c - T_J(S) q) from q = X[:, centre], the
@@ -1155,80 +1213,62 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
   for (int it = 0; it < kRefineMax && !conv; ++it) {
     for (int e = tid; e < nbc; e += kThreads) qp[e] = split_f64(q[e]);
     __syncthreads();
-    // R = E_c - T_J(S) q, one warp per row, lanes along it (coalesced), 8 columns of q per sweep, in
-    // double-FP32 arithmetic (as residual_df); the lanes' (hi, lo) sums are combined with TwoSum
-    for (int i = warp; i < n; i += kWarps) {
-      const double* Si = S + (size_t)i * n;
+    // R = E_c - T_J(S) q: one row per lane, the row's products along k in double-FP32 arithmetic (as
+    // residual_df), up to 8 centre columns per sweep; every lane reads the same entries of q
+    for (int i0 = 32 * warp; i0 < n; i0 += 32 * kWarps) {
+      const int i = i0 + lane;
+      const bool rv = i < n;
+      const double* Si = S + (size_t)(rv ? i : 0) * n;
       for (int cg = 0; cg < bJ; cg += 8) {
-        const int cn = min(8, bJ - cg);
-        float sh[8], sl[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) sh[c] = sl[c] = 0.0f;
-        for (int k = lane; k < n; k += 32) {
-          const float2 a = split_f64(Si[k]);
-          const float2* qk = qp + (size_t)k * bJ + cg;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            if (c < cn) {
-              const float2 v = qk[c];
-              const float pr = a.x * v.x;
-              sl[c] += fmaf(a.x, v.x, -pr);
-              two_sum(sh[c], sl[c], pr);
-              sl[c] = fmaf(a.x, v.y, fmaf(a.y, v.x, sl[c]));
-            }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
-            const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
-            two_sum(sh[c], sl[c], oh);
-            sl[c] += ol;
-          }
-        }
-        if (lane < cn) {
-          float hv = sh[0], lv = sl[0];
-#pragma unroll
-          for (int c = 1; c < 8; ++c)
-            if (lane == c) { hv = sh[c]; lv = sl[c]; }
-          Wsh[i * bJ + cg + lane] = ((i == c0 + cg + lane ? 1.0f : 0.0f) - hv) - lv;
+        float* w = Wsh + (size_t)(rv ? i : 0) * bJ + cg;
+        const float2* qc = qp + cg;
+        const int ce = i - c0 - cg;   // row i holds the 1 of E_c's column cg + c when c == ce
+        switch (min(8, bJ - cg)) {
+          case 1: residual_row<1>(Si, qc, n, bJ, rv, ce, w); break;
+          case 2: residual_row<2>(Si, qc, n, bJ, rv, ce, w); break;
+          case 3: residual_row<3>(Si, qc, n, bJ, rv, ce, w); break;
+          case 4: residual_row<4>(Si, qc, n, bJ, rv, ce, w); break;
+          case 5: residual_row<5>(Si, qc, n, bJ, rv, ce, w); break;
+          case 6: residual_row<6>(Si, qc, n, bJ, rv, ce, w); break;
+          case 7: residual_row<7>(Si, qc, n, bJ, rv, ce, w); break;
+          default: residual_row<8>(Si, qc, n, bJ, rv, ce, w); break;
         }
       }
     }
     __syncthreads();
-    // q <- q + X R, one warp per row of X (coalesced), R from shared memory
+    // q <- q + X R, one row of X per lane, R from shared memory (the same entries for every lane)
     float dmax = 0.0f;
     double qmax = 0.0;
     bool finite = true;
-    for (int i = warp; i < n; i += kWarps) {
-      const float* xi = X + (size_t)i * n;
+    for (int i0 = 32 * warp; i0 < n; i0 += 32 * kWarps) {
+      const int i = i0 + lane;
+      const bool rv = i < n;
+      const float* xi = X + (size_t)(rv ? i : 0) * n;
       for (int cg = 0; cg < bJ; cg += 8) {
         const int cn = min(8, bJ - cg);
-        float acc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
-        for (int k = lane; k < n; k += 32) {
-          const float x = xi[k];
-          const float* rk = Wsh + k * bJ + cg;
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < cn) acc[c] = fmaf(x, rk[c], acc[c]);
+        float d[8];
+        switch (cn) {
+          case 1: update_row<1>(xi, Wsh + cg, n, bJ, d); break;
+          case 2: update_row<2>(xi, Wsh + cg, n, bJ, d); break;
+          case 3: update_row<3>(xi, Wsh + cg, n, bJ, d); break;
+          case 4: update_row<4>(xi, Wsh + cg, n, bJ, d); break;
+          case 5: update_row<5>(xi, Wsh + cg, n, bJ, d); break;
+          case 6: update_row<6>(xi, Wsh + cg, n, bJ, d); break;
+          case 7: update_row<7>(xi, Wsh + cg, n, bJ, d); break;
+          default: update_row<8>(xi, Wsh + cg, n, bJ, d); break;
         }
+        if (rv) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-        if (lane < cn) {
-          float d = acc[0];
-#pragma unroll
-          for (int c = 1; c < 8; ++c)
-            if (lane == c) d = acc[c];
-          const size_t e = (size_t)i * bJ + cg + lane;
-          const double qe = q[e] + (double)d;
-          q[e] = qe;
-          finite = finite && isfinite(d) && isfinite(qe);
-          dmax = fmaxf(dmax, fabsf(d));
-          qmax = fmax(qmax, fabs(qe));
+          for (int c = 0; c < 8; ++c) {
+            if (c < cn) {
+              const size_t e = (size_t)i * bJ + cg + c;
+              const double qe = q[e] + (double)d[c];
+              q[e] = qe;
+              finite = finite && isfinite(d[c]) && isfinite(qe);
+              dmax = fmaxf(dmax, fabsf(d[c]));
+              qmax = fmax(qmax, fabs(qe));
+            }
+          }
         }
       }
     }
@@ -1249,8 +1289,8 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
       qm = fmax(qm, red_q[w2]);
     }
     // converged when the correction is below 1e-6 of q, or after the first step when that correction (the
-    // error of X's columns, about the contraction factor ||I - X T_J(S)|| too) is below 3e-6 of q: the error
-    // left is then about its square, below 1e-11 of q
+    // error of X's columns, about the contraction factor ||I - X T_J(S)|| too) is below 1e-5 of q: the error
+    // left is then about its square, below 1e-10 of q
     conv = (double)dm <= kRefineTol * qm || (it == 0 && (double)dm <= kNsOneStep * qm);
     __syncthreads();
   }
