@@ -91,28 +91,38 @@ __device__ __forceinline__ double aniso_factor(const GatherArgs& g, int k, const
 }
 
 constexpr int kGatherWarps = 8;
+constexpr int kGatherTableBytes = 32;   // per block column of a band: two int64 offsets, three int32, padding
 
 __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
-  extern __shared__ int32_t sm[];
+  extern __shared__ __align__(8) unsigned char gsm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t p = g.p0 + (int64_t)blockIdx.x * kGatherWarps + w;
   if (p >= g.p1) return;   // whole warps only; no block-wide barrier follows
-  // generated elements: the block models of the band, after every warp's integer tables (8-byte aligned)
-  BlockModel* bm = reinterpret_cast<BlockModel*>(sm + ((kGatherWarps * 3 * g.max_nq + 1) & ~1)) + w * g.max_nq;
+  // this warp's tables, one entry per block column c of the band (32 bytes each): the offsets of block
+  // (Ia, Ic) in the stored S and H0 values (-1: no block), its first column, its width and Ic; the block
+  // models of generated elements follow every warp's tables
+  int64_t* sbase = reinterpret_cast<int64_t*>(gsm + (size_t)w * kGatherTableBytes * g.max_nq);
+  int64_t* hbase = sbase + g.max_nq;
+  int32_t* coff = reinterpret_cast<int32_t*>(hbase + g.max_nq);
+  int32_t* bcs = coff + g.max_nq;
+  int32_t* mol = bcs + g.max_nq;
+  BlockModel* bm = reinterpret_cast<BlockModel*>(gsm + (size_t)kGatherWarps * kGatherTableBytes * g.max_nq) +
+                   w * g.max_nq;
   const int J = owner_of(g.nb_ptr, g.n_mol, p);
   const int q0 = g.nb_ptr[J], nq = g.nb_ptr[J + 1] - q0;
   const int Ia = g.nb_idx[p];
   const int ba = g.nbf[Ia];
   const int offa = g.nb_off[p];
   const int n = g.sub_n[J];
-  int32_t* s_slot = sm + w * 3 * g.max_nq;
-  int32_t* h_slot = s_slot + nq;
-  int32_t* coff = s_slot + 2 * nq;
   for (int c = lane; c < nq; c += 32) {
     const int32_t Ic = g.nb_idx[q0 + c];
-    s_slot[c] = find_sorted(g.sci, g.srp[Ia], g.srp[Ia + 1], Ic);
-    h_slot[c] = find_sorted(g.hci, g.hrp[Ia], g.hrp[Ia + 1], Ic);
+    const int ss = find_sorted(g.sci, g.srp[Ia], g.srp[Ia + 1], Ic);
+    const int hs = find_sorted(g.hci, g.hrp[Ia], g.hrp[Ia + 1], Ic);
+    sbase[c] = ss < 0 ? -1 : (g.gen ? 0 : g.soff[ss]);
+    hbase[c] = hs < 0 ? -1 : (g.gen ? 0 : g.hoff[hs]);
     coff[c] = g.nb_off[q0 + c];
+    bcs[c] = g.nbf[Ic];
+    mol[c] = Ic;
     if (g.gen && Ic != Ia) bm[c] = block_model(g, Ia, Ic, ba, g.nbf[Ic]);
   }
   __syncwarp();
@@ -122,31 +132,44 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_gather(GatherArgs g) {
   double* TH = TS + g.chunk_n2;
   double* Sc = g.Sc + g.c_off[J];
   double* Hc = g.Hc + g.c_off[J];
-  for (int r = 0; r < ba; ++r) {
-    int c = 0;   // molecule block of column col; columns advance by 32, blocks by at least one function
-    for (int col = lane; col < n; col += 32) {
-      while (c + 1 < nq && coff[c + 1] <= col) ++c;
-      const int bc = g.nbf[g.nb_idx[q0 + c]];
-      const int cc = col - coff[c];
-      const int ss = s_slot[c], hs = h_slot[c];
-      double vs, vh;
-      if (!g.gen) {
-        vs = ss >= 0 ? g.sval[g.soff[ss] + r * bc + cc] : 0.0;
-        vh = hs >= 0 ? g.hval[g.hoff[hs] + r * bc + cc] : 0.0;
-      } else if (g.nb_idx[q0 + c] == Ia) {   // intra-molecular: identity and the on-site energies
-        vs = (ss >= 0 && r == cc) ? 1.0 : 0.0;
-        vh = (hs >= 0 && r == cc) ? g.onsite[g.onsite_off[Ia] + r] : 0.0;
-      } else {
-        const BlockModel& m = bm[c];
-        vs = ss >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.s, aniso_factor(g, 0, m, r, cc)) : m.s) : 0.0;
-        vh = hs >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.h, aniso_factor(g, 1, m, r, cc)) : m.h) : 0.0;
+  int c = 0;   // block column of col; columns advance by 32, blocks by at least one function
+  for (int col = lane; col < n; col += 32) {
+    while (c + 1 < nq && coff[c + 1] <= col) ++c;
+    const int bc = bcs[c], cc = col - coff[c];
+    const int64_t sb = sbase[c], hb = hbase[c];
+    const bool intra = mol[c] == Ia;
+    const bool centre = col >= c0 && col < c0 + bJ;
+    // the column's ba rows, four at a time: their loads issued together, then their stores
+    for (int r0 = 0; r0 < ba; r0 += 4) {
+      double vs[4], vh[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        vs[u] = vh[u] = 0.0;
+        if (r >= ba) continue;
+        if (!g.gen) {
+          if (sb >= 0) vs[u] = __ldg(g.sval + sb + r * bc + cc);
+          if (hb >= 0) vh[u] = __ldg(g.hval + hb + r * bc + cc);
+        } else if (intra) {   // intra-molecular: identity and the on-site energies
+          vs[u] = (sb >= 0 && r == cc) ? 1.0 : 0.0;
+          vh[u] = (hb >= 0 && r == cc) ? g.onsite[g.onsite_off[Ia] + r] : 0.0;
+        } else {
+          const BlockModel& m = bm[c];
+          vs[u] = sb >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.s, aniso_factor(g, 0, m, r, cc)) : m.s) : 0.0;
+          vh[u] = hb >= 0 ? (g.aniso != 0.0 ? __dmul_rn(m.h, aniso_factor(g, 1, m, r, cc)) : m.h) : 0.0;
+        }
       }
-      const int64_t at = (int64_t)(offa + r) * n + col;
-      TS[at] = vs;
-      TH[at] = vh;
-      if (col >= c0 && col < c0 + bJ) {
-        Sc[(int64_t)(offa + r) * bJ + (col - c0)] = vs;
-        Hc[(int64_t)(offa + r) * bJ + (col - c0)] = vh;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        if (r >= ba) break;
+        const int64_t at = (int64_t)(offa + r) * n + col;
+        TS[at] = vs[u];
+        TH[at] = vh[u];
+        if (centre) {
+          Sc[(int64_t)(offa + r) * bJ + (col - c0)] = vs[u];
+          Hc[(int64_t)(offa + r) * bJ + (col - c0)] = vh[u];
+        }
       }
     }
   }
@@ -496,7 +519,7 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       return NOLSM_ERR_ARG;
     }
     pmark(plan, st);
-    const size_t gsm = sizeof(int32_t) * (size_t)((kGatherWarps * 3 * max_nq + 1) & ~1) +
+    const size_t gsm = (size_t)kGatherTableBytes * kGatherWarps * max_nq +
                        (plan->gen ? sizeof(BlockModel) * kGatherWarps * (size_t)max_nq : 0);
     if (gsm > 48 * 1024) NOLSM_CUDA_TRY(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     k_gather<<<(unsigned)((bands + kGatherWarps - 1) / kGatherWarps), 32 * kGatherWarps, gsm, st>>>(g);
