@@ -221,11 +221,15 @@ def test_trained_network_saves_steps_on_fresh_molecules(nl, system, plan):
     p2 = nl.nolsm_build_submatrices(nl.DeviceSystem(fresh))
     nl.nolsm_plan_set_mlp(p2, m)
     r_g, D_g, _ = _solve(nl, p2, nl.BOUND_GERSHGORIN)
+    r_p, _, _ = _solve(nl, p2, nl.BOUND_POWER)
     r_m, D_m, st = _solve(nl, p2, nl.BOUND_MLP)
     it_g, it_m = r_g.iters.cpu().numpy().mean(), r_m.iters.cpu().numpy().mean()
+    it_p = r_p.iters.cpu().numpy().mean()
     diff = float(np.max(np.abs(D_m - D_g)))
-    print(f"fresh molecules: mean steps learned {it_m:.3f} vs Gershgorin {it_g:.3f}, reruns {st['reruns']}, "
-          f"max|dD| {diff:.2e}")
+    # the power-iteration interval (its own fallback) takes fewer steps still: the network's gain is over the
+    # interval that needs no extra kernel, not over the power iteration (reported, not asserted)
+    print(f"fresh molecules: mean steps learned {it_m:.3f} vs Gershgorin {it_g:.3f} vs power {it_p:.3f}, "
+          f"reruns {st['reruns']}, max|dD| {diff:.2e}")
     assert np.all(r_m.sub_status.cpu().numpy() == 0)
     assert diff <= 2e-6
     assert it_m < it_g
