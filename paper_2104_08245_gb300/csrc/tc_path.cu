@@ -164,6 +164,8 @@ struct SlotState {
   int yc, zc;                    // inverse mode: plane pairs of the current Y and Z
   int zdone;                     // inverse mode: this step's Z update was made at the start (step 0)
   float cinv;                    // inverse mode: 1 / c
+  float zs;                      // inverse mode: Z = zs x (Z's planes); 1/2 until the first Z update, whose
+                                 // planes hold T_0 = 2 Z_1
 };
 
 // One product as scheduled by the producer: read in order by the MMA issuer and the epilogue.
@@ -175,6 +177,7 @@ struct Desc {
   int za, zb, zo;                // plane indices (hi planes) of A, B and the output
   int epi;                       // kEpi*
   float scale;                   // kEpiScale, kEpiX
+  float pscale;                  // kEpiT: the product is pscale P
 };
 
 struct Shared {
@@ -394,6 +397,7 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
         d.f = st.fcur;
         d.n = st.n; d.n64 = st.n64; d.nrb = st.nrb; d.ncb = st.ncb; d.nks = st.nks;
         const int zb = (sub0 + pick) * kPps;
+        d.pscale = 1.0f;
         if constexpr (kMode == 0) {   // the epilogue derives epi and scale from the kind
           d.last = st.kind == 1 && st.last;
           d.fo = st.kind == 0 ? st.fcur : st.fnxt;
@@ -404,21 +408,26 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
           d.zo = st.kind == 0 ? zb + 4 : (st.ncb == 1 ? d.za : zb + 2 * (st.cur ^ 1));
         } else {
           // pairs: Y in 0 (updated in place when one column tile covers the matrix, else ping-pong with 3),
-          // Z in 1 or 4 (ping-pong: every row tile of T Z reads all of Z), T and then X in 2; T_J(H0) goes
-          // into Y's pair once Y is no longer needed
+          // Z in 1 or 4 (ping-pong: every row tile of T Z reads all of Z; until the first Z update the pair
+          // holds T_0 = 2 Z_1, hence the factor zs), T and then X in 2; T_J(H0) goes into Y's pair once Y is
+          // no longer needed
           d.last = st.kind == 4;
           d.scale = 0.5f;
           d.fo = st.fcur;
           switch (st.kind) {
             case 0:  // V = Z Y -> T = 3I - V
-              d.za = zb + 2 * st.zc; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiT; break;
-            case 1:  // Y' = 1/2 Y T (row block mb of Y is read only by tile (mb, 0), as for X X T)
-              d.za = zb + 2 * st.yc; d.zb = zb + 4; d.zo = st.ncb == 1 ? d.za : zb + 2 * (st.yc == 0 ? 3 : 0);
+              d.za = zb + 2 * st.zc; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiT; d.pscale = st.zs; break;
+            case 1:  // Y' = 1/2 Y T (row block mb of Y is read only by tile (mb, 0), as for X X T); at step 0
+                     // T_0 is in Z's pair
+              d.za = zb + 2 * st.yc; d.zb = st.zdone ? zb + 2 * st.zc : zb + 4;
+              d.zo = st.ncb == 1 ? d.za : zb + 2 * (st.yc == 0 ? 3 : 0);
               d.epi = kEpiScale; break;
             case 2:  // Z' = 1/2 T Z
-              d.za = zb + 4; d.zb = zb + 2 * st.zc; d.zo = zb + 2 * (st.zc == 1 ? 4 : 1); d.epi = kEpiScale; break;
+              d.za = zb + 4; d.zb = zb + 2 * st.zc; d.zo = zb + 2 * (st.zc == 1 ? 4 : 1); d.epi = kEpiScale;
+              d.scale = 0.5f * st.zs; break;
             case 3:  // X = Z Z / c = T_J(S)^-1
-              d.za = zb + 2 * st.zc; d.zb = d.za; d.zo = zb + 4; d.epi = kEpiX; d.scale = st.cinv; break;
+              d.za = zb + 2 * st.zc; d.zb = d.za; d.zo = zb + 4; d.epi = kEpiX; d.scale = st.cinv * st.zs * st.zs;
+              break;
             default:  // A_J = X T_J(H0)
               d.za = zb + 4; d.zb = zb + 2 * st.yc; d.zo = zb + 4; d.epi = kEpiA; break;
           }
@@ -569,8 +578,9 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
     };
 
     // inverse mode, a new submatrix J in slot s: c = Tr T_J(S) / n and step 0 without products, since Z_0 = I:
-    // V_0 = Y_0 = T_J(S) / c, T_0 = 3I - Y_0 and Z_1 = T_0 / 2 are written directly (pairs 0, 2, 1), with the
-    // defect ||I - Y_0||_F / sqrt(n); only Y_1 = Y_0 T_0 / 2 needs the tensor cores.
+    // V_0 = Y_0 = T_J(S) / c and T_0 = 3I - Y_0 are written directly (pairs 0 and 1, Z's pair: Z_1 = T_0 / 2,
+    // the factor 1/2 applied by the products that read Z until its first update), with the defect
+    // ||I - Y_0||_F / sqrt(n); only Y_1 = Y_0 T_0 / 2 needs the tensor cores.
     auto start_inverse = [&](int s, int J) {
       SlotState& st = sh.slot[s];
       const int n = g.sub_n[J], n64 = (n + 63) & ~63, R = (n + 127) & ~127;
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
       const float inv = (float)(1.0 / c);
       uint16_t* base = g.planes + (size_t)(sub0 + s) * kPps * plane_elems;
       float dpart = 0.0f;   // this thread's share of ||I - Y_0||_F^2
-      // Y_0, T_0 and Z_1 from one read of T_J(S): the same pass pattern as fill_pair, three pairs out
+      // Y_0 and T_0 from one read of T_J(S): the same pass pattern as fill_pair, two pairs out
       for (int i0 = 4 * (warp - 4); i0 < n64; i0 += 4 * kEpiWarps) {
         for (int j0 = 8 * lane; j0 < n64; j0 += 256) {
           float sv[4][8];   // the pass's 32 loads, all issued before its first store
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
           for (int r = 0; r < 4; ++r) {
             const int i = i0 + r;
             if (i >= n64) break;
-            float y[8], t[8], z[8];
+            float y[8], t[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int j = j0 + u;
@@ -607,7 +617,6 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
               const float e = (i == j && in ? 1.0f : 0.0f) - y[u];
               dpart += e * e;
               t[u] = in ? (i == j ? 3.0f : 0.0f) - y[u] : 0.0f;
-              z[u] = 0.5f * t[u];
             }
             uint32_t h[4], l[4];
             const size_t off = (size_t)i * g.LD + j0;
@@ -617,10 +626,6 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
             *reinterpret_cast<uint4*>(base + plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) split2(t[2 * u], t[2 * u + 1], FMT_F16, h[u], l[u]);
-            *reinterpret_cast<uint4*>(base + 4 * plane_elems + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<uint4*>(base + 5 * plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) split2(z[2 * u], z[2 * u + 1], FMT_F16, h[u], l[u]);
             *reinterpret_cast<uint4*>(base + 2 * plane_elems + off) = make_uint4(h[0], h[1], h[2], h[3]);
             *reinterpret_cast<uint4*>(base + 3 * plane_elems + off) = make_uint4(l[0], l[1], l[2], l[3]);
           }
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
         st.job = J;
         st.n = n; st.n64 = n64; st.R = R;
         st.nrb = R / 128; st.ncb = (n64 + kTileN - 1) / kTileN; st.nks = n64 / 64;
-        st.yc = 0; st.zc = 1; st.cinv = inv;
+        st.yc = 0; st.zc = 1; st.cinv = inv; st.zs = 0.5f;
         st.steps = 1; st.rsteps = 0; st.status = kSubOk;
         st.fcur = Fmt{FMT_F16, 3}; st.fnxt = st.fcur;
         st.dprev = INFINITY;
@@ -894,7 +899,8 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
           const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * 256;
           uint32_t r[32];
           if (live && grp < nch) tc::tmem_ld32(taddr + 32 * grp, r);
-          const float sc = d.f.fmt == FMT_E4M3 ? kF8Down : 1.0f;   // E4M3 operand scales
+          // E4M3 operand scales; and the factor of the inverse mode's Z before its first update
+          const float sc = (d.f.fmt == FMT_E4M3 ? kF8Down : 1.0f) * (kMode == 1 && epi == kEpiT ? d.pscale : 1.0f);
           for (int c0 = grp; c0 < nch; c0 += kGroups) {
             const int col0 = kTileN * cb + 32 * c0;
             float v[32];
@@ -1044,7 +1050,7 @@ __global__ void __launch_bounds__(Shape<kMode>::kThreads, 1)
             st.kind = st.zdone ? 0 : 2;
             st.zdone = 0;
             break;
-          case 2: st.zc = st.zc == 1 ? 4 : 1; st.kind = st.last ? 3 : 0; break;
+          case 2: st.zc = st.zc == 1 ? 4 : 1; st.zs = 1.0f; st.kind = st.last ? 3 : 0; break;
           case 3: st.kind = 4; break;
           default: break;
         }
