@@ -848,6 +848,8 @@ def main():
         "extra": extra,
         "paths_one_mu": paths,
         "learned_bounds": bounds,
+        "tuned_shapes": {f"{k} bucket {b}": nl.nolsm_tc_shape(k, args.precision if k == "sign" else "fp16", b)
+                         for k in ("sign", "inverse") for b in (0, 1)},
         "energy_weighted": energy_weighted,
         "combination": combination,
     }

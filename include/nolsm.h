@@ -517,6 +517,19 @@ nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, const int32
                                 const double* Hc, const double* lam, double mu, const nolsm_options* opts,
                                 nolsm_stream_t stream, double* Dc, double* t_S, double* t_H, int32_t* iters,
                                 int32_t* status);
+/* Launch shape of the tensor-core kernel (no counterpart in the paper, which drives library GEMMs). The kernel
+ * comes in two shapes: 0 (384 threads, two epilogue groups, output tiles of 128 rows x up to 256 columns) and
+ * 1 (512 threads, three epilogue groups, 128 x up to 192, a register split between warpgroups). Each solve
+ * (kernel 0: sign iteration) or preparation chunk (kernel 1: inverse square root) splits its submatrices,
+ * largest first, into two buckets, n above 192 (bucket 1) and the rest (bucket 0). The first time a process
+ * meets a (kernel, precision, bucket), both shapes run on that bucket's largest submatrices (32 per slot
+ * of every SM), timed with CUDA events on the caller's stream, and the faster is kept for the life of the
+ * process; the timed runs' results are computed again by the bucket's launch. Setting the environment
+ * variable NOLSM_TC_SHAPE to "0" or "1" fixes the shape instead (read at every call); E4M3 and the reruns of
+ * failed submatrices always take shape 0. Returns the shape chosen so far for (kernel, precision, bucket), or
+ * -1 when none has been measured yet. Host only; thread-safe. */
+int32_t nolsm_tc_shape(int32_t kernel, int32_t precision, int32_t bucket);
+
 const char* nolsm_status_str(nolsm_status s);
 const char* nolsm_last_error(void);
 

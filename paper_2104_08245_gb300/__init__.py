@@ -59,6 +59,15 @@ def options(precision="fp64", **kw) -> NolsmOptions:
     return o
 
 
+def nolsm_tc_shape(kernel: str, precision, bucket: int) -> int:
+    """Launch shape chosen in this process (0 or 1, -1 while not measured) for kernel "sign" or "inverse",
+    a precision (name or value; the inverse square root always runs in "fp16") and bucket 0 (n <= 192) or
+    1 (n > 192)."""
+    k = {"sign": 0, "inverse": 1}[kernel]
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return int(_abi.load().nolsm_tc_shape(k, p, int(bucket)))
+
+
 class DeviceSystem:
     """Block-CSR S and H0 copied to device tensors (caller-owned memory for the ABI). values=False copies
     the patterns only (the elements are then generated on the device, nolsm_plan_set_elements)."""

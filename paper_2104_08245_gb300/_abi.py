@@ -119,6 +119,7 @@ SIGNATURES = [
     ("nolsm_training_data", c_int32, [c_void_p, c_double, ctypes.POINTER(NolsmOptions), c_void_p, c_void_p,
                                       c_void_p]),
     ("nolsm_status_str", ctypes.c_char_p, [c_int32]),
+    ("nolsm_tc_shape", c_int32, [c_int32, c_int32, c_int32]),
     ("nolsm_last_error", ctypes.c_char_p, []),
 ]
 

@@ -558,6 +558,8 @@ nolsm_status prepare(nolsm_plan* plan, int64_t j0, int64_t j1, int cls, cudaStre
       NsInvArgs ia;
       ia.order = plan->prep_order.as<int32_t>();
       ia.count = (int32_t)(e - J);
+      ia.n_large = 0;
+      while (ia.n_large < ia.count && plan->h_sub_n[ord[(size_t)ia.n_large]] > 192) ++ia.n_large;
       ia.max_n = chunk_max_n;
       ia.ws = g.ws;
       ia.a_base = g.a_base;

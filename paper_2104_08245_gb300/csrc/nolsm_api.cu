@@ -177,6 +177,10 @@ void nolsm_options_default(nolsm_options* o, int32_t precision) {
   o->sub_end = 0;
 }
 
+int32_t nolsm_tc_shape(int32_t kernel, int32_t precision, int32_t bucket) {
+  return tc_shape_choice(kernel, precision, bucket);
+}
+
 const char* nolsm_status_str(nolsm_status s) {
   switch (s) {
     case NOLSM_OK: return "ok";

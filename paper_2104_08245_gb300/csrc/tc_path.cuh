@@ -17,8 +17,9 @@ int main_terms(int precision);
 // a_off[J] - a_base; prep_out[J] = kSubOk, or kSubRefine when the iteration did not reach tol_inv within
 // max_inv steps (the FP64 preparation then takes the submatrix), or kSubTimeout.
 struct NsInvArgs {
-  const int32_t* order;
+  const int32_t* order;         // largest first
   int32_t count;
+  int32_t n_large;              // how many of them (a prefix of order) have n above 192
   int32_t max_n;
   const double* ws;
   int64_t a_base, chunk_n2;
@@ -32,5 +33,9 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
 
 // frees the tensor-core path's workspaces held by the plan
 void tc_release(nolsm_plan* plan);
+
+// launch shape chosen in this process for (mode 0 sign / 1 inverse, precision, bucket 0: n <= 192 / 1: n > 192):
+// 0 or 1, or -1 while not measured
+int tc_shape_choice(int mode, int precision, int bucket);
 
 }  // namespace nolsm
