@@ -919,12 +919,14 @@ __global__ void __launch_bounds__(Shape<kShape>::kThreads, 1)
               if (epi == kEpiT) {
                 if (inner) {
                   const float s = rin ? sc : 0.0f;
+                  float q4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four partial sums: a dependence chain of 8, not 32
 #pragma unroll
                   for (int j = 0; j < 32; ++j) {
                     const float p = s * __uint_as_float(r[j]);   // P_ij, off the diagonal: (I - P)_ij = -p
-                    part = fmaf(p, p, part);
+                    q4[j & 3] = fmaf(p, p, q4[j & 3]);
                     v[j] = -p;                                   // (3I - P)_ij
                   }
+                  part += (q4[0] + q4[1]) + (q4[2] + q4[3]);
                 } else {
 #pragma unroll
                   for (int j = 0; j < 32; ++j) {
@@ -1290,7 +1292,8 @@ static int env_shape() {
 // first time, both shapes run on the bucket's largest submatrices (32 per slot of every SM: with fewer, the
 // start and the tail of the launch decide; the shapes differ by 3-40 % in steady state), timed with CUDA
 // events on the stream, and the faster is kept; every result of those runs is then computed again by the
-// bucket's launch. pending(order, count) resets the bucket's statuses before each launch.
+// bucket's launch (a measurement in which a bounded wait ran out is not kept). pending(order, count) resets
+// the bucket's statuses before each launch.
 template <typename Pending>
 static nolsm_status run_bucket(int mode, int precision, int bucket, bool fixed0, const TcMaps& m, TcArgs g,
                                const int32_t* order, int32_t count, int sms, cudaStream_t st, Pending pending) {
@@ -1320,9 +1323,17 @@ static nolsm_status run_bucket(int mode, int precision, int bucket, bool fixed0,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    shape = ms[1] < ms[0] ? 1 : 0;
-    std::lock_guard<std::mutex> lk(g_shape_mu);
-    g_shape[mode][pi][bucket] = shape;
+    // a measurement in which a wait ran out (the kernels' error flag) is not kept: this call takes shape 0
+    int32_t errf = 0;
+    NOLSM_CUDA_TRY(cudaMemcpyAsync(&errf, g.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (errf != 0) {
+      shape = 0;
+    } else {
+      shape = ms[1] < ms[0] ? 1 : 0;
+      std::lock_guard<std::mutex> lk(g_shape_mu);
+      g_shape[mode][pi][bucket] = shape;
+    }
   }
   g.j1 = count;
   NOLSM_TRY(pending(order, count));
