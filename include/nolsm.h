@@ -521,7 +521,8 @@ nolsm_status nolsm_sign_noalloc(int32_t count, const int32_t* sub_n, const int32
  * comes in two shapes: 0 (384 threads, two epilogue groups, output tiles of 128 rows x up to 256 columns) and
  * 1 (512 threads, three epilogue groups, 128 x up to 192, a register split between warpgroups). Each solve
  * (kernel 0: sign iteration) or preparation chunk (kernel 1: inverse square root) splits its submatrices,
- * largest first, into two buckets, n above 192 (bucket 1) and the rest (bucket 0). The first time a process
+ * largest first, into two buckets, n above 192 (bucket 1) and the rest (bucket 0), and launches them once
+ * together when both take the same shape, else once each. The first time a process
  * meets a (kernel, precision, bucket), both shapes run on that bucket's largest submatrices (32 per slot
  * of every SM), timed with CUDA events on the caller's stream, and the faster is kept for the life of the
  * process; the timed runs' results are computed again by the bucket's launch. Setting the environment

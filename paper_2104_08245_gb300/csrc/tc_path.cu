@@ -1287,26 +1287,26 @@ static int env_shape() {
   return -1;
 }
 
-// Runs one bucket of submatrices, order[0, count) (all with n above 192, or all at most 192): with the shape
-// that NOLSM_TC_SHAPE fixes, else the one measured faster for (mode, precision, bucket) in this process. The
+// The launch shape of one bucket of submatrices, order[0, count) (all with n above 192, or all at most 192):
+// the one NOLSM_TC_SHAPE fixes, else the one measured faster for (mode, precision, bucket) in this process. The
 // first time, both shapes run on the bucket's largest submatrices (32 per slot of every SM: with fewer, the
 // start and the tail of the launch decide; the shapes differ by 3-40 % in steady state), timed with CUDA
-// events on the stream, and the faster is kept; every result of those runs is then computed again by the
-// bucket's launch (a measurement in which a bounded wait ran out is not kept). pending(order, count) resets
-// the bucket's statuses before each launch.
+// events on the stream, and the faster is kept (not when a bounded wait ran out in the measurement); the
+// results of those runs are computed again by the launches that follow. pending(order, count) resets the
+// statuses of the submatrices a launch takes.
 template <typename Pending>
-static nolsm_status run_bucket(int mode, int precision, int bucket, bool fixed0, const TcMaps& m, TcArgs g,
-                               const int32_t* order, int32_t count, int sms, cudaStream_t st, Pending pending) {
-  if (count <= 0) return NOLSM_OK;
+static nolsm_status bucket_shape(int mode, int precision, int bucket, bool fixed0, const TcMaps& m, TcArgs g,
+                                 const int32_t* order, int32_t count, int sms, cudaStream_t st, Pending pending,
+                                 int* out) {
   int shape = fixed0 ? 0 : env_shape();
   const int pi = precision & 7;
   if (shape < 0) {
     std::lock_guard<std::mutex> lk(g_shape_mu);
     shape = g_shape[mode][pi][bucket];
   }
-  g.j0 = 0;
-  g.order = order;
   if (shape < 0) {
+    g.j0 = 0;
+    g.order = order;
     const int32_t sample = std::min<int32_t>(count, 32 * kSlots * sms);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms[2] = {0.0f, 0.0f};
@@ -1323,7 +1323,6 @@ static nolsm_status run_bucket(int mode, int precision, int bucket, bool fixed0,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // a measurement in which a wait ran out (the kernels' error flag) is not kept: this call takes shape 0
     int32_t errf = 0;
     NOLSM_CUDA_TRY(cudaMemcpyAsync(&errf, g.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1335,9 +1334,36 @@ static nolsm_status run_bucket(int mode, int precision, int bucket, bool fixed0,
       g_shape[mode][pi][bucket] = shape;
     }
   }
-  g.j1 = count;
-  NOLSM_TRY(pending(order, count));
-  return launch_shape(mode, shape, m, g, sms, st);
+  *out = shape;
+  return NOLSM_OK;
+}
+
+// Runs the submatrices order[0, count), largest first, of which the first n_large have n above 192: each bucket
+// in its shape (bucket_shape), as one launch over both when the shapes agree (no second launch tail), else one
+// launch per bucket.
+template <typename Pending>
+static nolsm_status run_buckets(int mode, int precision, bool fixed0, const TcMaps& m, TcArgs g, const int32_t* order,
+                                int32_t n_large, int32_t count, int sms, cudaStream_t st, Pending pending) {
+  if (count <= 0) return NOLSM_OK;
+  int s1 = -1, s0 = -1;
+  if (n_large > 0) NOLSM_TRY(bucket_shape(mode, precision, 1, fixed0, m, g, order, n_large, sms, st, pending, &s1));
+  if (count > n_large)
+    NOLSM_TRY(bucket_shape(mode, precision, 0, fixed0, m, g, order + n_large, count - n_large, sms, st, pending, &s0));
+  g.j0 = 0;
+  if (n_large == 0 || n_large == count || s1 == s0) {
+    g.order = order;
+    g.j1 = count;
+    NOLSM_TRY(pending(order, count));
+    return launch_shape(mode, n_large > 0 ? s1 : s0, m, g, sms, st);
+  }
+  g.order = order;
+  g.j1 = n_large;
+  NOLSM_TRY(pending(order, n_large));
+  NOLSM_TRY(launch_shape(mode, s1, m, g, sms, st));
+  g.order = order + n_large;
+  g.j1 = count - n_large;
+  NOLSM_TRY(pending(order + n_large, count - n_large));
+  return launch_shape(mode, s0, m, g, sms, st);
 }
 
 int tc_shape_choice(int mode, int precision, int bucket) {
@@ -1466,11 +1492,9 @@ nolsm_status solve_tc(nolsm_plan* plan, double mu, const nolsm_options& o, int64
   if (spec.list) {   // reruns: one launch in list order, shape 0
     NOLSM_TRY(pending(spec.list, spec.count));
     NOLSM_TRY(launch_shape(0, 0, m, g, sms, st));
-  } else {           // two buckets of the largest-first order: n above 192, the rest
-    const int32_t* ord = S->order.as<int32_t>();
-    const int32_t nl = S->ord_large, nall = (int32_t)(j1 - j0);
-    NOLSM_TRY(run_bucket(0, o.precision, 1, f8, m, g, ord, nl, sms, st, pending));
-    NOLSM_TRY(run_bucket(0, o.precision, 0, f8, m, g, ord + nl, nall - nl, sms, st, pending));
+  } else {           // the largest-first order in its two buckets: n above 192, the rest
+    NOLSM_TRY(run_buckets(0, o.precision, f8, m, g, S->order.as<int32_t>(), S->ord_large, (int32_t)(j1 - j0), sms, st,
+                          pending));
   }
   plan->stats.launches += 2;
   if (sym) {   // D_c = L^-T U and the traces
@@ -1545,8 +1569,8 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
   g.tol_inv = a.tol_inv; g.max_inv = a.max_inv;
   g.wait_ns = kWaitNs;
   g.flops = S->inv_flops.as<double>();
-  // two buckets of the largest-first order (n above 192, the rest), each in its tuned shape; every submatrix
-  // of a launch starts as "timed out" and the kernel overwrites what it takes. (The first call in a process
+  // the largest-first order in its two buckets (n above 192, the rest), each in its tuned shape; every
+  // submatrix of a launch starts as "timed out" and the kernel overwrites what it takes. (The first call in a process
   // also counts the flops of the shape measurements.)
   TcMaps m{mA, mB, mS, mA, mB, mS16, mS2, mS16x2};
   auto pending = [&](const int32_t* list, int32_t count) -> nolsm_status {
@@ -1554,8 +1578,7 @@ nolsm_status launch_ns_inverse(nolsm_plan* plan, const NsInvArgs& a, cudaStream_
     NOLSM_LAUNCH_CHECK();
     return NOLSM_OK;
   };
-  NOLSM_TRY(run_bucket(1, NOLSM_FP16, 1, false, m, g, a.order, a.n_large, sms, st, pending));
-  NOLSM_TRY(run_bucket(1, NOLSM_FP16, 0, false, m, g, a.order + a.n_large, a.count - a.n_large, sms, st, pending));
+  NOLSM_TRY(run_buckets(1, NOLSM_FP16, false, m, g, a.order, a.n_large, a.count, sms, st, pending));
   double fl[2];
   NOLSM_CUDA_TRY(cudaMemcpyAsync(fl, S->inv_flops.p, sizeof(fl), cudaMemcpyDeviceToHost, st));
   NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
