@@ -34,6 +34,9 @@ WORKLOADS = {
                     "field, 6 A cutoff (profiling size)"),
     "streamed_bf16": ("spec_streamed_bf16",
                       "water-like lattice, 262144 molecules (64x64x64), 6 functions each, 6 A cutoff"),
+    "streamed_4096": ("spec_streamed_4096",
+                      "water-like lattice, 4096 molecules (16x16x16), 6 functions each, 6 A cutoff (profiling size of "
+                      "the 262144-molecule workload)"),
     "split_valence": ("spec_split_valence",
                       "water-like lattice, 16384 molecules (32x32x16), 23 functions each (split-valence-like), "
                       "6 A cutoff"),

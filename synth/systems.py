@@ -336,6 +336,12 @@ def spec_streamed_bf16(**kw) -> SystemSpec:
     return SystemSpec(64, 64, 64, **{"seed": 1003, **kw})
 
 
+def spec_streamed_4096(**kw) -> SystemSpec:
+    """4,096 molecules (16x16x16), 6 functions each: a smaller case of the 262,144-molecule workload (same recipe,
+    its own seed), for profiling."""
+    return SystemSpec(16, 16, 16, **{"seed": 1013, **kw})
+
+
 def spec_split_valence(**kw) -> SystemSpec:
     """16,384 molecules (32x32x16), 23 functions each."""
     return SystemSpec(32, 32, 16, **{"nbf": "23", "seed": 1004, **kw})
