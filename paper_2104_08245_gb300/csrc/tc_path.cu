@@ -373,24 +373,38 @@ __global__ void __launch_bounds__(Shape<kShape>::kThreads, 1)
   if (warp < 4) {
   if constexpr (kShape == 1) tc::setmaxnreg_dec<kRegsLow>();   // the TMA / MMA warpgroup gives registers up
   if (warp == 0 && lane == 0) {
-    // ------------------------------------------------ producer: schedules the products of both slots
-    // round robin over live slots; a slot's next product is issued once the epilogue of its previous
-    // product (or its initialisation) has arrived on the slot's epi_done barrier
-    bool alive[kSlots] = {true, true};
-    uint32_t epar[kSlots] = {0, 0};
+    // ------------------------------------------------ producer: schedules the products of the slots
+    // a slot's next product is issued once the epilogue of its previous product (or its initialisation) has
+    // arrived on the slot's epi_done barrier; the live slots are polled round robin from the one after the
+    // last pick, and the first that is ready goes (no slot waits behind another's epilogue)
+    bool alive[kSlots];
+    uint32_t epar[kSlots];
+    for (int c = 0; c < kSlots; ++c) {
+      alive[c] = true;
+      epar[c] = 0;
+    }
     uint32_t kcount = 0;
     int s = 0;
     for (uint32_t i = 0;; ++i) {
       int pick = -1;
-      while (!sh.err && (alive[0] || alive[1])) {
-        if (alive[s]) {
-          if (!tc::mbar_wait(&sh.epi_done[s], epar[s], tc::globaltimer() + 4 * g.wait_ns)) { sh.err = 1; break; }
-          epar[s] ^= 1;
+      const uint64_t deadline = tc::globaltimer() + 4 * g.wait_ns;
+      for (;;) {
+        bool any = false;
+        for (int t = 0; t < kSlots && pick < 0; ++t) {
+          const int c = (s + t) % kSlots;
+          if (!alive[c]) continue;
+          any = true;
+          if (!tc::mbar_test_wait(&sh.epi_done[c], epar[c])) continue;
+          epar[c] ^= 1;
           tc::fence_proxy_async_global();   // the epilogue's plane writes, before TMA reads them
-          if (sh.slot[s].job >= 0) { pick = s; break; }
-          alive[s] = false;
+          if (sh.slot[c].job >= 0) pick = c;
+          else alive[c] = false;
         }
-        s ^= 1;
+        if (pick >= 0 || !any || sh.err) break;
+        if (tc::globaltimer() > deadline) {
+          sh.err = 1;
+          break;
+        }
       }
       Desc d;
       d.term = pick < 0 ? 1 : 0;
@@ -474,7 +488,7 @@ __global__ void __launch_bounds__(Shape<kShape>::kThreads, 1)
             ++kcount;
           }
         }
-      s = pick ^ 1;
+      s = (pick + 1) % kSlots;
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------ MMA issuer: the products in the scheduler's order
@@ -868,8 +882,7 @@ __global__ void __launch_bounds__(Shape<kShape>::kThreads, 1)
       epi_bar<kEpiThreads>();   // staging and dred free again
     };
 
-    start_slot(0);
-    start_slot(1);
+    for (int c = 0; c < kSlots; ++c) start_slot(c);
     for (uint32_t i = 0;; ++i) {
       // every epilogue thread waits for the descriptor; a wait that ran out in any of them ends all
       const bool got = tc::mbar_wait(&sh.desc_full[i % kRing], (i / kRing) & 1, tc::globaltimer() + 8 * g.wait_ns);
@@ -1599,7 +1612,7 @@ namespace {
 
 constexpr int kNaMaxN = 192;                  // largest submatrix dimension accepted
 constexpr int kNaR = 256, kNaLD = 192;        // scratch plane shape: rows rounded to 128, columns to 64
-constexpr int kNaSlots = 8;                   // scratch sub-slots: 4 CTAs with kSlots each
+constexpr int kNaSlots = 4 * kSlots;          // scratch sub-slots: 4 CTAs with kSlots each
 constexpr int kNaMaxSub = 4096;               // submatrices per call
 constexpr size_t kNaPlaneElems = (size_t)kNaR * kNaLD;
 constexpr size_t kNaPlanesBytes = sizeof(uint16_t) * kPlanes * kNaSlots * kNaPlaneElems;
