@@ -1321,21 +1321,25 @@ static nolsm_status bucket_shape(int mode, int precision, int bucket, bool fixed
     g.j0 = 0;
     g.order = order;
     const int32_t sample = std::min<int32_t>(count, 32 * kSlots * sms);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct Events {   // destroyed on every way out
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~Events() {
+        for (cudaEvent_t x : e)
+          if (x) cudaEventDestroy(x);
+      }
+    } ev;
     float ms[2] = {0.0f, 0.0f};
-    NOLSM_CUDA_TRY(cudaEventCreate(&e0));
-    NOLSM_CUDA_TRY(cudaEventCreate(&e1));
+    NOLSM_CUDA_TRY(cudaEventCreate(&ev.e[0]));
+    NOLSM_CUDA_TRY(cudaEventCreate(&ev.e[1]));
     for (int sh = 0; sh < 2; ++sh) {
       g.j1 = sample;
       NOLSM_TRY(pending(order, sample));
-      NOLSM_CUDA_TRY(cudaEventRecord(e0, st));
+      NOLSM_CUDA_TRY(cudaEventRecord(ev.e[0], st));
       NOLSM_TRY(launch_shape(mode, sh, m, g, sms, st));
-      NOLSM_CUDA_TRY(cudaEventRecord(e1, st));
-      NOLSM_CUDA_TRY(cudaEventSynchronize(e1));
-      NOLSM_CUDA_TRY(cudaEventElapsedTime(&ms[sh], e0, e1));
+      NOLSM_CUDA_TRY(cudaEventRecord(ev.e[1], st));
+      NOLSM_CUDA_TRY(cudaEventSynchronize(ev.e[1]));
+      NOLSM_CUDA_TRY(cudaEventElapsedTime(&ms[sh], ev.e[0], ev.e[1]));
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     int32_t errf = 0;
     NOLSM_CUDA_TRY(cudaMemcpyAsync(&errf, g.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     NOLSM_CUDA_TRY(cudaStreamSynchronize(st));
