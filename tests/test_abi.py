@@ -125,3 +125,15 @@ def test_c_program_links_and_calls_the_host_entry_points(lib, tmp_path):
     first, second = run.stdout.splitlines()[:2]
     assert first == "0 0 0 1 3 43 27"
     assert second
+
+
+def test_tuner_reports_no_shape_before_any_solve(lib):
+    # the launch-shape tuner measures on the GPU at the first solve of a (kernel, precision, bucket); until then,
+    # and for arguments out of range, it reports -1
+    for kernel in (0, 1):
+        for precision in range(6):
+            for bucket in (0, 1):
+                assert lib.nolsm_tc_shape(kernel, precision, bucket) == -1
+    assert lib.nolsm_tc_shape(2, 1, 0) == -1
+    assert lib.nolsm_tc_shape(0, 1, 2) == -1
+    assert lib.nolsm_tc_shape(-1, 1, 0) == -1
