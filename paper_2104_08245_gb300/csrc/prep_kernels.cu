@@ -1115,10 +1115,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_prepare_mixed(PrepArgs g, float
   if (tid == 0) g.prep_status[J] = ok ? kSubOk : (n <= g.fallback_max_n ? kSubRefine : kSubNotSpd);
 }
 
-// One row of R = E_c - T_J(S) q for CN centre columns: S_i (FP64 row of T_J(S)) against q (float2 hi/lo
-// pairs, rows of stride bJ), products and sums in double-FP32 arithmetic (each product's rounding error by FMA,
-// each sum's by TwoSum); column c is on the diagonal of E_c when c == ce. Writes w[c] (FP32) when rv.
-template <int CN>
+// One row i of R = E_c - T_J(S) q for CN centre columns: S_i[k] at Si[k] (kCol false: Si is row i, each lane
+// streams its own row through L1) or at Si[k n] (kCol: Si is column i of the symmetric T_J(S), the lanes of a
+// warp read consecutive entries; better for long rows, whose lines leave L1 before their reuse); against q
+// (float2 hi/lo pairs, rows of stride bJ), products and sums in double-FP32 arithmetic (each product's
+// rounding error by FMA, each sum's by TwoSum); column c is on the diagonal of E_c when c == ce. Writes w[c]
+// (FP32) when rv.
+template <int CN, bool kCol>
 __device__ __forceinline__ void residual_row(const double* __restrict__ Si, const float2* __restrict__ q, int n,
                                              int bJ, bool rv, int ce, float* __restrict__ w) {
   float sh[CN], sl[CN];
@@ -1126,7 +1129,7 @@ __device__ __forceinline__ void residual_row(const double* __restrict__ Si, cons
   for (int c = 0; c < CN; ++c) sh[c] = sl[c] = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < n; ++k) {
-    const float2 a = split_f64(Si[k]);
+    const float2 a = split_f64(Si[kCol ? (size_t)k * n : (size_t)k]);
     const float2* qk = q + (size_t)k * bJ;
 #pragma unroll
     for (int c = 0; c < CN; ++c) {
@@ -1143,9 +1146,11 @@ __device__ __forceinline__ void residual_row(const double* __restrict__ Si, cons
   }
 }
 
-// One row of the correction X R for CN columns of R (FP32, rows of stride bJ): four interleaved FP32 partial
-// sums along k per column, added at the end; d[c] for c < CN.
-template <int CN>
+// One row i of the correction X R (kCol false: xi is row i of X) or X^T R (kCol: xi is column i; X =
+// T_J(S)^-1 is symmetric up to its rounding, so its transpose serves as the approximate inverse as well) for
+// CN columns of R (FP32, rows of stride bJ): four interleaved FP32 partial sums along k per column, added at
+// the end; d[c] for c < CN.
+template <int CN, bool kCol>
 __device__ __forceinline__ void update_row(const float* __restrict__ xi, const float* __restrict__ R, int n, int bJ,
                                            float (&d)[8]) {
   float acc[4][CN];
@@ -1157,14 +1162,14 @@ __device__ __forceinline__ void update_row(const float* __restrict__ xi, const f
   for (; k + 4 <= n; k += 4) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float x = xi[k + u];
+      const float x = xi[kCol ? (size_t)(k + u) * n : (size_t)(k + u)];
       const float* rk = R + (size_t)(k + u) * bJ;
 #pragma unroll
       for (int c = 0; c < CN; ++c) acc[u][c] = fmaf(x, rk[c], acc[u][c]);
     }
   }
   for (; k < n; ++k) {
-    const float x = xi[k];
+    const float x = xi[kCol ? (size_t)k * n : (size_t)k];
     const float* rk = R + (size_t)k * bJ;
 #pragma unroll
     for (int c = 0; c < CN; ++c) acc[0][c] = fmaf(x, rk[c], acc[0][c]);
@@ -1175,7 +1180,8 @@ __device__ __forceinline__ void update_row(const float* __restrict__ xi, const f
 
 // After the tensor-core inverse square root (Eqs. inv1-inv3), which leaves X = T_J(S)^-1 in FP32 (in g.L32,
 // accurate to about 1e-6 of its norm) and A_J in Acache: the centre columns of T_J(S)^-1 by iterative
-// refinement with X as the approximate inverse, q <- q + X (E_c - T_J(S) q) from q = X[:, centre], the
+// refinement with X as the approximate inverse (for n above 256 its transpose, read coalesced: X is symmetric up
+// to its rounding), q <- q + X (E_c - T_J(S) q) from q = X[:, centre], the
 // residual in double-FP32 arithmetic (as in k_prepare_mixed), until the correction is below 1e-6 of q; then
 // the Gershgorin interval of A_J. A submatrix the inverse kernel flagged, or whose refinement does not
 // contract, is left flagged for the FP64 preparation.
@@ -1210,52 +1216,56 @@ __global__ void __launch_bounds__(kThreads) k_ns_qrefine(PrepArgs g, const float
   __syncthreads();
   bool conv = false;
   constexpr int kWarps = kThreads / 32;
+  // rows of T_J(S) and X read along the row by each lane up to 256 columns, as columns (coalesced) beyond
+  const bool col = n > 256;
   for (int it = 0; it < kRefineMax && !conv; ++it) {
     for (int e = tid; e < nbc; e += kThreads) qp[e] = split_f64(q[e]);
     __syncthreads();
-    // R = E_c - T_J(S) q: one row per lane, the row's products along k in double-FP32 arithmetic (as
-    // residual_df), up to 8 centre columns per sweep; every lane reads the same entries of q
+    // R = E_c - T_J(S) q: one row per lane (for n above 256 read as the column of the symmetric T_J(S):
+    // coalesced), the row's products along k in double-FP32 arithmetic (as residual_df), up to 8 centre columns
+    // per sweep; every lane reads the same entries of q
     for (int i0 = 32 * warp; i0 < n; i0 += 32 * kWarps) {
       const int i = i0 + lane;
       const bool rv = i < n;
-      const double* Si = S + (size_t)(rv ? i : 0) * n;
+      const double* Si = col ? S + (rv ? i : 0) : S + (size_t)(rv ? i : 0) * n;   // row i (or column i)
       for (int cg = 0; cg < bJ; cg += 8) {
         float* w = Wsh + (size_t)(rv ? i : 0) * bJ + cg;
         const float2* qc = qp + cg;
         const int ce = i - c0 - cg;   // row i holds the 1 of E_c's column cg + c when c == ce
         switch (min(8, bJ - cg)) {
-          case 1: residual_row<1>(Si, qc, n, bJ, rv, ce, w); break;
-          case 2: residual_row<2>(Si, qc, n, bJ, rv, ce, w); break;
-          case 3: residual_row<3>(Si, qc, n, bJ, rv, ce, w); break;
-          case 4: residual_row<4>(Si, qc, n, bJ, rv, ce, w); break;
-          case 5: residual_row<5>(Si, qc, n, bJ, rv, ce, w); break;
-          case 6: residual_row<6>(Si, qc, n, bJ, rv, ce, w); break;
-          case 7: residual_row<7>(Si, qc, n, bJ, rv, ce, w); break;
-          default: residual_row<8>(Si, qc, n, bJ, rv, ce, w); break;
+          case 1: col ? residual_row<1, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<1, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 2: col ? residual_row<2, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<2, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 3: col ? residual_row<3, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<3, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 4: col ? residual_row<4, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<4, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 5: col ? residual_row<5, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<5, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 6: col ? residual_row<6, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<6, false>(Si, qc, n, bJ, rv, ce, w); break;
+          case 7: col ? residual_row<7, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<7, false>(Si, qc, n, bJ, rv, ce, w); break;
+          default: col ? residual_row<8, true>(Si, qc, n, bJ, rv, ce, w) : residual_row<8, false>(Si, qc, n, bJ, rv, ce, w); break;
         }
       }
     }
     __syncthreads();
-    // q <- q + X R, one row of X per lane, R from shared memory (the same entries for every lane)
+    // q <- q + X R (for n above 256 X^T R, one column of X per lane: coalesced), R from shared memory (the
+    // same entries for every lane)
     float dmax = 0.0f;
     double qmax = 0.0;
     bool finite = true;
     for (int i0 = 32 * warp; i0 < n; i0 += 32 * kWarps) {
       const int i = i0 + lane;
       const bool rv = i < n;
-      const float* xi = X + (size_t)(rv ? i : 0) * n;
+      const float* xi = col ? X + (rv ? i : 0) : X + (size_t)(rv ? i : 0) * n;
       for (int cg = 0; cg < bJ; cg += 8) {
         const int cn = min(8, bJ - cg);
         float d[8];
         switch (cn) {
-          case 1: update_row<1>(xi, Wsh + cg, n, bJ, d); break;
-          case 2: update_row<2>(xi, Wsh + cg, n, bJ, d); break;
-          case 3: update_row<3>(xi, Wsh + cg, n, bJ, d); break;
-          case 4: update_row<4>(xi, Wsh + cg, n, bJ, d); break;
-          case 5: update_row<5>(xi, Wsh + cg, n, bJ, d); break;
-          case 6: update_row<6>(xi, Wsh + cg, n, bJ, d); break;
-          case 7: update_row<7>(xi, Wsh + cg, n, bJ, d); break;
-          default: update_row<8>(xi, Wsh + cg, n, bJ, d); break;
+          case 1: col ? update_row<1, true>(xi, Wsh + cg, n, bJ, d) : update_row<1, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 2: col ? update_row<2, true>(xi, Wsh + cg, n, bJ, d) : update_row<2, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 3: col ? update_row<3, true>(xi, Wsh + cg, n, bJ, d) : update_row<3, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 4: col ? update_row<4, true>(xi, Wsh + cg, n, bJ, d) : update_row<4, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 5: col ? update_row<5, true>(xi, Wsh + cg, n, bJ, d) : update_row<5, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 6: col ? update_row<6, true>(xi, Wsh + cg, n, bJ, d) : update_row<6, false>(xi, Wsh + cg, n, bJ, d); break;
+          case 7: col ? update_row<7, true>(xi, Wsh + cg, n, bJ, d) : update_row<7, false>(xi, Wsh + cg, n, bJ, d); break;
+          default: col ? update_row<8, true>(xi, Wsh + cg, n, bJ, d) : update_row<8, false>(xi, Wsh + cg, n, bJ, d); break;
         }
         if (rv) {
 #pragma unroll
